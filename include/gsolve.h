@@ -1,0 +1,152 @@
+/*
+ * gsolve — C-ABI of the GB300 solver for plane-wave scattering by a three-layer periodic
+ * dielectric grating whose middle layer holds M disk inclusions (Lai, Kobayashi, Barnett,
+ * arXiv:1412.7466).
+ *
+ * All functions return an int status (GS_OK == 0 on success) and never throw across the ABI.
+ * Host arrays passed to gs_set_* are copied; the library keeps no pointer to them.  Device
+ * pointers passed to the compute calls are owned by the caller, must hold the stated number of
+ * complex128 values (interleaved re, im) and must be valid on the context's device; the library
+ * owns and frees (in gs_destroy) every buffer it allocates.  Every kernel runs on the stream given
+ * to gs_create (the legacy default stream when NULL).  Calls on one context are not thread-safe.
+ *
+ * Paper notation used throughout: period d, interfaces Gamma1 (top) and Gamma2, wavenumbers
+ * k1, k2, k3 of the three layers and kp inside a disk, incidence angle theta with
+ * u_inc = exp(i k1 (cos(theta) x + sin(theta) y)) (sin(theta) < 0, downward), Bloch phase
+ * alpha = exp(i k1 cos(theta) d), multipole order p (2p+1 coefficients per disk).
+ */
+#ifndef GSOLVE_H
+#define GSOLVE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+#define GS_OK 0
+#define GS_ERR_ARG 1             /* a null pointer, a size out of range, an angle index out of range */
+#define GS_ERR_STATE 2           /* calls out of order (e.g. gs_solve before gs_factor)             */
+#define GS_ERR_CUDA 3            /* a CUDA runtime call failed; gs_last_error() has the message      */
+#define GS_ERR_OOM 4             /* device allocation failed                                         */
+#define GS_ERR_GEOMETRY 5        /* overlapping disks (minimum-image), disk crossing an interface    */
+#define GS_ERR_NOT_CONVERGED 6   /* GMRES hit maxit; the iterate and its residual remain readable    */
+#define GS_ERR_NUMERIC 7         /* a NaN or Inf appeared in a result                                */
+
+typedef struct gs_ctx gs_ctx;
+typedef struct { double re, im; } gs_c128;
+
+/* Precision of the inclusion-to-inclusion translation inside the matrix-vector product. */
+#define GS_FP64 0                /* complex128 throughout                                            */
+#define GS_C64 1                 /* complex64 translation with order rescaling, FP32 accumulation    */
+
+/*
+ * Layered grating (Sec. 2 "Problem formulation"; Sec. 3 discretisation; Sec. 6 parameters).
+ * Interface j is the graph y = h_j(x) = hj_0 + sum_{m=1..n_fourier} (hj_cos[m-1] cos(2 pi m x/d)
+ * + hj_sin[m-1] sin(2 pi m x/d)), x in [-d/2, d/2].  N equispaced parameter nodes per interface,
+ * J-expansions of orders -Qj..Qj about the layer centres (0,(h1_0+y0)/2), (0,(h1_0+h2_0)/2),
+ * (0,(h2_0-y0)/2) (Eq. qGreen2, repre1-repre3), Rayleigh-Bloch orders -K_rb..K_rb (Eqs. rad1,
+ * rad2), n_wallj Gauss-Legendre nodes on the walls of layer j, n_bound equispaced nodes on
+ * Gamma_u (y = y0) and Gamma_d (y = -y0), pseudo-inverse regularisation eps_pinv (Sec. 5).
+ */
+typedef struct {
+    double d;
+    double h1_0, h2_0;
+    int n_fourier;
+    const double *h1_cos, *h1_sin, *h2_cos, *h2_sin;   /* host, length n_fourier (NULL if 0) */
+    double k1, k2, k3;
+    int N;
+    double y0;
+    int Q1, Q2, Q3;
+    int K_rb;
+    int n_wall1, n_wall2, n_wall3;
+    int n_bound;
+    double eps_pinv;
+} gs_layers;
+
+/* Disk inclusions (Sec. 4): M centres xy[2*i], xy[2*i+1] (host, unit cell x in [-d/2, d/2)),
+ * radii and interior wavenumbers kp (host, length M), multipole order p (1 <= p <= 16). */
+typedef struct {
+    int M;
+    int p;
+    const double *xy;
+    const double *radius;
+    const double *kp;
+} gs_inclusions;
+
+typedef struct {
+    double tol;       /* stop when ||b - L beta|| <= tol ||b|| (relative residual, Sec. 5)            */
+    int maxit;        /* total iteration cap                                                          */
+    int restart;      /* Krylov dimension before restart (<= 400)                                     */
+    int precision;    /* GS_FP64 or GS_C64 (the latter wraps inner c64 GMRES in FP64 refinement)      */
+} gs_solve_opts;
+
+/* ---- context --------------------------------------------------------------------------------- */
+/* Creates a context on CUDA device `device`; cuda_stream is a cudaStream_t (may be NULL). */
+int gs_create(gs_ctx **out, int device, void *cuda_stream);
+void gs_destroy(gs_ctx *ctx);
+const char *gs_strerror(int status);
+/* Detail of the last failure on this context (static storage owned by the context). */
+const char *gs_last_error(gs_ctx *ctx);
+
+/* ---- problem definition ---------------------------------------------------------------------- */
+/* Sets the grating; invalidates any factorisation.  GS_ERR_ARG on non-positive sizes or
+ * wavenumbers, N odd, N > 4096, or Q, K_rb, n_wall, n_bound outside [1, 1024]. */
+int gs_set_layers(gs_ctx *ctx, const gs_layers *layers);
+/* Incidence angles (host array of n_angles values, paper convention, sin(theta) < 0). */
+int gs_set_incidence(gs_ctx *ctx, int n_angles, const double *theta);
+/* Disks; GS_ERR_GEOMETRY if two disks overlap (minimum image in x) or a disk touches an
+ * interface's extreme height band.  Requires gs_set_layers first. */
+int gs_set_inclusions(gs_ctx *ctx, const gs_inclusions *inc);
+
+/* Builds everything that depends on (geometry, angle) on the GPU in FP64 (Sec. 3 and Sec. 5):
+ * assembles the empty-grating matrix A (Eq. matA) and right-hand side f (Eq. Arhs), rescales its
+ * J-expansion columns to unit 2-norm, takes the SVD A D = U Sigma V^* by one-sided Jacobi, and
+ * assembles the disk scattering diagonal S (Sec. 4.1), B_phys (Eq. matB, physical sign) and C
+ * (Eq. matC).  Must follow gs_set_layers, gs_set_incidence and gs_set_inclusions. */
+int gs_factor(gs_ctx *ctx);
+
+/* ---- sizes ----------------------------------------------------------------------------------- */
+/* rows, cols of A; n = M (2p+1) unknowns; nB = columns of B_phys (4N + 2 Q2 + 1); nC = rows of C
+ * (4N + 2 n_wall2).  Any output pointer may be NULL. */
+int gs_dims(gs_ctx *ctx, int *rows, int *cols, int *n, int *nB, int *nC);
+
+/* ---- parity / inspection (device outputs, caller-owned) -------------------------------------- */
+/* A (unscaled) column-major rows x cols, lda = rows (Eq. matA), for angle index `angle`. */
+int gs_get_A(gs_ctx *ctx, int angle, gs_c128 *A_dev);
+/* f (Eq. Arhs), length rows. */
+int gs_get_f(gs_ctx *ctx, int angle, gs_c128 *f_dev);
+/* B_phys row-major n x nB and C row-major nC x n (Eqs. matB, matC; B carries the physical sign,
+ * so the paper's B equals -B_phys).  Either pointer may be NULL. */
+int gs_get_coupling(gs_ctx *ctx, int angle, gs_c128 *B_dev, gs_c128 *C_dev);
+/* Disk scattering diagonal s, M x (2p+1), order index fastest (Sec. 4.1). */
+int gs_get_scattering(gs_ctx *ctx, gs_c128 *s_dev);
+/* x = A^+ g = D V Sigma^+ U^* g with Sigma^+ = min(1/sigma_j, 1/eps) (Eq. applypA); g length rows,
+ * x length cols. */
+int gs_pinv_apply(gs_ctx *ctx, int angle, const gs_c128 *g_dev, gs_c128 *x_dev);
+
+/* ---- hot path (device vectors of length n, layout beta[i*(2p+1) + (m+p)]) ------------------- */
+/* alpha = T beta: all-pairs Graf translation including the +-d images, self term (i, l=0) left
+ * out (Sec. 4.2 Eq. trans, Sec. 5 Eq. repre3_mod).  precision GS_FP64 or GS_C64. */
+int gs_translate(gs_ctx *ctx, int angle, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision);
+/* y = L x = x - S T x + S B_phys A^+ C x (the preconditioned Schur operator, Sec. 5). */
+int gs_apply(gs_ctx *ctx, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision);
+/* b = S B_phys A^+ f (right-hand side of the preconditioned Schur system, Sec. 5). */
+int gs_rhs(gs_ctx *ctx, int angle, gs_c128 *b_dev);
+/* Solves L beta = b by restarted GMRES on the device (Sec. 5); beta0_dev (nullable) is the start.
+ * Returns GS_ERR_NOT_CONVERGED if maxit is reached (the iterate stays readable). */
+int gs_solve(gs_ctx *ctx, int angle, const gs_solve_opts *opts, const gs_c128 *beta0_dev);
+/* Copies the last solution of `angle` into beta_dev (length n). */
+int gs_get_beta(gs_ctx *ctx, int angle, gs_c128 *beta_dev);
+/* Iterations and final relative residial ||b - L beta||/||b|| (recomputed in FP64) of the last solve. */
+int gs_stats(gs_ctx *ctx, int angle, int *iters, double *relres);
+/* Bragg amplitudes of the propagating orders (Sec. 2 rad1/rad2; Sec. 5 alpha = A^+(f - C beta)),
+ * written to HOST arrays: orders_top[*n_top], c[*n_top], orders_bot[*n_bot], d[*n_bot], each of
+ * capacity >= 2 K_rb + 1, and the relative flux error
+ * |sum k_{1,n}|c_n|^2 + sum k_{3,n}|d_n|^2 - k1|sin theta|| / (k1 |sin theta|)  (Sec. 6). */
+int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
+             int *n_bot, int *orders_bot, gs_c128 *d, double *flux_err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSOLVE_H */

@@ -1,0 +1,283 @@
+"""Python binding of libgsolve (the C-ABI declared in include/gsolve.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA kernels.
+Device vectors are torch complex128 tensors on the context's device; host inputs are numpy or
+Python sequences.  Importing this package does not load the library; creating a GratingSolver
+does, and raises if libgsolve.so has not been built (``python -m paper_1412_7466_gb300.build``)
+or no CUDA device is present -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsolve.so")
+
+GS_OK = 0
+GS_ERR_ARG = 1
+GS_ERR_STATE = 2
+GS_ERR_CUDA = 3
+GS_ERR_OOM = 4
+GS_ERR_GEOMETRY = 5
+GS_ERR_NOT_CONVERGED = 6
+GS_ERR_NUMERIC = 7
+GS_FP64 = 0
+GS_C64 = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class gs_layers(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_double), ("h1_0", ctypes.c_double), ("h2_0", ctypes.c_double),
+                ("n_fourier", ctypes.c_int),
+                ("h1_cos", _dp), ("h1_sin", _dp), ("h2_cos", _dp), ("h2_sin", _dp),
+                ("k1", ctypes.c_double), ("k2", ctypes.c_double), ("k3", ctypes.c_double),
+                ("N", ctypes.c_int), ("y0", ctypes.c_double),
+                ("Q1", ctypes.c_int), ("Q2", ctypes.c_int), ("Q3", ctypes.c_int),
+                ("K_rb", ctypes.c_int),
+                ("n_wall1", ctypes.c_int), ("n_wall2", ctypes.c_int), ("n_wall3", ctypes.c_int),
+                ("n_bound", ctypes.c_int), ("eps_pinv", ctypes.c_double)]
+
+
+class gs_inclusions(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("p", ctypes.c_int), ("xy", _dp), ("radius", _dp), ("kp", _dp)]
+
+
+class gs_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+_SIGS = {
+    "gs_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "gs_destroy": (None, [_vp]),
+    "gs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "gs_last_error": (ctypes.c_char_p, [_vp]),
+    "gs_set_layers": (ctypes.c_int, [_vp, ctypes.POINTER(gs_layers)]),
+    "gs_set_incidence": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "gs_set_inclusions": (ctypes.c_int, [_vp, ctypes.POINTER(gs_inclusions)]),
+    "gs_factor": (ctypes.c_int, [_vp]),
+    "gs_dims": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
+    "gs_get_A": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_get_f": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_get_coupling": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "gs_get_scattering": (ctypes.c_int, [_vp, _vp]),
+    "gs_pinv_apply": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "gs_translate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
+    "gs_apply": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
+    "gs_rhs": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_solve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gs_solve_opts), _vp]),
+    "gs_get_beta": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_stats": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
+    "gs_bragg": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _vp, _ip, _ip, _vp, _dp]),
+}
+
+_lib = None
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libgsolve.so (raises if it has not been built) and declares the signatures."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_1412_7466_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _arr(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(_dp)
+
+
+class GratingSolver:
+    """One gsolve context on a CUDA device (torch's current stream at creation)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("GratingSolver needs a CUDA device (there is no CPU fallback)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = _vp()
+        self._check(self.lib.gs_create(ctypes.byref(h), device, _vp(stream.cuda_stream)), "gs_create", ctx=None)
+        self.ctx = h
+        self._keep = []
+
+    # -- plumbing ------------------------------------------------------------------------------
+    def _check(self, st, what, ctx="self", ok=(GS_OK,)):
+        if st in ok:
+            return st
+        c = self.ctx if ctx == "self" else None
+        detail = self.lib.gs_last_error(c).decode() if c else ""
+        raise GsError(st, f"{what}: {self.lib.gs_strerror(st).decode()} {detail}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.gs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _cvec(self, n):
+        return self.torch.empty(n, dtype=self.torch.complex128, device=self.device)
+
+    def _as_dev(self, x):
+        t = self.torch.as_tensor(x)
+        return t.to(device=self.device, dtype=self.torch.complex128).contiguous()
+
+    # -- problem definition ---------------------------------------------------------------------
+    def set_layers(self, g: dict):
+        nf = max(len(g["gamma1"].get("cos", [])), len(g["gamma1"].get("sin", [])),
+                 len(g["gamma2"].get("cos", [])), len(g["gamma2"].get("sin", [])))
+
+        def pad(v):
+            v = list(v) + [0.0] * (nf - len(v))
+            return _arr(v if nf else [0.0])
+
+        arrs = [pad(g["gamma1"].get("cos", [])), pad(g["gamma1"].get("sin", [])),
+                pad(g["gamma2"].get("cos", [])), pad(g["gamma2"].get("sin", []))]
+        self._keep = [a for a, _ in arrs]
+        L = gs_layers(d=g["d"], h1_0=g["gamma1"]["h0"], h2_0=g["gamma2"]["h0"], n_fourier=nf,
+                      h1_cos=arrs[0][1], h1_sin=arrs[1][1], h2_cos=arrs[2][1], h2_sin=arrs[3][1],
+                      k1=g["k"][0], k2=g["k"][1], k3=g["k"][2], N=g["N"], y0=g["y0"],
+                      Q1=g["Q"][0], Q2=g["Q"][1], Q3=g["Q"][2], K_rb=g["K_rb"],
+                      n_wall1=g["n_wall"][0], n_wall2=g["n_wall"][1], n_wall3=g["n_wall"][2],
+                      n_bound=g["n_bound"], eps_pinv=g["eps_pinv"])
+        self._check(self.lib.gs_set_layers(self.ctx, ctypes.byref(L)), "gs_set_layers")
+        self.grating = g
+
+    def set_incidence(self, thetas):
+        a, p = _arr(np.atleast_1d(thetas))
+        self._check(self.lib.gs_set_incidence(self.ctx, a.size, p), "gs_set_incidence")
+        self.thetas = a.copy()
+
+    def set_inclusions(self, disks: dict):
+        xy, pxy = _arr(disks["xy"])
+        r, pr = _arr(disks["radius"])
+        kp, pkp = _arr(disks["kp"])
+        I = gs_inclusions(M=xy.shape[0], p=int(disks["p"]), xy=pxy, radius=pr, kp=pkp)
+        self._check(self.lib.gs_set_inclusions(self.ctx, ctypes.byref(I)), "gs_set_inclusions")
+        self.M, self.p = xy.shape[0], int(disks["p"])
+
+    def factor(self):
+        self._check(self.lib.gs_factor(self.ctx), "gs_factor")
+
+    def dims(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(self.lib.gs_dims(self.ctx, *[ctypes.byref(x) for x in v]), "gs_dims")
+        return dict(zip(("rows", "cols", "n", "nB", "nC"), [x.value for x in v]))
+
+    # -- inspection -----------------------------------------------------------------------------
+    def get_A(self, angle=0):
+        d = self.dims()
+        t = self._cvec(d["rows"] * d["cols"])
+        self._check(self.lib.gs_get_A(self.ctx, angle, _ptr(t)), "gs_get_A")
+        return t.view(d["cols"], d["rows"]).T     # column-major storage
+
+    def get_f(self, angle=0):
+        t = self._cvec(self.dims()["rows"])
+        self._check(self.lib.gs_get_f(self.ctx, angle, _ptr(t)), "gs_get_f")
+        return t
+
+    def get_coupling(self, angle=0):
+        d = self.dims()
+        B = self._cvec(d["n"] * d["nB"])
+        Cm = self._cvec(d["nC"] * d["n"])
+        self._check(self.lib.gs_get_coupling(self.ctx, angle, _ptr(B), _ptr(Cm)), "gs_get_coupling")
+        return B.view(d["n"], d["nB"]), Cm.view(d["nC"], d["n"])
+
+    def get_scattering(self):
+        t = self._cvec(self.dims()["n"])
+        self._check(self.lib.gs_get_scattering(self.ctx, _ptr(t)), "gs_get_scattering")
+        return t.view(self.M, 2 * self.p + 1)
+
+    def pinv_apply(self, g, angle=0):
+        g = self._as_dev(g)
+        x = self._cvec(self.dims()["cols"])
+        self._check(self.lib.gs_pinv_apply(self.ctx, angle, _ptr(g), _ptr(x)), "gs_pinv_apply")
+        return x
+
+    # -- hot path -------------------------------------------------------------------------------
+    def translate(self, beta, angle=0, precision=GS_FP64, out=None):
+        beta = self._as_dev(beta)
+        out = self._cvec(beta.numel()) if out is None else out
+        self._check(self.lib.gs_translate(self.ctx, angle, _ptr(beta), _ptr(out), precision), "gs_translate")
+        return out
+
+    def apply(self, x, angle=0, precision=GS_FP64, out=None):
+        x = self._as_dev(x)
+        out = self._cvec(x.numel()) if out is None else out
+        self._check(self.lib.gs_apply(self.ctx, angle, _ptr(x), _ptr(out), precision), "gs_apply")
+        return out
+
+    def rhs(self, angle=0):
+        b = self._cvec(self.dims()["n"])
+        self._check(self.lib.gs_rhs(self.ctx, angle, _ptr(b)), "gs_rhs")
+        return b
+
+    def solve(self, angle=0, tol=1e-11, maxit=1000, restart=200, precision=GS_FP64, beta0=None,
+              allow_unconverged=False):
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision)
+        b0 = _ptr(self._as_dev(beta0)) if beta0 is not None else None
+        ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
+        return self._check(self.lib.gs_solve(self.ctx, angle, ctypes.byref(o), b0), "gs_solve", ok=ok)
+
+    def get_beta(self, angle=0):
+        t = self._cvec(self.dims()["n"])
+        self._check(self.lib.gs_get_beta(self.ctx, angle, _ptr(t)), "gs_get_beta")
+        return t
+
+    def stats(self, angle=0):
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.gs_stats(self.ctx, angle, ctypes.byref(it), ctypes.byref(rr)), "gs_stats")
+        return it.value, rr.value
+
+    def bragg(self, angle=0):
+        cap = 2 * self.grating["K_rb"] + 1
+        nt, nb = ctypes.c_int(), ctypes.c_int()
+        ot = (ctypes.c_int * cap)()
+        ob = (ctypes.c_int * cap)()
+        c = np.zeros(cap, dtype=np.complex128)
+        d = np.zeros(cap, dtype=np.complex128)
+        fe = ctypes.c_double()
+        self._check(self.lib.gs_bragg(self.ctx, angle, ctypes.byref(nt), ot, c.ctypes.data_as(_vp),
+                                      ctypes.byref(nb), ob, d.ctypes.data_as(_vp), ctypes.byref(fe)),
+                    "gs_bragg")
+        return {"n_top": np.array(ot[:nt.value]), "c": c[:nt.value].copy(),
+                "n_bot": np.array(ob[:nb.value]), "d": d[:nb.value].copy(), "flux_err": fe.value}

@@ -1,0 +1,125 @@
+// Internal context of the gsolve library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gsolve.h"
+#include "gs_common.cuh"
+
+// Row and column blocks of A (Eq. matA): unknowns [mu1, sigma1, mu2, sigma2, a2, a1, a3, c, d];
+// rows [Gamma1 value, Gamma1 normal, Gamma2 value, Gamma2 normal, middle walls (value, x-deriv),
+// upper walls, lower walls, Gamma_u (value, y-deriv), Gamma_d (value, y-deriv)].
+struct Layout {
+    int N, Q1, Q2, Q3, K, nw1, nw2, nw3, nb;
+    int col_mu1, col_sig1, col_mu2, col_sig2, col_a2, col_a1, col_a3, col_c, col_d, cols;
+    int row_g1v, row_g1n, row_g2v, row_g2n, row_w2v, row_w2n, row_w1v, row_w1n, row_w3v, row_w3n,
+        row_uv, row_un, row_dv, row_dn, rows;
+    int nB() const { return col_a1; }     // columns of B_phys: mu1..a2
+    int nC() const { return row_w1v; }    // rows of C: Gamma1, Gamma2, middle walls
+};
+
+struct AngleData {
+    double theta = 0, kappa0 = 0;
+    cplx alpha = {1, 0};
+    double *kappa = nullptr;     // 2K+1
+    cplx *k1n = nullptr;         // 2K+1, k_{1,n}
+    cplx *k3n = nullptr;         // 2K+1, k_{3,n}
+    cplx *f = nullptr;           // rows
+    cplx *W = nullptr;           // rows x cols column-major: A D V = U Sigma after Jacobi
+    cplx *Vr = nullptr;          // cols x cols row-major V
+    double *dscale = nullptr;    // cols, column scaling D
+    double *coef = nullptr;      // cols, 1/(sigma max(sigma, eps)) (0 for sigma = 0)
+    double *sigma = nullptr;     // cols
+    cplx *B = nullptr;           // n x nB row-major (physical sign)
+    cplx *Cm = nullptr;          // nC x n row-major
+    cplx *beta = nullptr;        // n, last solution
+    int sweeps = 0;
+    int iters = 0;
+    double relres = -1.0;
+};
+
+struct gs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // layers
+    bool have_layers = false;
+    gs_layers L{};
+    std::vector<double> four[4];   // h1_cos, h1_sin, h2_cos, h2_sin
+    Layout lay{};
+    double *curve[2] = {nullptr, nullptr};   // per interface: 7 arrays of N (x, px, py, nx, ny, speed, w)
+    double *wall_y[3] = {nullptr, nullptr, nullptr};
+    double *bound_x = nullptr;
+    double *kress = nullptr;
+    double *four_dev = nullptr;              // device copy of the Fourier coefficients
+    double yL1 = 0, yL2 = 0;                 // interface heights at the walls
+    double h1_min = 0, h2_max = 0;
+
+    // incidence
+    std::vector<double> thetas;
+
+    // inclusions
+    bool have_inc = false;
+    int M = 0, p = 0, nc = 0;
+    double *xy = nullptr, *radius = nullptr, *kp = nullptr;
+    cplx *s = nullptr;                       // M x nc
+
+    bool factored = false;
+    std::vector<AngleData> ang;
+
+    // scratch
+    cplx *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;   // n each
+    cplx *g = nullptr;                                  // rows
+    cplx *w = nullptr, *x = nullptr;                     // cols
+    cplx *Vtmp = nullptr;                                // cols x cols, Jacobi rotations
+    cplx *part = nullptr;                                // translation partials
+    size_t part_elems = 0;
+    // GMRES workspace
+    int kdim = 0;
+    cplx *Vk = nullptr;                                  // (kdim+1) x n
+    cplx *Hh = nullptr;                                  // (kdim+1) x kdim column-major
+    cplx *cs = nullptr, *sn = nullptr, *gg = nullptr, *yy = nullptr;
+    double *dscal = nullptr;                             // device scalars
+    double *hscal = nullptr;                             // pinned host scalars
+    unsigned long long *dcount = nullptr;
+
+    int n() const { return M * nc; }
+};
+
+// error helpers (defined in gs_api.cu)
+int gs_fail(gs_ctx *c, int code, const std::string &msg);
+#define GS_CUDA(ctx, call)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return gs_fail((ctx), e_ == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA,     \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+#define GS_CHECK_LAUNCH(ctx) GS_CUDA(ctx, cudaGetLastError())
+#define GS_TRY(expr)                \
+    do {                            \
+        int st_ = (expr);           \
+        if (st_ != GS_OK) return st_; \
+    } while (0)
+
+// assembly (gs_assemble.cu)
+int gs_build_geometry(gs_ctx *c);
+int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda);
+int gs_assemble_f(gs_ctx *c, const AngleData &a, cplx *f);
+int gs_angle_scalars(gs_ctx *c, AngleData &a);
+int gs_mie(gs_ctx *c);
+int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B);
+int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm);
+// factorisation (gs_svd.cu)
+int gs_factor_angle(gs_ctx *c, AngleData &a);
+// translation (gs_translate.cu)
+int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision);
+// low-rank, operator, GMRES, Bragg (gs_solve.cu)
+int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
+int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);
+int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b);
+int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0);
+int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux);

@@ -1,0 +1,356 @@
+// Schur-complement low-rank apply, preconditioned operator, right-hand side, GMRES and Bragg
+// recovery on the GPU (FP64; Sec. 4.2 preconditioner, Sec. 5 Eqs. applypA, schur and the
+// preconditioned system, Sec. 6 flux).
+//
+//   L x = x - S (T x) + S B_phys A^+ C x,   A^+ g = D V Sigma^+ U^* g   (never formed)
+// The low-rank term is four matrix-vector products (HBM-bound): g = C x (C rows only),
+// w = coef .* (W^* g), v = D .* (V w) restricted to the columns of B_phys, and z = B_phys v, whose
+// epilogue fuses the preconditioner and the combination y = x - s .* (T x) + s .* z.
+#include <algorithm>
+#include <vector>
+
+#include "gs_internal.h"
+
+size_t gs_translate_scratch_elems(int M, int p);
+
+namespace {
+
+// y[r] = scale[r] * sum_c A[r, c] x[c]   (A row-major, warp per row)
+__global__ void k_gemv_rows(const cplx *__restrict__ A, int nrows, int ncols, long lda,
+                            const cplx *__restrict__ x, const double *__restrict__ scale,
+                            cplx *__restrict__ y) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nrows) return;
+    const cplx *a = A + (size_t)warp * lda;
+    cplx s = C(0, 0);
+    for (int c = lane; c < ncols; c += 32) cfma(s, a[c], __ldg(&x[c]));
+    s.x = warp_sum(s.x);
+    s.y = warp_sum(s.y);
+    if (lane == 0) y[warp] = scale ? cscale(s, scale[warp]) : s;
+}
+
+// y[j] = coef[j] * sum_{i < nr} conj(W[i, j]) g[i]   (W column-major, warp per column)
+__global__ void k_gemv_colsH(const cplx *__restrict__ W, int m, int nr, int ncols, const cplx *__restrict__ g,
+                             const double *__restrict__ coef, cplx *__restrict__ y) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= ncols) return;
+    const cplx *a = W + (size_t)warp * m;
+    cplx s = C(0, 0);
+    for (int i = lane; i < nr; i += 32) cfma(s, cconj(a[i]), __ldg(&g[i]));
+    s.x = warp_sum(s.x);
+    s.y = warp_sum(s.y);
+    if (lane == 0) y[warp] = cscale(s, coef[warp]);
+}
+
+// y[r] = x[r] - s[r] * t[r] + s[r] * (B v)[r]   (B row-major n x nB, warp per row)
+__global__ void k_B_combine(const cplx *__restrict__ B, int n, int nB, const cplx *__restrict__ v,
+                            const cplx *__restrict__ x, const cplx *__restrict__ t,
+                            const cplx *__restrict__ s, cplx *__restrict__ y) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const cplx *b = B + (size_t)warp * nB;
+    cplx acc = C(0, 0);
+    for (int c = lane; c < nB; c += 32) cfma(acc, b[c], __ldg(&v[c]));
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    if (lane == 0) {
+        cplx r = x ? x[warp] : C(0, 0);
+        if (t) r = csub(r, cmul(s[warp], t[warp]));
+        r = cadd(r, cmul(s[warp], acc));
+        y[warp] = r;
+    }
+}
+
+// g[r] = f[r] - (C x)[r] for r < nC, and f[r] for nC <= r < rows
+__global__ void k_f_minus_Cx(const cplx *__restrict__ Cm, int nC, int n, const cplx *__restrict__ x,
+                             const cplx *__restrict__ f, int rows, cplx *__restrict__ g) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rows) return;
+    if (warp >= nC) {
+        if (lane == 0) g[warp] = f[warp];
+        return;
+    }
+    const cplx *a = Cm + (size_t)warp * n;
+    cplx s = C(0, 0);
+    for (int c = lane; c < n; c += 32) cfma(s, a[c], __ldg(&x[c]));
+    s.x = warp_sum(s.x);
+    s.y = warp_sum(s.y);
+    if (lane == 0) g[warp] = csub(f[warp], s);
+}
+
+// ---- GMRES helpers ------------------------------------------------------------------------------
+
+// h[i] (+)= V_i^* w for i < cnt (block per basis vector)
+__global__ void k_dots(const cplx *__restrict__ Vb, long n, const cplx *__restrict__ w, int cnt,
+                       cplx *__restrict__ h, int accumulate) {
+    int i = blockIdx.x;
+    if (i >= cnt) return;
+    __shared__ double sh[32];
+    const cplx *v = Vb + (size_t)i * n;
+    double re = 0, im = 0;
+    for (long e = threadIdx.x; e < n; e += blockDim.x) {
+        cplx a = v[e], b = w[e];
+        re += a.x * b.x + a.y * b.y;
+        im += a.x * b.y - a.y * b.x;
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) {
+        cplx r = C(re, im);
+        h[i] = accumulate ? cadd(h[i], r) : r;
+    }
+}
+
+// w -= sum_{i < cnt} coef[i] V_i
+__global__ void k_sub_combo(cplx *__restrict__ w, const cplx *__restrict__ Vb, long n,
+                            const cplx *__restrict__ coef, int cnt) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    cplx s = w[e];
+    for (int i = 0; i < cnt; ++i) s = csub(s, cmul(coef[i], Vb[(size_t)i * n + e]));
+    w[e] = s;
+}
+
+// x += sum_{i < cnt} y[i] V_i
+__global__ void k_add_combo(cplx *__restrict__ x, const cplx *__restrict__ Vb, long n,
+                            const cplx *__restrict__ y, int cnt) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    cplx s = x[e];
+    for (int i = 0; i < cnt; ++i) s = cadd(s, cmul(y[i], Vb[(size_t)i * n + e]));
+    x[e] = s;
+}
+
+// out[0] = ||w||_2 (single block)
+__global__ void k_norm(const cplx *__restrict__ w, long n, double *out) {
+    __shared__ double sh[32];
+    double s = 0;
+    for (long e = threadIdx.x; e < n; e += blockDim.x) s += cabs2(w[e]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
+// dst = src * (1 / norm[0]); also records norm into Hsub (complex) if given
+__global__ void k_scale_by_inv(const cplx *src, long n, const double *norm, cplx *dst,
+                               cplx *Hsub) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double nv = norm[0];
+    if (e == 0 && Hsub) *Hsub = C(nv, 0.0);
+    if (e >= n) return;
+    dst[e] = nv > 0.0 ? cscale(src[e], 1.0 / nv) : C(0, 0);
+}
+
+__global__ void k_add_vec(cplx *h, const cplx *v, int cnt) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) h[i] = cadd(h[i], v[i]);
+}
+
+__global__ void k_sub(const cplx *a, const cplx *b, long n, cplx *y) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) y[e] = csub(a[e], b[e]);
+}
+
+// Givens step for Hessenberg column j (column-major, leading dimension ld): applies the previous
+// rotations, forms the new one, updates g and writes the residual estimate |g[j+1]| to res.
+__global__ void k_givens(cplx *H, int ld, int j, cplx *cs, cplx *sn, cplx *g, double *res) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    cplx *h = H + (size_t)j * ld;
+    for (int i = 0; i < j; ++i) {
+        cplx t = cadd(cmul(cs[i], h[i]), cmul(sn[i], h[i + 1]));
+        h[i + 1] = cadd(cmul(cscale(cconj(sn[i]), -1.0), h[i]), cmul(cs[i], h[i + 1]));
+        h[i] = t;
+    }
+    cplx a = h[j], b = h[j + 1];
+    double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
+    double rr = hypot(aa, bb);
+    cplx c, s;
+    if (rr == 0.0) {
+        c = C(1, 0);
+        s = C(0, 0);
+    } else if (aa == 0.0) {
+        c = C(0, 0);
+        s = cscale(cconj(b), 1.0 / bb);
+    } else {
+        c = C(aa / rr, 0.0);
+        s = cmul(cscale(a, 1.0 / aa), cscale(cconj(b), 1.0 / rr));
+    }
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = cadd(cmul(c, a), cmul(s, b));
+    h[j + 1] = C(0, 0);
+    cplx gj = g[j];
+    g[j + 1] = cmul(cscale(cconj(s), -1.0), gj);
+    g[j] = cmul(c, gj);
+    res[0] = sqrt(cabs2(g[j + 1]));
+}
+
+// back substitution H[0:k,0:k] y = g[0:k] (upper triangular, single thread)
+__global__ void k_backsolve(const cplx *H, int ld, int kk, const cplx *g, cplx *y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = kk - 1; i >= 0; --i) {
+        cplx s = g[i];
+        for (int c = i + 1; c < kk; ++c) s = csub(s, cmul(H[(size_t)c * ld + i], y[c]));
+        y[i] = cdiv(s, H[(size_t)i * ld + i]);
+    }
+}
+
+__global__ void k_set_g0(cplx *g, int len, const double *beta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) g[i] = C(i == 0 ? beta[0] : 0.0, 0.0);
+}
+
+// Bragg amplitudes and flux error (single block): c_n = x_c[n], d_n = x_d[n] for propagating orders.
+__global__ void k_flux(int K, const cplx *cd, const cplx *k1n, const cplx *k3n, double inc, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int n = 0; n < 2 * K + 1; ++n) {
+        if (k1n[n].y == 0.0 && k1n[n].x > 0.0) s += k1n[n].x * cabs2(cd[n]);
+        if (k3n[n].y == 0.0 && k3n[n].x > 0.0) s += k3n[n].x * cabs2(cd[2 * K + 1 + n]);
+    }
+    out[0] = fabs(s - inc) / inc;
+}
+
+inline int warps_blocks(long nwarps) { return (int)((nwarps * 32 + 255) / 256); }
+
+}  // namespace
+
+// x = A^+ g (full): w = coef .* W^* g; x = D .* V w
+int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x) {
+    const Layout &ly = c->lay;
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.rows, ly.cols, g, a.coef, c->w);
+    k_gemv_rows<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.Vr, ly.cols, ly.cols, ly.cols, c->w, a.dscale, x);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// y = x - s .* T x + s .* (B_phys A^+ C x)
+int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision) {
+    const Layout &ly = c->lay;
+    int n = c->n(), nB = ly.nB(), nC = ly.nC();
+    cplx *tx = c->v3;
+    GS_TRY(gs_translate_impl(c, a, x, tx, precision));
+    k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, x, tx, c->s, y);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// b = s .* (B_phys A^+ f); f vanishes outside the Gamma1 rows
+int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
+    const Layout &ly = c->lay;
+    int n = c->n(), nB = ly.nB();
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.row_g2v, ly.cols, a.f, a.coef, c->w);
+    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, nullptr, nullptr, c->s, b);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// Restarted GMRES (Saad-Schultz) with classical Gram-Schmidt applied twice, Givens rotations on
+// the device; the host reads one residual estimate per iteration.
+int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0) {
+    const long n = c->n();
+    cudaStream_t st = c->stream;
+    const int kd = std::min(o.restart, c->kdim);
+    const int ld = c->kdim + 1;
+    const int eb = (int)((n + 255) / 256);
+    cplx *b = c->v1, *r = c->v2;
+    cplx *x = a.beta;
+    double *ds = c->dscal;   // [0] = ||b||, [1] = ||r||, [2] = residual estimate, [3] = scratch
+    GS_TRY(gs_rhs_impl(c, a, b));
+    k_norm<<<1, 1024, 0, st>>>(b, n, ds);
+    if (x0) {
+        GS_CUDA(c, cudaMemcpyAsync(x, x0, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+    }
+    GS_CUDA(c, cudaMemcpyAsync(c->hscal, ds, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    const double bnorm = c->hscal[0];
+    a.iters = 0;
+    a.relres = 0.0;
+    if (bnorm == 0.0) {
+        GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+        return GS_OK;
+    }
+    int it = 0;
+    bool first = (x0 == nullptr);
+    double est = 1.0;
+    while (it < o.maxit) {
+        // r = b - L x
+        if (first) {
+            GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+        }
+        first = false;
+        k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
+        GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(c, cudaStreamSynchronize(st));
+        est = c->hscal[1] / bnorm;
+        if (est <= o.tol) break;
+        k_scale_by_inv<<<eb, 256, 0, st>>>(r, n, ds + 1, c->Vk, nullptr);
+        k_set_g0<<<(ld + 255) / 256, 256, 0, st>>>(c->gg, ld, ds + 1);
+        GS_CUDA(c, cudaMemsetAsync(c->Hh, 0, sizeof(cplx) * (size_t)ld * c->kdim, st));
+        int j = 0, kk = 0;
+        for (; j < kd && it < o.maxit; ++j) {
+            cplx *vj = c->Vk + (size_t)j * n;
+            cplx *w = c->Vk + (size_t)(j + 1) * n;
+            GS_TRY(gs_apply_impl(c, a, vj, w, GS_FP64));
+            ++it;
+            cplx *h = c->Hh + (size_t)j * ld;
+            // CGS2
+            k_dots<<<j + 1, 256, 0, st>>>(c->Vk, n, w, j + 1, h, 0);
+            k_sub_combo<<<eb, 256, 0, st>>>(w, c->Vk, n, h, j + 1);
+            k_dots<<<j + 1, 256, 0, st>>>(c->Vk, n, w, j + 1, c->yy, 0);
+            k_sub_combo<<<eb, 256, 0, st>>>(w, c->Vk, n, c->yy, j + 1);
+            k_add_vec<<<1, 256, 0, st>>>(h, c->yy, j + 1);   // h += second-pass coefficients
+            k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
+            k_scale_by_inv<<<eb, 256, 0, st>>>(w, n, ds + 3, w, h + j + 1);
+            k_givens<<<1, 1, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
+            GS_CHECK_LAUNCH(c);
+            GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            est = c->hscal[2] / bnorm;
+            kk = j + 1;
+            if (est <= o.tol) break;
+        }
+        k_backsolve<<<1, 1, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
+        k_add_combo<<<eb, 256, 0, st>>>(x, c->Vk, n, c->yy, kk);
+        GS_CHECK_LAUNCH(c);
+        if (est <= o.tol) {
+            // confirm with the true residual
+            GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+            k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
+            GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            est = c->hscal[1] / bnorm;
+            if (est <= 10.0 * o.tol) break;
+            first = false;
+        }
+    }
+    a.iters = it;
+    a.relres = est;
+    return est <= 10.0 * o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
+}
+
+// Bragg amplitudes: x_cd = D_cd .* V[cd rows] (coef .* W^* (f - C beta)); flux error on the device.
+int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux) {
+    const Layout &ly = c->lay;
+    int n = c->n();
+    int ncd = 2 * (2 * ly.K + 1);
+    k_f_minus_Cx<<<warps_blocks(ly.rows), 256, 0, c->stream>>>(a.Cm, ly.nC(), n, a.beta, a.f, ly.rows, c->g);
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.rows, ly.cols, c->g, a.coef, c->w);
+    k_gemv_rows<<<warps_blocks(ncd), 256, 0, c->stream>>>(a.Vr + (size_t)ly.col_c * ly.cols, ncd, ly.cols, ly.cols,
+                                                          c->w, a.dscale + ly.col_c, c->x);
+    double inc = c->L.k1 * fabs(sin(a.theta));
+    k_flux<<<1, 1, 0, c->stream>>>(ly.K, c->x, a.k1n, a.k3n, inc, c->dscal + 4);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(cd_host, c->x, sizeof(cplx) * ncd, cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(flux, c->dscal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}

@@ -1,0 +1,172 @@
+// All-pairs Graf translation (M2L) between the inclusions, with the +-d images (Sec. 4.2 Eq. trans,
+// Sec. 5 Eq. repre3_mod):
+//   alpha_i[m] = sum_{(j,l) != (i,0)} alpha^l sum_n H_{n-m}(k R) e^{i(n-m) Th} beta_j[n],
+//   (R, Th) = polar(c_i - c_j - l d).
+//
+// Kernel design (FP64): one warp per target particle, its 32 lanes over 32 source images at a
+// time.  A thread block of WARPS targets shares each tile of 32 source images, staged in shared
+// memory with the image phase alpha^l already folded into the coefficients (layout [n][lane], so
+// lane-indexed reads are conflict-free).  Each lane seeds H_0, H_1 once per pair from the CUDA
+// Bessel functions, recurs upward in the order (H_{q+1} = (2q/z) H_q - H_{q-1}) in registers,
+// forms H_q u^q and (-1)^q H_q conj(u)^q with u = e^{i Th}, and applies the (2p+1)x(2p+1)
+// Toeplitz block to the staged coefficients with the 2p+1 accumulators held in registers (fully
+// unrolled for the compile-time order P).  Warp-shuffle reductions combine the lanes.  The source
+// images are split into `nsplit` chunks across blockIdx.y to fill the 152 SMs; a second kernel
+// sums the chunk partials in a fixed order (deterministic).
+#include "gs_internal.h"
+
+namespace {
+
+constexpr int TILE = 32;
+
+template <int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_translate_f64(const double *__restrict__ xy, int M, const cplx *__restrict__ beta, double k, double d,
+                cplx alpha, int nsplit, cplx *__restrict__ out) {
+    constexpr int NC = 2 * P + 1;
+    __shared__ cplx sb[NC][TILE];
+    __shared__ double sx[TILE], sy[TILE];
+    __shared__ int sid[TILE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WARPS + warp;
+    const long total = 3L * M;
+    const long s0 = total * blockIdx.y / nsplit, s1 = total * (blockIdx.y + 1) / nsplit;
+    double xi = 0.0, yi = 0.0;
+    if (i < M) {
+        xi = xy[2 * i];
+        yi = xy[2 * i + 1];
+    }
+    cplx acc[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) acc[m] = C(0.0, 0.0);
+    const cplx ainv = cconj(alpha);
+
+    for (long t0 = s0; t0 < s1; t0 += TILE) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TILE * NC; e += WARPS * 32) {
+            int u = e / NC, n = e - u * NC;
+            long s = t0 + u;
+            cplx v = C(0.0, 0.0);
+            if (s < s1) {
+                int l = (int)(s / M) - 1;
+                int j = (int)(s - (long)(l + 1) * M);
+                cplx b = beta[(size_t)j * NC + n];
+                v = (l == 0) ? b : cmul(l == 1 ? alpha : ainv, b);
+            }
+            sb[n][u] = v;
+        }
+        for (int u = threadIdx.x; u < TILE; u += WARPS * 32) {
+            long s = t0 + u;
+            if (s < s1) {
+                int l = (int)(s / M) - 1;
+                int j = (int)(s - (long)(l + 1) * M);
+                sx[u] = xy[2 * j] + l * d;
+                sy[u] = xy[2 * j + 1];
+                sid[u] = (l == 0) ? j : -1;
+            } else {
+                sid[u] = -2;
+                sx[u] = 0.0;
+                sy[u] = 0.0;
+            }
+        }
+        __syncthreads();
+        if (i >= M) continue;
+        const long s = t0 + lane;
+        if (s >= s1 || sid[lane] == i) continue;
+        const double dx = xi - sx[lane], dy = yi - sy[lane];
+        const double R = hypot(dx, dy);
+        const double z = k * R;
+        const double twoz = 2.0 / z;
+        cplx Hm1, Hc;
+        hankel01(z, Hm1, Hc);   // H_0, H_1
+        const cplx u1 = C(dx / R, dy / R);
+        cplx up = u1;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) cfma(acc[m], Hm1, sb[m][lane]);
+#pragma unroll
+        for (int q = 1; q <= 2 * P; ++q) {
+            const cplx hq = cmul(Hc, up);
+            cplx hmq = cmul(Hc, cconj(up));
+            if (q & 1) hmq = C(-hmq.x, -hmq.y);
+#pragma unroll
+            for (int m = 0; m + q < NC; ++m) cfma(acc[m], hq, sb[m + q][lane]);
+#pragma unroll
+            for (int m = q; m < NC; ++m) cfma(acc[m], hmq, sb[m - q][lane]);
+            if (q < 2 * P) {
+                const cplx Hn = csub(cscale(Hc, q * twoz), Hm1);
+                Hm1 = Hc;
+                Hc = Hn;
+                up = cmul(up, u1);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        acc[m].x = warp_sum(acc[m].x);
+        acc[m].y = warp_sum(acc[m].y);
+    }
+    if (i < M) {
+        cplx *o = out + ((size_t)blockIdx.y * M + i) * NC;
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+            if (lane == (m & 31)) o[m] = acc[m];
+    }
+}
+
+__global__ void k_sum_partials(const cplx *part, int nsplit, long len, cplx *out) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    cplx s = part[e];
+    for (int c = 1; c < nsplit; ++c) s = cadd(s, part[(size_t)c * len + e]);
+    out[e] = s;
+}
+
+template <int P>
+int launch_f64(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
+    constexpr int WARPS = 4;
+    const int M = c->M;
+    const int gx = (M + WARPS - 1) / WARPS;
+    // enough blocks for several waves over the SMs
+    int nsplit = (int)((152L * 8 + gx - 1) / gx);
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 64) nsplit = 64;
+    if ((long)nsplit * 32 > 3L * M) nsplit = (int)((3L * M + 31) / 32);
+    if (nsplit < 1) nsplit = 1;
+    size_t need = (size_t)nsplit * M * (2 * P + 1);
+    cplx *dst = out;
+    if (nsplit > 1) {
+        if (need > c->part_elems) return gs_fail(c, GS_ERR_STATE, "translation scratch too small");
+        dst = c->part;
+    }
+    dim3 grid(gx, nsplit);
+    k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, beta, c->L.k2, c->L.d, a.alpha,
+                                                                  nsplit, dst);
+    if (nsplit > 1) {
+        long len = (long)M * (2 * P + 1);
+        k_sum_partials<<<(int)((len + 255) / 256), 256, 0, c->stream>>>(c->part, nsplit, len, out);
+    }
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+}  // namespace
+
+size_t gs_translate_scratch_elems(int M, int p) { return (size_t)64 * M * (2 * p + 1); }
+
+int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision) {
+    (void)precision;
+    switch (c->p) {
+        case 1: return launch_f64<1>(c, a, beta, out);
+        case 2: return launch_f64<2>(c, a, beta, out);
+        case 3: return launch_f64<3>(c, a, beta, out);
+        case 4: return launch_f64<4>(c, a, beta, out);
+        case 5: return launch_f64<5>(c, a, beta, out);
+        case 6: return launch_f64<6>(c, a, beta, out);
+        case 7: return launch_f64<7>(c, a, beta, out);
+        case 8: return launch_f64<8>(c, a, beta, out);
+        case 10: return launch_f64<10>(c, a, beta, out);
+        case 12: return launch_f64<12>(c, a, beta, out);
+        case 16: return launch_f64<16>(c, a, beta, out);
+        default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+}

@@ -1,0 +1,199 @@
+"""GPU parity: every step of the CUDA path (called through the C-ABI) against the oracle on the
+same seeded inputs.  Floating-point tolerances: assembled matrices agree to 1e-10 of each block's
+largest entry (two independent FP64 evaluations of the same formulas, with different Bessel
+implementations); the translation and the operator to 1e-12 relative (norm); Bragg amplitudes to
+the stated 1e-9 relative (the FP64 path's target)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import inclusions as I
+from oracle import layers as L
+from oracle import solver as S
+
+pytestmark = pytest.mark.gpu
+
+BRAGG_TOL = 1e-9
+
+
+def _solver():
+    from paper_1412_7466_gb300 import GratingSolver
+    return GratingSolver(0)
+
+
+def _setup_gpu(cfg_grating, theta, disks):
+    gs = _solver()
+    gs.set_layers(cfg_grating)
+    gs.set_incidence([theta])
+    gs.set_inclusions(disks)
+    gs.factor()
+    return gs
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = W.config("small")
+    prob = S.setup(cfg["grating"], cfg["theta"], cfg["disks"])
+    gs = _setup_gpu(cfg["grating"], cfg["theta"], cfg["disks"])
+    yield cfg, prob, gs
+    gs.close()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _blocks(eg):
+    return [(rn, rs, cn, cs) for rn, rs in eg.rows.items() for cn, cs in eg.cols.items()]
+
+
+def test_assembled_A_matches_oracle(small):
+    cfg, prob, gs = small
+    A = _np(gs.get_A())
+    Ao = prob.eg.A
+    assert A.shape == Ao.shape
+    for rn, rs, cn, cs in _blocks(prob.eg):
+        blk_o = Ao[rs, cs]
+        scale = np.max(np.abs(blk_o))
+        err = np.max(np.abs(A[rs, cs] - blk_o))
+        assert err <= 1e-10 * max(scale, 1e-300), (rn, cn, err, scale)
+
+
+def test_rhs_f_matches_oracle(small):
+    cfg, prob, gs = small
+    np.testing.assert_allclose(_np(gs.get_f()), prob.eg.f, atol=1e-13)
+
+
+def test_scattering_diagonal(small):
+    cfg, prob, gs = small
+    s = _np(gs.get_scattering())
+    np.testing.assert_allclose(s, prob.s, rtol=1e-11, atol=1e-300)
+
+
+def test_coupling_B_C(small):
+    cfg, prob, gs = small
+    B, Cm = gs.get_coupling()
+    B, Cm = _np(B), _np(Cm)
+    nB = B.shape[1]
+    Bo = prob.B[:, :nB]
+    assert np.all(prob.B[:, nB:] == 0)
+    for blk in ("mu1", "sigma1", "mu2", "sigma2", "a2"):
+        sl = prob.eg.cols[blk]
+        sc = np.max(np.abs(Bo[:, sl]))
+        assert np.max(np.abs(B[:, sl] - Bo[:, sl])) <= 1e-11 * sc, blk
+    nC = Cm.shape[0]
+    Co = prob.C[:nC]
+    assert np.all(prob.C[nC:] == 0)
+    sc = np.max(np.abs(Co))
+    assert np.max(np.abs(Cm - Co)) <= 1e-11 * sc
+
+
+def test_empty_grating_pseudo_inverse(small):
+    """A^+ f from the GPU Jacobi SVD gives the oracle's empty-grating Bragg amplitudes."""
+    cfg, prob, gs = small
+    x = _np(gs.pinv_apply(gs.get_f()))
+    xo = prob.pinv.apply(prob.eg.f)
+    for blk in ("c", "d"):
+        a, b = x[prob.eg.cols[blk]], xo[prob.eg.cols[blk]]
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+    res = np.linalg.norm(prob.eg.A @ x - prob.eg.f) / np.linalg.norm(prob.eg.f)
+    assert res < 1e-10
+
+
+def test_translate_matches_oracle(small):
+    cfg, prob, gs = small
+    rng = np.random.default_rng(0)
+    n = prob.M * prob.nc
+    beta = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    got = _np(gs.translate(beta))
+    ref = prob.translate(beta)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_operator_and_rhs_match_oracle(small):
+    cfg, prob, gs = small
+    rng = np.random.default_rng(1)
+    n = prob.M * prob.nc
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.tile(0.3 ** np.abs(np.arange(-prob.disks["p"], prob.disks["p"] + 1)), prob.M)
+    got = _np(gs.apply(x))
+    ref = prob.apply(x)
+    assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+    b = _np(gs.rhs())
+    bo = prob.rhs()
+    assert np.linalg.norm(b - bo) <= 1e-10 * np.linalg.norm(bo)
+
+
+def test_solve_small_bragg(small):
+    cfg, prob, gs = small
+    gs.solve(tol=cfg["tol"], maxit=500)
+    its, rr = gs.stats()
+    assert rr <= 10 * cfg["tol"]
+    got = gs.bragg()
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, fe = prob.recover(beta)
+    assert np.array_equal(got["n_top"], ref["n_top"]) and np.array_equal(got["n_bot"], ref["n_bot"])
+    a = np.concatenate([got["c"], got["d"]])
+    b = np.concatenate([ref["c"], ref["d"]])
+    assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b)
+    assert got["flux_err"] < 1e-10
+    bg = _np(gs.get_beta())
+    assert np.linalg.norm(bg - beta) <= 1e-8 * np.linalg.norm(beta)
+
+
+@pytest.mark.parametrize("M,p", [(1, 3), (7, 5), (13, 8)])
+def test_translate_ragged_and_orders(M, p):
+    """Single disk (images only), ragged M (not a multiple of the warps per block), other orders."""
+    g = W.grating("tiny")
+    dk = W.disks(M, 0.02, 0.01, 2.0, g["k"][0], seed=100 + M, p=p)
+    gs = _setup_gpu(g, -0.9, dk)
+    rng = np.random.default_rng(M)
+    n = M * (2 * p + 1)
+    beta = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    alpha = np.exp(1j * g["k"][0] * math.cos(-0.9) * g["d"])
+    T = I.translation_matrix(dk["xy"], g["k"][1], p, g["d"], alpha)
+    ref = T @ beta
+    got = _np(gs.translate(beta))
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    gs.close()
+
+
+def test_wood_anomaly_solve():
+    """At the Wood angle of k1 the GPU path keeps matching the oracle and conserving flux."""
+    cfg = W.config("small")
+    g = cfg["grating"]
+    theta = W.wood_angle(g["k"][0], g["d"])
+    dk = cfg["disks"]
+    prob = S.setup(g, theta, dk)
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, _ = prob.recover(beta)
+    gs = _setup_gpu(g, theta, dk)
+    gs.solve(tol=1e-12, maxit=500)
+    got = gs.bragg()
+    a = np.concatenate([got["c"], got["d"]])
+    b = np.concatenate([ref["c"], ref["d"]])
+    assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b)
+    gs.close()
+
+
+def test_geometry_and_state_errors():
+    from paper_1412_7466_gb300 import GS_ERR_GEOMETRY, GS_ERR_STATE, GsError
+    g = W.grating("tiny")
+    gs = _solver()
+    gs.set_layers(g)
+    gs.set_incidence([-0.8])
+    bad = {"xy": np.array([[0.0, 0.0], [0.01, 0.0]]), "radius": np.array([0.01, 0.01]),
+           "kp": np.array([10.0, 10.0]), "p": 3}
+    with pytest.raises(GsError) as e:
+        gs.set_inclusions(bad)
+    assert e.value.status == GS_ERR_GEOMETRY
+    # overlap across the wall (minimum image)
+    bad["xy"] = np.array([[-0.499, 0.0], [0.4985, 0.0]])
+    with pytest.raises(GsError) as e:
+        gs.set_inclusions(bad)
+    assert e.value.status == GS_ERR_GEOMETRY
+    with pytest.raises(GsError) as e:
+        gs.solve()
+    assert e.value.status == GS_ERR_STATE
+    gs.close()
