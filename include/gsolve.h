@@ -146,6 +146,18 @@ int gs_stats(gs_ctx *ctx, int angle, int *iters, double *relres);
 int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
              int *n_bot, int *orders_bot, gs_c128 *d, double *flux_err);
 
+/* ---- instrumentation (not part of the method) ------------------------------------------------ */
+/* Kernel launches issued by this context since gs_create (all calls). */
+int gs_launch_count(gs_ctx *ctx, unsigned long long *count);
+/* enable != 0 starts CUDA-event timing of every launch of the translation kernel (the events are
+ * recorded on the context's stream around the launch); any call resets the accumulated record. */
+int gs_profile(gs_ctx *ctx, int enable);
+/* Number of timed translation launches and their summed device time in ms (synchronises). */
+int gs_profile_read(gs_ctx *ctx, int *launches, double *total_ms);
+/* Measures the FMA throughput of this GPU with independent multiply-add chains (precision GS_FP64
+ * or GS_C64 for FP32) over all SMs; writes the achieved TFLOP/s (2 flops per FMA). */
+int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

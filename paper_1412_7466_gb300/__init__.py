@@ -75,6 +75,10 @@ _SIGS = {
     "gs_get_beta": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "gs_stats": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
     "gs_bragg": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _vp, _ip, _ip, _vp, _dp]),
+    "gs_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "gs_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "gs_profile_read": (ctypes.c_int, [_vp, _ip, _dp]),
+    "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
 }
 
 _lib = None
@@ -267,6 +271,25 @@ class GratingSolver:
         it, rr = ctypes.c_int(), ctypes.c_double()
         self._check(self.lib.gs_stats(self.ctx, angle, ctypes.byref(it), ctypes.byref(rr)), "gs_stats")
         return it.value, rr.value
+
+    # -- instrumentation ------------------------------------------------------------------------
+    def launch_count(self):
+        v = ctypes.c_ulonglong()
+        self._check(self.lib.gs_launch_count(self.ctx, ctypes.byref(v)), "gs_launch_count")
+        return v.value
+
+    def profile(self, enable=True):
+        self._check(self.lib.gs_profile(self.ctx, int(bool(enable))), "gs_profile")
+
+    def profile_read(self):
+        n, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.gs_profile_read(self.ctx, ctypes.byref(n), ctypes.byref(ms)), "gs_profile_read")
+        return n.value, ms.value
+
+    def probe_fma(self, precision=GS_FP64):
+        v = ctypes.c_double()
+        self._check(self.lib.gs_probe_fma(self.ctx, precision, ctypes.byref(v)), "gs_probe_fma")
+        return v.value
 
     def bragg(self, angle=0):
         cap = 2 * self.grating["K_rb"] + 1

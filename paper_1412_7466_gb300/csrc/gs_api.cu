@@ -17,6 +17,22 @@ int gs_fail(gs_ctx *c, int code, const std::string &msg) {
     return code;
 }
 
+bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1) {
+    if (!c->prof_on) return false;
+    while (c->prof_ev.size() < c->prof_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        c->prof_ev.push_back(e);
+    }
+    *e0 = c->prof_ev[c->prof_used];
+    *e1 = c->prof_ev[c->prof_used + 1];
+    c->prof_used += 2;
+    return true;
+}
+
 namespace {
 
 template <typename T>
@@ -66,6 +82,11 @@ void free_factor(gs_ctx *c) {
     dfree(c->w);
     dfree(c->x);
     dfree(c->Vtmp);
+    dfree(c->Xtmp);
+    dfree(c->Vxtmp);
+    dfree(c->nrm2);
+    dfree(c->perm);
+    dfree(c->tau);
     dfree(c->part);
     c->part_elems = 0;
     dfree(c->Vk);
@@ -163,6 +184,7 @@ void gs_destroy(gs_ctx *c) {
     dfree(c->s);
     dfree(c->dscal);
     dfree(c->dcount);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->hscal) cudaFreeHost(c->hscal);
     delete c;
 }
@@ -346,7 +368,12 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->g, ly.rows));
     GS_TRY(dalloc(c, &c->w, ly.cols));
     GS_TRY(dalloc(c, &c->x, ly.cols));
-    GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.cols * ly.cols));
+    GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
+    GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
+    GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
+    GS_TRY(dalloc(c, &c->nrm2, ly.cols));
+    GS_TRY(dalloc(c, &c->perm, ly.cols));
+    GS_TRY(dalloc(c, &c->tau, ly.cols));
     c->part_elems = gs_translate_scratch_elems(c->M, c->p);
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     c->kdim = 200;
@@ -382,6 +409,8 @@ int gs_factor(gs_ctx *c) {
     }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     dfree(c->Vtmp);
+    dfree(c->Xtmp);
+    dfree(c->Vxtmp);
     c->factored = true;
     return GS_OK;
 }
@@ -533,6 +562,35 @@ int gs_bragg(gs_ctx *c, int angle, int *n_top, int *orders_top, gs_c128 *cc, int
     *n_bot = nbt;
     *flux_err = flux;
     return finite ? GS_OK : gs_fail(c, GS_ERR_NUMERIC, "non-finite Bragg amplitude");
+}
+
+int gs_launch_count(gs_ctx *c, unsigned long long *count) {
+    if (!c || !count) return GS_ERR_ARG;
+    *count = c->nlaunch;
+    return GS_OK;
+}
+
+int gs_profile(gs_ctx *c, int enable) {
+    CTX_GUARD(c);
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->prof_on = enable != 0;
+    c->prof_used = 0;
+    return GS_OK;
+}
+
+int gs_profile_read(gs_ctx *c, int *launches, double *total_ms) {
+    CTX_GUARD(c);
+    if (!launches || !total_ms) return gs_fail(c, GS_ERR_ARG, "null output");
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (size_t q = 0; q + 1 < c->prof_used; q += 2) {
+        float ms = 0.f;
+        GS_CUDA(c, cudaEventElapsedTime(&ms, c->prof_ev[q], c->prof_ev[q + 1]));
+        tot += ms;
+    }
+    *launches = (int)(c->prof_used / 2);
+    *total_ms = tot;
+    return GS_OK;
 }
 
 }  // extern "C"

@@ -441,14 +441,21 @@ int gs_build_geometry(gs_ctx *c) {
         for (int m = 0; m < nf; ++m) four[q * nfa + m] = c->four[q][m];
     GS_CUDA(c, cudaMemcpyAsync(c->four_dev, four.data(), sizeof(double) * four.size(),
                                cudaMemcpyHostToDevice, c->stream));
+    GS_COUNT_LAUNCH(c);
     k_curve_nodes<<<nblk(N), TPB, 0, c->stream>>>(N, L.d, L.h1_0, nf, c->four_dev, c->four_dev + nfa,
                                                    c->curve[0]);
+    GS_COUNT_LAUNCH(c);
     k_curve_nodes<<<nblk(N), TPB, 0, c->stream>>>(N, L.d, L.h2_0, nf, c->four_dev + 2 * nfa,
                                                    c->four_dev + 3 * nfa, c->curve[1]);
+    GS_COUNT_LAUNCH(c);
     k_gauss_legendre<<<nblk(ly.nw1), TPB, 0, c->stream>>>(ly.nw1, c->yL1, L.y0, c->wall_y[0]);
+    GS_COUNT_LAUNCH(c);
     k_gauss_legendre<<<nblk(ly.nw2), TPB, 0, c->stream>>>(ly.nw2, c->yL2, c->yL1, c->wall_y[1]);
+    GS_COUNT_LAUNCH(c);
     k_gauss_legendre<<<nblk(ly.nw3), TPB, 0, c->stream>>>(ly.nw3, -L.y0, c->yL2, c->wall_y[2]);
+    GS_COUNT_LAUNCH(c);
     k_linspace_mid<<<nblk(ly.nb), TPB, 0, c->stream>>>(ly.nb, -0.5 * L.d, 0.5 * L.d, c->bound_x);
+    GS_COUNT_LAUNCH(c);
     k_kress<<<nblk(N), TPB, 0, c->stream>>>(N, c->kress);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -458,6 +465,7 @@ int gs_angle_scalars(gs_ctx *c, AngleData &a) {
     a.kappa0 = c->L.k1 * cos(a.theta);
     a.alpha = C(cos(a.kappa0 * c->L.d), sin(a.kappa0 * c->L.d));
     int K = c->lay.K;
+    GS_COUNT_LAUNCH(c);
     k_angle_scalars<<<nblk(2 * K + 1), TPB, 0, c->stream>>>(K, c->L.k1, c->L.k3, a.kappa0, c->L.d,
                                                             a.kappa, a.k1n, a.k3n);
     GS_CHECK_LAUNCH(c);
@@ -510,24 +518,32 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
     double x1c = 0.0, y1c = 0.5 * (L.h1_0 + L.y0), y2c = 0.5 * (L.h1_0 + L.h2_0), y3c = 0.5 * (L.h2_0 - L.y0);
 
     // Gamma1 rows: u1 - u2 = -u_inc (Eq. bound1)
+    GS_COUNT_LAUNCH(c);
     k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c1, al, L.k1, L.k2, c->kress, A, lda,
                                                    ly.row_g1v, ly.row_g1n, ly.col_mu1, ly.col_sig1);
     Targets t1 = curve_targets(c1, N), t2 = curve_targets(c2, N);
+    GS_COUNT_LAUNCH(c);
     k_potentials<<<nblk((long)N * N), TPB, 0, st>>>(t1, c2, N, L.k2, 3, -d, 0.0, d, ai, one, al, -1.0,
                                                      A, lda, ly.row_g1v, ly.row_g1n, ly.col_mu2,
                                                      ly.col_sig2);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t1, x1c, y2c, L.k2, ly.Q2, C(-1, 0), A, lda,
                                                             ly.row_g1v, ly.row_g1n, ly.col_a2);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)N * (2 * ly.Q1 + 1)), TPB, 0, st>>>(t1, x1c, y1c, L.k1, ly.Q1, one, A, lda,
                                                             ly.row_g1v, ly.row_g1n, ly.col_a1);
     // Gamma2 rows: u2 - u3 = 0
+    GS_COUNT_LAUNCH(c);
     k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c2, al, L.k2, L.k3, c->kress, A, lda,
                                                    ly.row_g2v, ly.row_g2n, ly.col_mu2, ly.col_sig2);
+    GS_COUNT_LAUNCH(c);
     k_potentials<<<nblk((long)N * N), TPB, 0, st>>>(t2, c1, N, L.k2, 3, -d, 0.0, d, ai, one, al, 1.0, A,
                                                      lda, ly.row_g2v, ly.row_g2n, ly.col_mu1,
                                                      ly.col_sig1);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t2, x1c, y2c, L.k2, ly.Q2, one, A, lda,
                                                             ly.row_g2v, ly.row_g2n, ly.col_a2);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)N * (2 * ly.Q3 + 1)), TPB, 0, st>>>(t2, x1c, y3c, L.k3, ly.Q3, C(-1, 0), A, lda,
                                                             ly.row_g2v, ly.row_g2n, ly.col_a3);
     // walls (Eq. bound2, cancelled form for the layer potentials)
@@ -545,33 +561,45 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
         const WallJob &w = wj[q];
         Targets TL = wall_targets(w.ys, w.nw, -0.5 * d), TR = wall_targets(w.ys, w.nw, 0.5 * d);
         bool has1 = (q == 0 || q == 1), has2 = (q == 0 || q == 2);
-        if (has1)
+        if (has1) {
+            GS_COUNT_LAUNCH(c);
             k_potentials<<<nblk((long)w.nw * N), TPB, 0, st>>>(TL, c1, N, w.k, 2, d, -2.0 * d, 0.0, al2,
                                                                 mai, one, 1.0, A, lda, w.rv, w.rn,
                                                                 ly.col_mu1, ly.col_sig1);
-        if (has2)
+        }
+        if (has2) {
+            GS_COUNT_LAUNCH(c);
             k_potentials<<<nblk((long)w.nw * N), TPB, 0, st>>>(TL, c2, N, w.k, 2, d, -2.0 * d, 0.0, al2,
                                                                 mai, one, 1.0, A, lda, w.rv, w.rn,
                                                                 ly.col_mu2, ly.col_sig2);
+        }
+        GS_COUNT_LAUNCH(c);
         k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TL, x1c, w.cy, w.k, w.Q, al, A, lda, w.rv,
                                                                  w.rn, w.col);
+        GS_COUNT_LAUNCH(c);
         k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TR, x1c, w.cy, w.k, w.Q, C(-1, 0), A,
                                                                  lda, w.rv, w.rn, w.col);
     }
     // Gamma_u / Gamma_d (Eq. bound3)
     Targets tu = bound_targets(c->bound_x, ly.nb, L.y0), td = bound_targets(c->bound_x, ly.nb, -L.y0);
+    GS_COUNT_LAUNCH(c);
     k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(tu, c1, N, L.k1, 3, -d, 0.0, d, ai, one, al, 1.0,
                                                          A, lda, ly.row_uv, ly.row_un, ly.col_mu1,
                                                          ly.col_sig1);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)ly.nb * (2 * ly.Q1 + 1)), TPB, 0, st>>>(tu, x1c, y1c, L.k1, ly.Q1, one, A, lda,
                                                                 ly.row_uv, ly.row_un, ly.col_a1);
+    GS_COUNT_LAUNCH(c);
     k_rb<<<nblk(ly.nb * (2 * ly.K + 1)), TPB, 0, st>>>(ly.nb, c->bound_x, ly.K, a.kappa, a.k1n, 1, A, lda,
                                                       ly.row_uv, ly.row_un, ly.col_c);
+    GS_COUNT_LAUNCH(c);
     k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(td, c2, N, L.k3, 3, -d, 0.0, d, ai, one, al, 1.0,
                                                          A, lda, ly.row_dv, ly.row_dn, ly.col_mu2,
                                                          ly.col_sig2);
+    GS_COUNT_LAUNCH(c);
     k_jexp<<<nblk((long)ly.nb * (2 * ly.Q3 + 1)), TPB, 0, st>>>(td, x1c, y3c, L.k3, ly.Q3, one, A, lda,
                                                                 ly.row_dv, ly.row_dn, ly.col_a3);
+    GS_COUNT_LAUNCH(c);
     k_rb<<<nblk(ly.nb * (2 * ly.K + 1)), TPB, 0, st>>>(ly.nb, c->bound_x, ly.K, a.kappa, a.k3n, 0, A, lda,
                                                       ly.row_dv, ly.row_dn, ly.col_d);
     GS_CHECK_LAUNCH(c);
@@ -582,6 +610,7 @@ int gs_assemble_f(gs_ctx *c, const AngleData &a, cplx *f) {
     const Layout &ly = c->lay;
     GS_CUDA(c, cudaMemsetAsync(f, 0, sizeof(cplx) * ly.rows, c->stream));
     Curve c1 = curve_of(c->curve[0], c->L.N);
+    GS_COUNT_LAUNCH(c);
     k_rhs<<<nblk(c->L.N), TPB, 0, c->stream>>>(c->L.N, c1, a.kappa0, c->L.k1 * sin(a.theta), f, ly.row_g1v,
                                                 ly.row_g1n);
     GS_CHECK_LAUNCH(c);
@@ -589,6 +618,7 @@ int gs_assemble_f(gs_ctx *c, const AngleData &a, cplx *f) {
 }
 
 int gs_mie(gs_ctx *c) {
+    GS_COUNT_LAUNCH(c);
     k_mie<<<nblk(c->M * c->nc), TPB, 0, c->stream>>>(c->M, c->p, c->radius, c->kp, c->L.k2, c->s);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -598,10 +628,13 @@ int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B) {
     const Layout &ly = c->lay;
     int N = c->L.N, nB = ly.nB();
     Curve c1 = curve_of(c->curve[0], N), c2 = curve_of(c->curve[1], N);
+    GS_COUNT_LAUNCH(c);
     k_B_layer<<<nblk((long)c->M * N, 128), 128, 0, c->stream>>>(c->M, c->p, c->xy, c1, N, c->L.k2, c->L.d,
                                                                a.alpha, B, nB, ly.col_mu1, ly.col_sig1);
+    GS_COUNT_LAUNCH(c);
     k_B_layer<<<nblk((long)c->M * N, 128), 128, 0, c->stream>>>(c->M, c->p, c->xy, c2, N, c->L.k2, c->L.d,
                                                                a.alpha, B, nB, ly.col_mu2, ly.col_sig2);
+    GS_COUNT_LAUNCH(c);
     k_B_a2<<<nblk((long)c->M * (2 * ly.Q2 + 1), 128), 128, 0, c->stream>>>(
         c->M, c->p, c->xy, 0.0, 0.5 * (c->L.h1_0 + c->L.h2_0), c->L.k2, ly.Q2, B, nB, ly.col_a2);
     GS_CHECK_LAUNCH(c);
@@ -617,10 +650,13 @@ int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm) {
     cplx al = a.alpha, ai = cconj(a.alpha), one = C(1, 0);
     Targets t1 = curve_targets(c1, N), t2 = curve_targets(c2, N);
     Targets tw = wall_targets(c->wall_y[1], ly.nw2, -0.5 * d);
+    GS_COUNT_LAUNCH(c);
     k_C<<<nblk((long)N * c->M, 128), 128, 0, c->stream>>>(t1, c->M, c->p, c->xy, c->L.k2, 3, -d, 0.0, d, ai,
                                                          one, al, -1.0, Cm, n, ly.row_g1v, ly.row_g1n);
+    GS_COUNT_LAUNCH(c);
     k_C<<<nblk((long)N * c->M, 128), 128, 0, c->stream>>>(t2, c->M, c->p, c->xy, c->L.k2, 3, -d, 0.0, d, ai,
                                                          one, al, 1.0, Cm, n, ly.row_g2v, ly.row_g2n);
+    GS_COUNT_LAUNCH(c);
     k_C<<<nblk((long)ly.nw2 * c->M, 128), 128, 0, c->stream>>>(tw, c->M, c->p, c->xy, c->L.k2, 2, d,
                                                               -2.0 * d, 0.0, cmul(al, al),
                                                               cscale(ai, -1.0), one, 1.0, Cm, n,

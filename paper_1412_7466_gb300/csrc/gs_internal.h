@@ -27,8 +27,8 @@ struct AngleData {
     cplx *k1n = nullptr;         // 2K+1, k_{1,n}
     cplx *k3n = nullptr;         // 2K+1, k_{3,n}
     cplx *f = nullptr;           // rows
-    cplx *W = nullptr;           // rows x cols column-major: A D V = U Sigma after Jacobi
-    cplx *Vr = nullptr;          // cols x cols row-major V
+    cplx *W = nullptr;           // rows x cols column-major U (orthonormal left singular vectors)
+    cplx *Vr = nullptr;          // cols x cols row-major V Sigma (= P W_x)
     double *dscale = nullptr;    // cols, column scaling D
     double *coef = nullptr;      // cols, 1/(sigma max(sigma, eps)) (0 for sigma = 0)
     double *sigma = nullptr;     // cols
@@ -74,7 +74,11 @@ struct gs_ctx {
     cplx *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;   // n each
     cplx *g = nullptr;                                  // rows
     cplx *w = nullptr, *x = nullptr;                     // cols
-    cplx *Vtmp = nullptr;                                // cols x cols, Jacobi rotations
+    cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
+    cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
+    double *nrm2 = nullptr;                              // cols, trailing column norms
+    int *perm = nullptr;                                 // cols, column pivots
+    cplx *tau = nullptr;                                 // cols, reflector scalars
     cplx *part = nullptr;                                // translation partials
     size_t part_elems = 0;
     // GMRES workspace
@@ -86,8 +90,18 @@ struct gs_ctx {
     double *hscal = nullptr;                             // pinned host scalars
     unsigned long long *dcount = nullptr;
 
+    // instrumentation: kernel launches issued, optional event timing of the translation kernel
+    unsigned long long nlaunch = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;   // start/stop pairs, reused
+    size_t prof_used = 0;               // events used since the last reset
+
     int n() const { return M * nc; }
 };
+
+#define GS_COUNT_LAUNCH(ctx) ((ctx)->nlaunch++)
+// returns a (start, stop) event pair for timing one launch, or false when profiling is off
+bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1);
 
 // error helpers (defined in gs_api.cu)
 int gs_fail(gs_ctx *c, int code, const std::string &msg);

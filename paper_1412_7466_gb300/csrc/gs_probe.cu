@@ -1,0 +1,57 @@
+// FMA-throughput probe: the denominator of the ALU roofline of the translation kernels.  Each
+// thread runs 8 independent multiply-add chains so that the FMA pipe, not latency, is the limit.
+#include "gs_internal.h"
+
+namespace {
+
+template <typename T>
+__global__ void k_fma_chains(T *out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = x[i] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+int run(gs_ctx *c, int iters, double *tflops) {
+    int dev = c->device, sms = 0;
+    GS_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    T *buf = nullptr;
+    GS_CUDA(c, cudaMalloc((void **)&buf, sizeof(T) * blocks * threads));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    GS_COUNT_LAUNCH(c);
+    k_fma_chains<T><<<blocks, threads, 0, c->stream>>>(buf, iters, (T)0.999999, (T)1e-7);   // warm-up
+    cudaEventRecord(e0, c->stream);
+    GS_COUNT_LAUNCH(c);
+    k_fma_chains<T><<<blocks, threads, 0, c->stream>>>(buf, iters, (T)0.999999, (T)1e-7);
+    cudaEventRecord(e1, c->stream);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (err != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, cudaGetErrorString(err));
+    *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3) / 1e12;
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" int gs_probe_fma(gs_ctx *c, int precision, double *tflops) {
+    if (!c || !tflops) return GS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, "cudaSetDevice");
+    if (precision == GS_FP64) return run<double>(c, 20000, tflops);
+    if (precision == GS_C64) return run<float>(c, 400000, tflops);
+    return gs_fail(c, GS_ERR_ARG, "bad precision");
+}

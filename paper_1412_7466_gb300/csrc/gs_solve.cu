@@ -216,7 +216,9 @@ inline int warps_blocks(long nwarps) { return (int)((nwarps * 32 + 255) / 256); 
 // x = A^+ g (full): w = coef .* W^* g; x = D .* V w
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x) {
     const Layout &ly = c->lay;
+    GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.rows, ly.cols, g, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.Vr, ly.cols, ly.cols, ly.cols, c->w, a.dscale, x);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -228,9 +230,13 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
     int n = c->n(), nB = ly.nB(), nC = ly.nC();
     cplx *tx = c->v3;
     GS_TRY(gs_translate_impl(c, a, x, tx, precision));
+    GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+    GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    GS_COUNT_LAUNCH(c);
     k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, x, tx, c->s, y);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -240,8 +246,11 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
 int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
     const Layout &ly = c->lay;
     int n = c->n(), nB = ly.nB();
+    GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.row_g2v, ly.cols, a.f, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    GS_COUNT_LAUNCH(c);
     k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, nullptr, nullptr, c->s, b);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -259,6 +268,7 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
     cplx *x = a.beta;
     double *ds = c->dscal;   // [0] = ||b||, [1] = ||r||, [2] = residual estimate, [3] = scratch
     GS_TRY(gs_rhs_impl(c, a, b));
+    GS_COUNT_LAUNCH(c);
     k_norm<<<1, 1024, 0, st>>>(b, n, ds);
     if (x0) {
         GS_CUDA(c, cudaMemcpyAsync(x, x0, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
@@ -283,15 +293,19 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
             GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
         } else {
             GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            GS_COUNT_LAUNCH(c);
             k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
         }
         first = false;
+        GS_COUNT_LAUNCH(c);
         k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
         GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
         GS_CUDA(c, cudaStreamSynchronize(st));
         est = c->hscal[1] / bnorm;
         if (est <= o.tol) break;
+        GS_COUNT_LAUNCH(c);
         k_scale_by_inv<<<eb, 256, 0, st>>>(r, n, ds + 1, c->Vk, nullptr);
+        GS_COUNT_LAUNCH(c);
         k_set_g0<<<(ld + 255) / 256, 256, 0, st>>>(c->gg, ld, ds + 1);
         GS_CUDA(c, cudaMemsetAsync(c->Hh, 0, sizeof(cplx) * (size_t)ld * c->kdim, st));
         int j = 0, kk = 0;
@@ -302,13 +316,21 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
             ++it;
             cplx *h = c->Hh + (size_t)j * ld;
             // CGS2
+            GS_COUNT_LAUNCH(c);
             k_dots<<<j + 1, 256, 0, st>>>(c->Vk, n, w, j + 1, h, 0);
+            GS_COUNT_LAUNCH(c);
             k_sub_combo<<<eb, 256, 0, st>>>(w, c->Vk, n, h, j + 1);
+            GS_COUNT_LAUNCH(c);
             k_dots<<<j + 1, 256, 0, st>>>(c->Vk, n, w, j + 1, c->yy, 0);
+            GS_COUNT_LAUNCH(c);
             k_sub_combo<<<eb, 256, 0, st>>>(w, c->Vk, n, c->yy, j + 1);
+            GS_COUNT_LAUNCH(c);
             k_add_vec<<<1, 256, 0, st>>>(h, c->yy, j + 1);   // h += second-pass coefficients
+            GS_COUNT_LAUNCH(c);
             k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
+            GS_COUNT_LAUNCH(c);
             k_scale_by_inv<<<eb, 256, 0, st>>>(w, n, ds + 3, w, h + j + 1);
+            GS_COUNT_LAUNCH(c);
             k_givens<<<1, 1, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
             GS_CHECK_LAUNCH(c);
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -317,13 +339,17 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
             kk = j + 1;
             if (est <= o.tol) break;
         }
+        GS_COUNT_LAUNCH(c);
         k_backsolve<<<1, 1, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
+        GS_COUNT_LAUNCH(c);
         k_add_combo<<<eb, 256, 0, st>>>(x, c->Vk, n, c->yy, kk);
         GS_CHECK_LAUNCH(c);
         if (est <= o.tol) {
             // confirm with the true residual
             GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            GS_COUNT_LAUNCH(c);
             k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+            GS_COUNT_LAUNCH(c);
             k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
@@ -342,11 +368,15 @@ int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux) {
     const Layout &ly = c->lay;
     int n = c->n();
     int ncd = 2 * (2 * ly.K + 1);
+    GS_COUNT_LAUNCH(c);
     k_f_minus_Cx<<<warps_blocks(ly.rows), 256, 0, c->stream>>>(a.Cm, ly.nC(), n, a.beta, a.f, ly.rows, c->g);
+    GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, ly.rows, ly.cols, c->g, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(ncd), 256, 0, c->stream>>>(a.Vr + (size_t)ly.col_c * ly.cols, ncd, ly.cols, ly.cols,
                                                           c->w, a.dscale + ly.col_c, c->x);
     double inc = c->L.k1 * fabs(sin(a.theta));
+    GS_COUNT_LAUNCH(c);
     k_flux<<<1, 1, 0, c->stream>>>(ly.K, c->x, a.k1n, a.k3n, inc, c->dscal + 4);
     GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaMemcpyAsync(cd_host, c->x, sizeof(cplx) * ncd, cudaMemcpyDeviceToHost, c->stream));

@@ -1,12 +1,19 @@
 // Factorisation of the empty-grating block on the GPU (FP64, Sec. 5 "We precompute A = U Sigma V^*").
 //
-// The J-expansion columns of A are rescaled to unit 2-norm (Sec. 3, Fig. 2a remark), then the
-// SVD of the scaled matrix is taken by one-sided (Hestenes) Jacobi: pairs of columns of W = A D
-// are rotated until every pair is orthogonal to relative precision tol; then W = U Sigma and the
-// accumulated rotations form V.  Column pairs follow the round-robin (circle) schedule, so each
-// launch rotates n/2 disjoint pairs, one thread block per pair.  The pseudo-inverse is applied as
-// A^+ g = D V Sigma^+ U^* g with Sigma^+ = min(1/sigma, 1/eps) (Eq. applypA), stored as
-// coef_j = 1/(sigma_j max(sigma_j, eps)) acting on W^* g.
+// The J-expansion columns of A are rescaled to unit 2-norm (Sec. 3, Fig. 2a remark).  The SVD of
+// the scaled matrix A D is then taken by preconditioned one-sided Jacobi (Drmac-Veselic):
+//   1. Householder QR with column pivoting, A D P = Q R (one thread block picks the pivot by the
+//      trailing column norms and builds the reflector; one block per trailing column applies it and
+//      recomputes that column's trailing norm);
+//   2. one-sided (Hestenes) Jacobi on X = R^*: column pairs of X are rotated until every pair is
+//      orthogonal to relative precision tol, giving X V_x = W_x with orthogonal columns; pairs
+//      follow the round-robin (circle) schedule, n/2 disjoint pairs per launch, one block per pair;
+//   3. R = V_x W_x^*, hence A D = (Q V_x) Sigma (P W_x Sigma^{-1})^*: U = Q V_x is formed by
+//      applying the reflectors to V_x, and V Sigma = P W_x.
+// U is orthonormal to working precision by construction (reflectors and rotations), which keeps
+// the clipped pseudo-inverse safe in the near-null directions.  A^+ g = D V Sigma^+ U^* g with
+// Sigma^+ = min(1/sigma, 1/eps) (Eq. applypA) is applied as D (P W_x) (coef .* (U^* g)) with
+// coef_j = 1/(sigma_j max(sigma_j, eps)), sigma_j = ||W_x e_j||.
 #include "gs_internal.h"
 
 namespace {
@@ -124,27 +131,234 @@ __global__ void k_transpose(const cplx *V, int n, cplx *Vr) {
     }
 }
 
+
+// ---- Householder QR with column pivoting ----------------------------------------------------------
+
+// Pivot + reflector for step j (single block): p = argmax_{k >= j} nrm2[k]; swap columns j and p;
+// H = I - tau v v^*, v = [1; x/(x0 - beta)], beta = -sign(Re x0) ||A[j:, j]||, tau = (beta - x0)/beta,
+// so that H^* A[j:, j] = beta e_1 (the LAPACK zlarfg convention).
+__global__ void __launch_bounds__(1024) k_qr_pivot_house(cplx *A, int m, int n, int j, double *nrm2, int *perm,
+                                                        cplx *tau) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ double shs[32];
+    __shared__ int piv;
+    __shared__ cplx hb[2];   // beta (real in .x), scale 1/(x0 - beta)
+    double best = -1.0;
+    int bi = j;
+    for (int k = j + threadIdx.x; k < n; k += blockDim.x) {
+        double v = nrm2[k];
+        if (v > best) {
+            best = v;
+            bi = k;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+        sv[w] = best;
+        si[w] = bi;
+    }
+    __syncthreads();
+    if (w == 0) {
+        best = l < nw ? sv[l] : -1.0;
+        bi = l < nw ? si[l] : n;
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (l == 0) piv = bi;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != j) {
+        cplx *a = A + (size_t)j * m, *b = A + (size_t)p * m;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            cplx t = a[i];
+            a[i] = b[i];
+            b[i] = t;
+        }
+        if (threadIdx.x == 0) {
+            double t = nrm2[j];
+            nrm2[j] = nrm2[p];
+            nrm2[p] = t;
+            int ti = perm[j];
+            perm[j] = perm[p];
+            perm[p] = ti;
+        }
+    }
+    __syncthreads();
+    cplx *a = A + (size_t)j * m;
+    double s2 = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) s2 += cabs2(a[i]);
+    s2 = block_sum(s2, shs);
+    if (threadIdx.x == 0) {
+        cplx x0 = a[j];
+        if (s2 == 0.0 && x0.y == 0.0) {
+            tau[j] = C(0.0, 0.0);
+            hb[0] = C(x0.x, 0.0);
+            hb[1] = C(0.0, 0.0);
+        } else {
+            double beta = -copysign(sqrt(cabs2(x0) + s2), x0.x);
+            tau[j] = C((beta - x0.x) / beta, -x0.y / beta);
+            hb[0] = C(beta, 0.0);
+            hb[1] = cdiv(C(1.0, 0.0), C(x0.x - beta, x0.y));
+        }
+    }
+    __syncthreads();
+    cplx sc = hb[1];
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) a[i] = cmul(a[i], sc);
+    if (threadIdx.x == 0) a[j] = hb[0];
+}
+
+// Applies H_j^* to trailing column k = j + 1 + blockIdx.x and recomputes its trailing norm.
+__global__ void k_qr_apply(cplx *A, int m, int n, int j, const cplx *tau, double *nrm2) {
+    int k = j + 1 + blockIdx.x;
+    if (k >= n) return;
+    __shared__ double sh[32];
+    const cplx *v = A + (size_t)j * m;   // v_j = 1 implicit, v_i = A[i, j] for i > j
+    cplx *a = A + (size_t)k * m;
+    double wr = 0.0, wi = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
+        cplx ai = a[i];
+        wr += vi.x * ai.x + vi.y * ai.y;
+        wi += vi.x * ai.y - vi.y * ai.x;
+    }
+    wr = block_sum(wr, sh);
+    wi = block_sum(wi, sh);
+    cplx f = cmul(cconj(tau[j]), C(wr, wi));   // conj(tau) (v^* a)
+    double s2 = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
+        cplx ai = csub(a[i], cmul(f, vi));
+        a[i] = ai;
+        if (i > j) s2 += cabs2(ai);
+    }
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) nrm2[k] = s2;
+}
+
+__global__ void k_colnorm2(const cplx *A, int m, int n, double *nrm2) {
+    int col = blockIdx.x;
+    if (col >= n) return;
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += cabs2(A[(size_t)col * m + i]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) nrm2[col] = s;
+}
+
+__global__ void k_iota(int *p, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+// X = R^* (n x n, column-major, lower triangular): X[i, j] = conj(R[j, i]) for i >= j
+__global__ void k_r_adjoint(const cplx *A, int m, int n, cplx *X) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    int i = (int)(id % n), j = (int)(id / n);
+    X[id] = (i >= j) ? cconj(A[(size_t)i * m + j]) : C(0.0, 0.0);
+}
+
+// Y (m x n, column-major) = [Vx; 0]
+__global__ void k_pad_rows(const cplx *Vx, int n, int m, cplx *Y) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)m * n) return;
+    int i = (int)(id % m), j = (int)(id / m);
+    Y[id] = (i < n) ? Vx[(size_t)j * n + i] : C(0.0, 0.0);
+}
+
+// Y[j:, col] = H_j Y[j:, col] = Y - tau_j v (v^* Y), block per column col
+__global__ void k_apply_reflector(const cplx *Aqr, int m, int j, const cplx *tau, cplx *Y, int ncols) {
+    int col = blockIdx.x;
+    if (col >= ncols) return;
+    __shared__ double sh[32];
+    const cplx *v = Aqr + (size_t)j * m;
+    cplx *y = Y + (size_t)col * m;
+    double wr = 0.0, wi = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
+        cplx yi = y[i];
+        wr += vi.x * yi.x + vi.y * yi.y;
+        wi += vi.x * yi.y - vi.y * yi.x;
+    }
+    wr = block_sum(wr, sh);
+    wi = block_sum(wi, sh);
+    cplx f = cmul(tau[j], C(wr, wi));
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
+        y[i] = csub(y[i], cmul(f, vi));
+    }
+}
+
+// Vr (row-major) = P W_x: row perm[i] of Vr is row i of W_x (column-major n x n)
+__global__ void k_permute_rows(const cplx *Wx, int n, const int *perm, cplx *Vr) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    int i = (int)(id % n), j = (int)(id / n);
+    Vr[(size_t)perm[i] * n + j] = Wx[id];
+}
+
 }  // namespace
 
 int gs_factor_angle(gs_ctx *c, AngleData &a) {
     const Layout &ly = c->lay;
-    int m = ly.rows, n = ly.cols;
+    const int m = ly.rows, n = ly.cols;
     cudaStream_t st = c->stream;
-    GS_TRY(gs_assemble_A(c, a, a.W, m));
+    cplx *Aqr = c->Vtmp;                       // m x n: scaled A, then R and the reflectors
+    cplx *X = c->Xtmp;                         // n x n: R^*, rotated into W_x
+    cplx *Vx = c->Vxtmp;                       // n x n: accumulated rotations
+    double *nrm2 = c->nrm2;
+    int *perm = c->perm;
+    cplx *tau = c->tau;
+    GS_TRY(gs_assemble_A(c, a, Aqr, m));
     GS_TRY(gs_assemble_f(c, a, a.f));
+    GS_COUNT_LAUNCH(c);
     k_fill<<<(n + 255) / 256, 256, 0, st>>>(a.dscale, n, 1.0);
-    k_colnorm_scale<<<ly.col_c - ly.col_a2, 256, 0, st>>>(a.W, m, m, ly.col_a2, ly.col_c, a.dscale);
-    // V (column-major) accumulates the rotations; a.Vr receives its row-major copy at the end
-    cplx *V = c->Vtmp;   // cols x cols, allocated by gs_factor
-    k_identity<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(V, n);
+    GS_COUNT_LAUNCH(c);
+    k_colnorm_scale<<<ly.col_c - ly.col_a2, 256, 0, st>>>(Aqr, m, m, ly.col_a2, ly.col_c, a.dscale);
+    // 1. QR with column pivoting
+    GS_COUNT_LAUNCH(c);
+    k_colnorm2<<<n, 256, 0, st>>>(Aqr, m, n, nrm2);
+    GS_COUNT_LAUNCH(c);
+    k_iota<<<(n + 255) / 256, 256, 0, st>>>(perm, n);
+    for (int j = 0; j < n; ++j) {
+        GS_COUNT_LAUNCH(c);
+        k_qr_pivot_house<<<1, 1024, 0, st>>>(Aqr, m, n, j, nrm2, perm, tau);
+        if (j + 1 < n) {
+            GS_COUNT_LAUNCH(c);
+            k_qr_apply<<<n - j - 1, 256, 0, st>>>(Aqr, m, n, j, tau, nrm2);
+        }
+    }
+    GS_CHECK_LAUNCH(c);
+    // 2. one-sided Jacobi on X = R^*
+    GS_COUNT_LAUNCH(c);
+    k_r_adjoint<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(Aqr, m, n, X);
+    GS_COUNT_LAUNCH(c);
+    k_identity<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(Vx, n);
     GS_CHECK_LAUNCH(c);
     int npad = n + (n & 1);
     const double tol = 1e-14;
     a.sweeps = 0;
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
         GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
-        for (int r = 0; r < npad - 1; ++r)
-            k_jacobi_round<<<npad / 2, JTPB, 0, st>>>(a.W, m, V, n, r, npad, tol, c->dcount);
+        for (int r = 0; r < npad - 1; ++r) {
+            GS_COUNT_LAUNCH(c);
+            k_jacobi_round<<<npad / 2, JTPB, 0, st>>>(X, n, Vx, n, r, npad, tol, c->dcount);
+        }
         GS_CHECK_LAUNCH(c);
         unsigned long long h = 0;
         GS_CUDA(c, cudaMemcpyAsync(&h, c->dcount, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -152,9 +366,17 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         a.sweeps = sweep + 1;
         if (h == 0) break;
     }
-    k_sigma<<<n, 256, 0, st>>>(a.W, m, n, c->L.eps_pinv, a.sigma, a.coef);
-    dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
-    k_transpose<<<tg, tb, 0, st>>>(V, n, a.Vr);
+    GS_COUNT_LAUNCH(c);
+    k_sigma<<<n, 256, 0, st>>>(X, n, n, c->L.eps_pinv, a.sigma, a.coef);
+    // 3. U = Q V_x (reflectors applied to [V_x; 0] in reverse order), V Sigma = P W_x
+    GS_COUNT_LAUNCH(c);
+    k_pad_rows<<<(int)(((long)m * n + 255) / 256), 256, 0, st>>>(Vx, n, m, a.W);
+    for (int j = n - 1; j >= 0; --j) {
+        GS_COUNT_LAUNCH(c);
+        k_apply_reflector<<<n, 256, 0, st>>>(Aqr, m, j, tau, a.W, n);
+    }
+    GS_COUNT_LAUNCH(c);
+    k_permute_rows<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(X, n, perm, a.Vr);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }

@@ -139,10 +139,16 @@ int launch_f64(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
         dst = c->part;
     }
     dim3 grid(gx, nsplit);
+    cudaEvent_t e0, e1;
+    const bool timed = gs_prof_pair(c, &e0, &e1);
+    if (timed) cudaEventRecord(e0, c->stream);
+    GS_COUNT_LAUNCH(c);
     k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, beta, c->L.k2, c->L.d, a.alpha,
                                                                   nsplit, dst);
+    if (timed) cudaEventRecord(e1, c->stream);
     if (nsplit > 1) {
         long len = (long)M * (2 * P + 1);
+        GS_COUNT_LAUNCH(c);
         k_sum_partials<<<(int)((len + 255) / 256), 256, 0, c->stream>>>(c->part, nsplit, len, out);
     }
     GS_CHECK_LAUNCH(c);
