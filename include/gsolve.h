@@ -77,7 +77,11 @@ typedef struct {
     double tol;       /* stop when ||b - L beta|| <= tol ||b|| (relative residual, Sec. 5)            */
     int maxit;        /* total iteration cap                                                          */
     int restart;      /* Krylov dimension before restart (<= 400)                                     */
-    int precision;    /* GS_FP64 or GS_C64 (the latter wraps inner c64 GMRES in FP64 refinement)      */
+    int precision;    /* GS_FP64: GMRES on the FP64 operator.  GS_C64: iterative refinement -- FP64
+                         residual b - L beta, inner GMRES on the operator with the complex64
+                         translation to relative residual inner_tol, FP64 correction; repeated until
+                         the FP64 residual meets tol                                                 */
+    double inner_tol; /* inner GMRES tolerance of the GS_C64 refinement (ignored for GS_FP64)       */
 } gs_solve_opts;
 
 /* ---- context --------------------------------------------------------------------------------- */
@@ -98,11 +102,14 @@ int gs_set_incidence(gs_ctx *ctx, int n_angles, const double *theta);
  * interface's extreme height band.  Requires gs_set_layers first. */
 int gs_set_inclusions(gs_ctx *ctx, const gs_inclusions *inc);
 
-/* Builds everything that depends on (geometry, angle) on the GPU in FP64 (Sec. 3 and Sec. 5):
- * assembles the empty-grating matrix A (Eq. matA) and right-hand side f (Eq. Arhs), rescales its
- * J-expansion columns to unit 2-norm, takes the SVD A D = U Sigma V^* by one-sided Jacobi, and
- * assembles the disk scattering diagonal S (Sec. 4.1), B_phys (Eq. matB, physical sign) and C
- * (Eq. matC).  Must follow gs_set_layers, gs_set_incidence and gs_set_inclusions. */
+/* Builds, on the GPU in FP64, what the solve needs (Sec. 3 and Sec. 5).  Per incidence angle, once
+ * for the grating: assembles the empty-grating matrix A (Eq. matA) and right-hand side f (Eq. Arhs),
+ * rescales its J-expansion columns to unit 2-norm and takes the SVD A D = U Sigma V^* (pivoted
+ * Householder QR, then one-sided Jacobi on R^*).  For the current disks: the scattering diagonal S
+ * (Sec. 4.1), B_phys (Eq. matB, physical sign) and C (Eq. matC).  The grating part is kept until
+ * gs_set_layers or gs_set_incidence; gs_set_inclusions only invalidates the disk part, so a new
+ * geometry on the same grating re-runs only the coupling.  Must follow gs_set_layers,
+ * gs_set_incidence and gs_set_inclusions. */
 int gs_factor(gs_ctx *ctx);
 
 /* ---- sizes ----------------------------------------------------------------------------------- */
@@ -137,8 +144,11 @@ int gs_rhs(gs_ctx *ctx, int angle, gs_c128 *b_dev);
 int gs_solve(gs_ctx *ctx, int angle, const gs_solve_opts *opts, const gs_c128 *beta0_dev);
 /* Copies the last solution of `angle` into beta_dev (length n). */
 int gs_get_beta(gs_ctx *ctx, int angle, gs_c128 *beta_dev);
-/* Iterations and final relative residial ||b - L beta||/||b|| (recomputed in FP64) of the last solve. */
+/* Iterations and final relative residual ||b - L beta||/||b|| (recomputed in FP64) of the last solve;
+ * for GS_C64 solves, iters counts all inner GMRES iterations. */
 int gs_stats(gs_ctx *ctx, int angle, int *iters, double *relres);
+/* Number of FP64 refinement sweeps of the last GS_C64 solve (0 after an FP64 solve). */
+int gs_stats_refinement(gs_ctx *ctx, int angle, int *outer);
 /* Bragg amplitudes of the propagating orders (Sec. 2 rad1/rad2; Sec. 5 alpha = A^+(f - C beta)),
  * written to HOST arrays: orders_top[*n_top], c[*n_top], orders_bot[*n_bot], d[*n_bot], each of
  * capacity >= 2 K_rb + 1, and the relative flux error
@@ -152,8 +162,9 @@ int gs_launch_count(gs_ctx *ctx, unsigned long long *count);
 /* enable != 0 starts CUDA-event timing of every launch of the translation kernel (the events are
  * recorded on the context's stream around the launch); any call resets the accumulated record. */
 int gs_profile(gs_ctx *ctx, int enable);
-/* Number of timed translation launches and their summed device time in ms (synchronises). */
-int gs_profile_read(gs_ctx *ctx, int *launches, double *total_ms);
+/* Number of timed translation launches of the given precision (GS_FP64 or GS_C64) and their
+ * summed device time in ms (synchronises). */
+int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms);
 /* Measures the FMA throughput of this GPU with independent multiply-add chains (precision GS_FP64
  * or GS_C64 for FP32) over all SMs; writes the achieved TFLOP/s (2 flops per FMA). */
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);

@@ -50,7 +50,7 @@ class gs_inclusions(ctypes.Structure):
 
 class gs_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 _SIGS = {
@@ -77,7 +77,8 @@ _SIGS = {
     "gs_bragg": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _vp, _ip, _ip, _vp, _dp]),
     "gs_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
     "gs_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
-    "gs_profile_read": (ctypes.c_int, [_vp, _ip, _dp]),
+    "gs_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
+    "gs_stats_refinement": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
     "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
 }
 
@@ -256,11 +257,16 @@ class GratingSolver:
         return b
 
     def solve(self, angle=0, tol=1e-11, maxit=1000, restart=200, precision=GS_FP64, beta0=None,
-              allow_unconverged=False):
-        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision)
+              allow_unconverged=False, inner_tol=1e-5):
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision, inner_tol=inner_tol)
         b0 = _ptr(self._as_dev(beta0)) if beta0 is not None else None
         ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
         return self._check(self.lib.gs_solve(self.ctx, angle, ctypes.byref(o), b0), "gs_solve", ok=ok)
+
+    def refinement_sweeps(self, angle=0):
+        v = ctypes.c_int()
+        self._check(self.lib.gs_stats_refinement(self.ctx, angle, ctypes.byref(v)), "gs_stats_refinement")
+        return v.value
 
     def get_beta(self, angle=0):
         t = self._cvec(self.dims()["n"])
@@ -281,9 +287,10 @@ class GratingSolver:
     def profile(self, enable=True):
         self._check(self.lib.gs_profile(self.ctx, int(bool(enable))), "gs_profile")
 
-    def profile_read(self):
+    def profile_read(self, precision=GS_FP64):
         n, ms = ctypes.c_int(), ctypes.c_double()
-        self._check(self.lib.gs_profile_read(self.ctx, ctypes.byref(n), ctypes.byref(ms)), "gs_profile_read")
+        self._check(self.lib.gs_profile_read(self.ctx, precision, ctypes.byref(n), ctypes.byref(ms)),
+                    "gs_profile_read")
         return n.value, ms.value
 
     def probe_fma(self, precision=GS_FP64):

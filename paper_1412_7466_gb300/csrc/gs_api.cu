@@ -17,7 +17,7 @@ int gs_fail(gs_ctx *c, int code, const std::string &msg) {
     return code;
 }
 
-bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1) {
+bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1, int precision) {
     if (!c->prof_on) return false;
     while (c->prof_ev.size() < c->prof_used + 2) {
         cudaEvent_t e;
@@ -29,6 +29,8 @@ bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1) {
     }
     *e0 = c->prof_ev[c->prof_used];
     *e1 = c->prof_ev[c->prof_used + 1];
+    if (c->prof_prec.size() < c->prof_used / 2 + 1) c->prof_prec.resize(c->prof_used / 2 + 1);
+    c->prof_prec[c->prof_used / 2] = precision;
     c->prof_used += 2;
     return true;
 }
@@ -57,6 +59,16 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// geometry-dependent data of an angle (rebuilt by gs_factor after gs_set_inclusions)
+void free_angle_geometry(AngleData &a) {
+    dfree(a.B);
+    dfree(a.Cm);
+    dfree(a.beta);
+    a.iters = 0;
+    a.outer = 0;
+    a.relres = -1.0;
+}
+
 void free_angle(AngleData &a) {
     dfree(a.kappa);
     dfree(a.k1n);
@@ -67,26 +79,17 @@ void free_angle(AngleData &a) {
     dfree(a.dscale);
     dfree(a.coef);
     dfree(a.sigma);
-    dfree(a.B);
-    dfree(a.Cm);
-    dfree(a.beta);
+    free_angle_geometry(a);
 }
 
-void free_factor(gs_ctx *c) {
-    for (auto &a : c->ang) free_angle(a);
-    c->ang.clear();
+// everything sized by the number of unknowns n = M (2p+1)
+void free_geometry(gs_ctx *c) {
+    for (auto &a : c->ang) free_angle_geometry(a);
     dfree(c->v1);
     dfree(c->v2);
     dfree(c->v3);
-    dfree(c->g);
-    dfree(c->w);
-    dfree(c->x);
-    dfree(c->Vtmp);
-    dfree(c->Xtmp);
-    dfree(c->Vxtmp);
-    dfree(c->nrm2);
-    dfree(c->perm);
-    dfree(c->tau);
+    dfree(c->v4);
+    dfree(c->v5);
     dfree(c->part);
     c->part_elems = 0;
     dfree(c->Vk);
@@ -97,6 +100,23 @@ void free_factor(gs_ctx *c) {
     dfree(c->yy);
     c->kdim = 0;
     c->factored = false;
+}
+
+// everything, including the per-angle factorisation of the empty grating
+void free_factor(gs_ctx *c) {
+    free_geometry(c);
+    for (auto &a : c->ang) free_angle(a);
+    c->ang.clear();
+    dfree(c->g);
+    dfree(c->w);
+    dfree(c->x);
+    dfree(c->Vtmp);
+    dfree(c->Xtmp);
+    dfree(c->Vxtmp);
+    dfree(c->nrm2);
+    dfree(c->perm);
+    dfree(c->tau);
+    c->grating_ready = false;
 }
 
 double iface_h(const gs_ctx *c, int which, double x) {
@@ -339,7 +359,7 @@ int gs_set_inclusions(gs_ctx *c, const gs_inclusions *I) {
                 }
             }
     }
-    free_factor(c);
+    free_geometry(c);
     c->M = I->M;
     c->p = I->p;
     c->nc = 2 * I->p + 1;
@@ -359,21 +379,50 @@ int gs_factor(gs_ctx *c) {
     CTX_GUARD(c);
     if (!c->have_layers || !c->have_inc || c->thetas.empty())
         return gs_fail(c, GS_ERR_STATE, "set layers, incidence and inclusions before gs_factor");
-    free_factor(c);
     const Layout &ly = c->lay;
+    // 1. per-angle factorisation of the empty grating (kept across gs_set_inclusions)
+    if (!c->grating_ready) {
+        free_factor(c);
+        GS_TRY(dalloc(c, &c->g, ly.rows));
+        GS_TRY(dalloc(c, &c->w, ly.cols));
+        GS_TRY(dalloc(c, &c->x, ly.cols));
+        GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
+        GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->nrm2, ly.cols));
+        GS_TRY(dalloc(c, &c->perm, ly.cols));
+        GS_TRY(dalloc(c, &c->tau, ly.cols));
+        c->ang.resize(c->thetas.size());
+        for (size_t q = 0; q < c->thetas.size(); ++q) {
+            AngleData &a = c->ang[q];
+            a.theta = c->thetas[q];
+            int K2 = 2 * ly.K + 1;
+            GS_TRY(dalloc(c, &a.kappa, K2));
+            GS_TRY(dalloc(c, &a.k1n, K2));
+            GS_TRY(dalloc(c, &a.k3n, K2));
+            GS_TRY(dalloc(c, &a.f, ly.rows));
+            GS_TRY(dalloc(c, &a.W, (size_t)ly.rows * ly.cols));
+            GS_TRY(dalloc(c, &a.Vr, (size_t)ly.cols * ly.cols));
+            GS_TRY(dalloc(c, &a.dscale, ly.cols));
+            GS_TRY(dalloc(c, &a.coef, ly.cols));
+            GS_TRY(dalloc(c, &a.sigma, ly.cols));
+            GS_TRY(gs_angle_scalars(c, a));
+            GS_TRY(gs_factor_angle(c, a));
+        }
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        dfree(c->Vtmp);
+        dfree(c->Xtmp);
+        dfree(c->Vxtmp);
+        c->grating_ready = true;
+    }
+    // 2. inclusion-dependent parts: S, B_phys, C, solver workspace
+    free_geometry(c);
     const int n = c->n();
     GS_TRY(dalloc(c, &c->v1, n));
     GS_TRY(dalloc(c, &c->v2, n));
     GS_TRY(dalloc(c, &c->v3, n));
-    GS_TRY(dalloc(c, &c->g, ly.rows));
-    GS_TRY(dalloc(c, &c->w, ly.cols));
-    GS_TRY(dalloc(c, &c->x, ly.cols));
-    GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
-    GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
-    GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
-    GS_TRY(dalloc(c, &c->nrm2, ly.cols));
-    GS_TRY(dalloc(c, &c->perm, ly.cols));
-    GS_TRY(dalloc(c, &c->tau, ly.cols));
+    GS_TRY(dalloc(c, &c->v4, n));
+    GS_TRY(dalloc(c, &c->v5, n));
     c->part_elems = gs_translate_scratch_elems(c->M, c->p);
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     c->kdim = 200;
@@ -384,33 +433,15 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->gg, c->kdim + 1));
     GS_TRY(dalloc(c, &c->yy, c->kdim + 1));
     GS_TRY(gs_mie(c));
-    c->ang.resize(c->thetas.size());
-    for (size_t q = 0; q < c->thetas.size(); ++q) {
-        AngleData &a = c->ang[q];
-        a.theta = c->thetas[q];
-        int K2 = 2 * ly.K + 1;
-        GS_TRY(dalloc(c, &a.kappa, K2));
-        GS_TRY(dalloc(c, &a.k1n, K2));
-        GS_TRY(dalloc(c, &a.k3n, K2));
-        GS_TRY(dalloc(c, &a.f, ly.rows));
-        GS_TRY(dalloc(c, &a.W, (size_t)ly.rows * ly.cols));
-        GS_TRY(dalloc(c, &a.Vr, (size_t)ly.cols * ly.cols));
-        GS_TRY(dalloc(c, &a.dscale, ly.cols));
-        GS_TRY(dalloc(c, &a.coef, ly.cols));
-        GS_TRY(dalloc(c, &a.sigma, ly.cols));
+    for (auto &a : c->ang) {
         GS_TRY(dalloc(c, &a.B, (size_t)n * ly.nB()));
         GS_TRY(dalloc(c, &a.Cm, (size_t)ly.nC() * n));
         GS_TRY(dalloc(c, &a.beta, n));
         GS_CUDA(c, cudaMemsetAsync(a.beta, 0, sizeof(cplx) * n, c->stream));
-        GS_TRY(gs_angle_scalars(c, a));
-        GS_TRY(gs_factor_angle(c, a));
         GS_TRY(gs_assemble_B(c, a, a.B));
         GS_TRY(gs_assemble_C(c, a, a.Cm));
     }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
-    dfree(c->Vtmp);
-    dfree(c->Xtmp);
-    dfree(c->Vxtmp);
     c->factored = true;
     return GS_OK;
 }
@@ -526,6 +557,13 @@ int gs_stats(gs_ctx *c, int angle, int *iters, double *relres) {
     return GS_OK;
 }
 
+int gs_stats_refinement(gs_ctx *c, int angle, int *outer) {
+    if (!c || !outer) return GS_ERR_ARG;
+    GS_TRY(check_angle(c, angle));
+    *outer = c->ang[angle].outer;
+    return GS_OK;
+}
+
 int gs_bragg(gs_ctx *c, int angle, int *n_top, int *orders_top, gs_c128 *cc, int *n_bot, int *orders_bot,
              gs_c128 *dd, double *flux_err) {
     CTX_GUARD(c);
@@ -578,17 +616,20 @@ int gs_profile(gs_ctx *c, int enable) {
     return GS_OK;
 }
 
-int gs_profile_read(gs_ctx *c, int *launches, double *total_ms) {
+int gs_profile_read(gs_ctx *c, int precision, int *launches, double *total_ms) {
     CTX_GUARD(c);
     if (!launches || !total_ms) return gs_fail(c, GS_ERR_ARG, "null output");
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     double tot = 0.0;
+    int cnt = 0;
     for (size_t q = 0; q + 1 < c->prof_used; q += 2) {
+        if (c->prof_prec[q / 2] != precision) continue;
         float ms = 0.f;
         GS_CUDA(c, cudaEventElapsedTime(&ms, c->prof_ev[q], c->prof_ev[q + 1]));
         tot += ms;
+        ++cnt;
     }
-    *launches = (int)(c->prof_used / 2);
+    *launches = cnt;
     *total_ms = tot;
     return GS_OK;
 }

@@ -36,7 +36,8 @@ struct AngleData {
     cplx *Cm = nullptr;          // nC x n row-major
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;
-    int iters = 0;
+    int iters = 0;               // GMRES iterations (all inner iterations for the mixed solve)
+    int outer = 0;               // refinement sweeps of the mixed solve (0 for FP64)
     double relres = -1.0;
 };
 
@@ -67,11 +68,13 @@ struct gs_ctx {
     double *xy = nullptr, *radius = nullptr, *kp = nullptr;
     cplx *s = nullptr;                       // M x nc
 
-    bool factored = false;
+    bool grating_ready = false;   // per-angle factorisation of the empty grating is built
+    bool factored = false;        // ... and the inclusion coupling for the current disks
     std::vector<AngleData> ang;
 
     // scratch
     cplx *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;   // n each
+    cplx *v4 = nullptr, *v5 = nullptr;                  // n each (refinement residual, correction)
     cplx *g = nullptr;                                  // rows
     cplx *w = nullptr, *x = nullptr;                     // cols
     cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
@@ -94,6 +97,7 @@ struct gs_ctx {
     unsigned long long nlaunch = 0;
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // start/stop pairs, reused
+    std::vector<int> prof_prec;         // precision of each timed launch
     size_t prof_used = 0;               // events used since the last reset
 
     int n() const { return M * nc; }
@@ -101,7 +105,7 @@ struct gs_ctx {
 
 #define GS_COUNT_LAUNCH(ctx) ((ctx)->nlaunch++)
 // returns a (start, stop) event pair for timing one launch, or false when profiling is off
-bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1);
+bool gs_prof_pair(gs_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1, int precision);
 
 // error helpers (defined in gs_api.cu)
 int gs_fail(gs_ctx *c, int code, const std::string &msg);

@@ -256,43 +256,35 @@ int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
     return GS_OK;
 }
 
-// Restarted GMRES (Saad-Schultz) with classical Gram-Schmidt applied twice, Givens rotations on
-// the device; the host reads one residual estimate per iteration.
-int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0) {
+namespace {
+
+__global__ void k_axpy_inplace(cplx *x, const cplx *y, long n) {
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) x[e] = cadd(x[e], y[e]);
+}
+
+// Restarted GMRES (Saad-Schultz) with classical Gram-Schmidt applied twice and Givens rotations on
+// the device; the host reads one residual estimate per iteration.  Solves L_prec x = b from the
+// start x (zero when x_zero) until ||b - L_prec x|| <= tol * bnorm; the true residual is checked
+// at the end of each cycle.  Uses v2 (residual), v3 (translation output) and the Krylov workspace.
+int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx *x, bool x_zero, double tol,
+               int maxit, int restart, int precision, int *iters, double *relres) {
     const long n = c->n();
     cudaStream_t st = c->stream;
-    const int kd = std::min(o.restart, c->kdim);
+    const int kd = std::min(restart, c->kdim);
     const int ld = c->kdim + 1;
     const int eb = (int)((n + 255) / 256);
-    cplx *b = c->v1, *r = c->v2;
-    cplx *x = a.beta;
-    double *ds = c->dscal;   // [0] = ||b||, [1] = ||r||, [2] = residual estimate, [3] = scratch
-    GS_TRY(gs_rhs_impl(c, a, b));
-    GS_COUNT_LAUNCH(c);
-    k_norm<<<1, 1024, 0, st>>>(b, n, ds);
-    if (x0) {
-        GS_CUDA(c, cudaMemcpyAsync(x, x0, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
-    } else {
-        GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
-    }
-    GS_CUDA(c, cudaMemcpyAsync(c->hscal, ds, sizeof(double), cudaMemcpyDeviceToHost, st));
-    GS_CUDA(c, cudaStreamSynchronize(st));
-    const double bnorm = c->hscal[0];
-    a.iters = 0;
-    a.relres = 0.0;
-    if (bnorm == 0.0) {
-        GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
-        return GS_OK;
-    }
+    cplx *r = c->v2;
+    double *ds = c->dscal;   // [1] = ||r||, [2] = residual estimate, [3] = scratch
     int it = 0;
-    bool first = (x0 == nullptr);
+    bool first = x_zero;
     double est = 1.0;
-    while (it < o.maxit) {
-        // r = b - L x
+    if (x_zero) GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+    while (it < maxit) {
         if (first) {
             GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
         } else {
-            GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            GS_TRY(gs_apply_impl(c, a, x, r, precision));
             GS_COUNT_LAUNCH(c);
             k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
         }
@@ -302,17 +294,17 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
         GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
         GS_CUDA(c, cudaStreamSynchronize(st));
         est = c->hscal[1] / bnorm;
-        if (est <= o.tol) break;
+        if (est <= tol) break;
         GS_COUNT_LAUNCH(c);
         k_scale_by_inv<<<eb, 256, 0, st>>>(r, n, ds + 1, c->Vk, nullptr);
         GS_COUNT_LAUNCH(c);
         k_set_g0<<<(ld + 255) / 256, 256, 0, st>>>(c->gg, ld, ds + 1);
         GS_CUDA(c, cudaMemsetAsync(c->Hh, 0, sizeof(cplx) * (size_t)ld * c->kdim, st));
         int j = 0, kk = 0;
-        for (; j < kd && it < o.maxit; ++j) {
+        for (; j < kd && it < maxit; ++j) {
             cplx *vj = c->Vk + (size_t)j * n;
             cplx *w = c->Vk + (size_t)(j + 1) * n;
-            GS_TRY(gs_apply_impl(c, a, vj, w, GS_FP64));
+            GS_TRY(gs_apply_impl(c, a, vj, w, precision));
             ++it;
             cplx *h = c->Hh + (size_t)j * ld;
             // CGS2
@@ -337,16 +329,16 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
             GS_CUDA(c, cudaStreamSynchronize(st));
             est = c->hscal[2] / bnorm;
             kk = j + 1;
-            if (est <= o.tol) break;
+            if (est <= tol) break;
         }
         GS_COUNT_LAUNCH(c);
         k_backsolve<<<1, 1, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
         GS_COUNT_LAUNCH(c);
         k_add_combo<<<eb, 256, 0, st>>>(x, c->Vk, n, c->yy, kk);
         GS_CHECK_LAUNCH(c);
-        if (est <= o.tol) {
-            // confirm with the true residual
-            GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+        if (est <= tol) {
+            // confirm with the true residual of this operator
+            GS_TRY(gs_apply_impl(c, a, x, r, precision));
             GS_COUNT_LAUNCH(c);
             k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
             GS_COUNT_LAUNCH(c);
@@ -354,13 +346,80 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
             est = c->hscal[1] / bnorm;
-            if (est <= 10.0 * o.tol) break;
-            first = false;
+            if (est <= 10.0 * tol) break;
         }
     }
-    a.iters = it;
-    a.relres = est;
-    return est <= 10.0 * o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
+    *iters = it;
+    *relres = est;
+    return GS_OK;
+}
+
+}  // namespace
+
+// FP64: GMRES on L.  GS_C64: iterative refinement with FP64 residuals and inner GMRES on the
+// operator whose translation runs in complex64 (the correction equation L d = r is solved to
+// inner_tol, x += d), until the FP64 relative residual meets tol.
+int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0) {
+    const long n = c->n();
+    cudaStream_t st = c->stream;
+    const int eb = (int)((n + 255) / 256);
+    cplx *b = c->v1;
+    cplx *x = a.beta;
+    GS_TRY(gs_rhs_impl(c, a, b));
+    GS_COUNT_LAUNCH(c);
+    k_norm<<<1, 1024, 0, st>>>(b, n, c->dscal);
+    if (x0) GS_CUDA(c, cudaMemcpyAsync(x, x0, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(c, cudaMemcpyAsync(c->hscal, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    const double bnorm = c->hscal[0];
+    a.iters = 0;
+    a.outer = 0;
+    a.relres = 0.0;
+    if (bnorm == 0.0) {
+        GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+        return GS_OK;
+    }
+    if (o.precision == GS_FP64) {
+        int its = 0;
+        double rr = 1.0;
+        GS_TRY(gmres_core(c, a, b, bnorm, x, x0 == nullptr, o.tol, o.maxit, o.restart, GS_FP64, &its, &rr));
+        a.iters = its;
+        a.relres = rr;
+        return rr <= 10.0 * o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
+    }
+    // mixed precision refinement
+    cplx *r = c->v4, *dx = c->v5;
+    if (!x0) GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+    const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
+    double rel = 1.0;
+    int total = 0;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        if (sweep == 0 && !x0) {
+            GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            GS_TRY(gs_apply_impl(c, a, x, r, GS_FP64));
+            GS_COUNT_LAUNCH(c);
+            k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+        }
+        GS_COUNT_LAUNCH(c);
+        k_norm<<<1, 1024, 0, st>>>(r, n, c->dscal + 5);
+        GS_CUDA(c, cudaMemcpyAsync(c->hscal + 5, c->dscal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(c, cudaStreamSynchronize(st));
+        const double rnorm = c->hscal[5];
+        rel = rnorm / bnorm;
+        a.outer = sweep;
+        if (rel <= o.tol || total >= o.maxit) break;
+        int its = 0;
+        double rr = 1.0;
+        GS_TRY(gmres_core(c, a, r, rnorm, dx, true, itol, o.maxit - total, o.restart, GS_C64, &its, &rr));
+        total += its;
+        GS_COUNT_LAUNCH(c);
+        k_axpy_inplace<<<eb, 256, 0, st>>>(x, dx, n);
+        GS_CHECK_LAUNCH(c);
+    }
+    a.iters = total;
+    a.relres = rel;
+    return rel <= o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
 }
 
 // Bragg amplitudes: x_cd = D_cd .* V[cd rows] (coef .* W^* (f - C beta)); flux error on the device.

@@ -113,6 +113,120 @@ k_translate_f64(const double *__restrict__ xy, int M, const cplx *__restrict__ b
     }
 }
 
+
+// ---- complex64 variant (the inner operator of the mixed-precision solve) --------------------------
+// Same tiling as the FP64 kernel; the pair geometry (dx, dy) is formed in FP64 and rounded, the
+// Hankel seeds come from the single-precision Bessel functions and the recurrence, the Toeplitz
+// products and the per-lane accumulators are FP32; the warp and chunk sums are FP64.  Values stay
+// in their natural scale: for p <= 12 and k R >= 0.5 the largest Hankel order is below 1e36 and the
+// smallest coefficients of interest above the FP32 normal range.
+typedef float2 cplxf;
+__device__ __forceinline__ cplxf CF(float r, float i) { return make_float2(r, i); }
+__device__ __forceinline__ cplxf cmulf(cplxf a, cplxf b) { return CF(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ void cfmaf(cplxf &acc, cplxf a, cplxf b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+template <int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_translate_c64(const double *__restrict__ xy, int M, const cplx *__restrict__ beta, double k, double d,
+                cplx alpha, int nsplit, cplx *__restrict__ out) {
+    constexpr int NC = 2 * P + 1;
+    __shared__ cplxf sb[NC][TILE];
+    __shared__ double sx[TILE], sy[TILE];
+    __shared__ int sid[TILE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WARPS + warp;
+    const long total = 3L * M;
+    const long s0 = total * blockIdx.y / nsplit, s1 = total * (blockIdx.y + 1) / nsplit;
+    double xi = 0.0, yi = 0.0;
+    if (i < M) {
+        xi = xy[2 * i];
+        yi = xy[2 * i + 1];
+    }
+    cplxf acc[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) acc[m] = CF(0.f, 0.f);
+    const cplx ainv = cconj(alpha);
+    const float kf = (float)k;
+
+    for (long t0 = s0; t0 < s1; t0 += TILE) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TILE * NC; e += WARPS * 32) {
+            int u = e / NC, n = e - u * NC;
+            long s = t0 + u;
+            cplx v = C(0.0, 0.0);
+            if (s < s1) {
+                int l = (int)(s / M) - 1;
+                int j = (int)(s - (long)(l + 1) * M);
+                cplx b = beta[(size_t)j * NC + n];
+                v = (l == 0) ? b : cmul(l == 1 ? alpha : ainv, b);
+            }
+            sb[n][u] = CF((float)v.x, (float)v.y);
+        }
+        for (int u = threadIdx.x; u < TILE; u += WARPS * 32) {
+            long s = t0 + u;
+            if (s < s1) {
+                int l = (int)(s / M) - 1;
+                int j = (int)(s - (long)(l + 1) * M);
+                sx[u] = xy[2 * j] + l * d;
+                sy[u] = xy[2 * j + 1];
+                sid[u] = (l == 0) ? j : -1;
+            } else {
+                sid[u] = -2;
+                sx[u] = 0.0;
+                sy[u] = 0.0;
+            }
+        }
+        __syncthreads();
+        if (i >= M) continue;
+        const long s = t0 + lane;
+        if (s >= s1 || sid[lane] == i) continue;
+        const float dx = (float)(xi - sx[lane]), dy = (float)(yi - sy[lane]);
+        const float R = hypotf(dx, dy);
+        const float z = kf * R;
+        const float twoz = 2.0f / z;
+        cplxf Hm1 = CF(j0f(z), y0f(z)), Hc = CF(j1f(z), y1f(z));
+        const float iR = 1.0f / R;
+        const cplxf u1 = CF(dx * iR, dy * iR);
+        cplxf up = u1;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) cfmaf(acc[m], Hm1, sb[m][lane]);
+#pragma unroll
+        for (int q = 1; q <= 2 * P; ++q) {
+            const cplxf hq = cmulf(Hc, up);
+            cplxf hmq = cmulf(Hc, CF(up.x, -up.y));
+            if (q & 1) hmq = CF(-hmq.x, -hmq.y);
+#pragma unroll
+            for (int m = 0; m + q < NC; ++m) cfmaf(acc[m], hq, sb[m + q][lane]);
+#pragma unroll
+            for (int m = q; m < NC; ++m) cfmaf(acc[m], hmq, sb[m - q][lane]);
+            if (q < 2 * P) {
+                const float f = q * twoz;
+                const cplxf Hn = CF(fmaf(f, Hc.x, -Hm1.x), fmaf(f, Hc.y, -Hm1.y));
+                Hm1 = Hc;
+                Hc = Hn;
+                up = cmulf(up, u1);
+            }
+        }
+    }
+    double accd[2 * NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        accd[2 * m] = warp_sum((double)acc[m].x);
+        accd[2 * m + 1] = warp_sum((double)acc[m].y);
+    }
+    if (i < M) {
+        cplx *o = out + ((size_t)blockIdx.y * M + i) * NC;
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+            if (lane == (m & 31)) o[m] = C(accd[2 * m], accd[2 * m + 1]);
+    }
+}
+
 __global__ void k_sum_partials(const cplx *part, int nsplit, long len, cplx *out) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= len) return;
@@ -122,7 +236,7 @@ __global__ void k_sum_partials(const cplx *part, int nsplit, long len, cplx *out
 }
 
 template <int P>
-int launch_f64(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
+int launch_translate(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision) {
     constexpr int WARPS = 4;
     const int M = c->M;
     const int gx = (M + WARPS - 1) / WARPS;
@@ -140,11 +254,15 @@ int launch_f64(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
     }
     dim3 grid(gx, nsplit);
     cudaEvent_t e0, e1;
-    const bool timed = gs_prof_pair(c, &e0, &e1);
+    const bool timed = gs_prof_pair(c, &e0, &e1, precision);
     if (timed) cudaEventRecord(e0, c->stream);
     GS_COUNT_LAUNCH(c);
-    k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, beta, c->L.k2, c->L.d, a.alpha,
-                                                                  nsplit, dst);
+    if (precision == GS_C64)
+        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, beta, c->L.k2, c->L.d, a.alpha,
+                                                                      nsplit, dst);
+    else
+        k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, beta, c->L.k2, c->L.d, a.alpha,
+                                                                      nsplit, dst);
     if (timed) cudaEventRecord(e1, c->stream);
     if (nsplit > 1) {
         long len = (long)M * (2 * P + 1);
@@ -160,19 +278,18 @@ int launch_f64(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
 size_t gs_translate_scratch_elems(int M, int p) { return (size_t)64 * M * (2 * p + 1); }
 
 int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision) {
-    (void)precision;
     switch (c->p) {
-        case 1: return launch_f64<1>(c, a, beta, out);
-        case 2: return launch_f64<2>(c, a, beta, out);
-        case 3: return launch_f64<3>(c, a, beta, out);
-        case 4: return launch_f64<4>(c, a, beta, out);
-        case 5: return launch_f64<5>(c, a, beta, out);
-        case 6: return launch_f64<6>(c, a, beta, out);
-        case 7: return launch_f64<7>(c, a, beta, out);
-        case 8: return launch_f64<8>(c, a, beta, out);
-        case 10: return launch_f64<10>(c, a, beta, out);
-        case 12: return launch_f64<12>(c, a, beta, out);
-        case 16: return launch_f64<16>(c, a, beta, out);
+        case 1: return launch_translate<1>(c, a, beta, out, precision);
+        case 2: return launch_translate<2>(c, a, beta, out, precision);
+        case 3: return launch_translate<3>(c, a, beta, out, precision);
+        case 4: return launch_translate<4>(c, a, beta, out, precision);
+        case 5: return launch_translate<5>(c, a, beta, out, precision);
+        case 6: return launch_translate<6>(c, a, beta, out, precision);
+        case 7: return launch_translate<7>(c, a, beta, out, precision);
+        case 8: return launch_translate<8>(c, a, beta, out, precision);
+        case 10: return launch_translate<10>(c, a, beta, out, precision);
+        case 12: return launch_translate<12>(c, a, beta, out, precision);
+        case 16: return launch_translate<16>(c, a, beta, out, precision);
         default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
     }
 }

@@ -61,3 +61,24 @@ def test_headline_solve_matches_golden(headline):
     b = np.array([ref[k] for k in keys])
     assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
     assert br["flux_err"] < 1e-10
+
+
+def test_headline_mixed_solve_matches_golden(headline):
+    from paper_1412_7466_gb300 import GS_C64
+    cfg, gs = headline
+    gs.solve(tol=cfg["tol"], maxit=4000, restart=200, precision=GS_C64)
+    its, rr = gs.stats()
+    assert rr <= cfg["tol"]
+    br = gs.bragg()
+    ref = {}
+    for ln in open(os.path.join(HERE, "golden", "headline_bragg.txt")):
+        if ln.startswith("#"):
+            continue
+        s, n, a, b = ln.split()
+        ref[(s, int(n))] = complex(float(a), float(b))
+    got = {("c", int(n)): v for n, v in zip(br["n_top"], br["c"])}
+    got.update({("d", int(n)): v for n, v in zip(br["n_bot"], br["d"])})
+    keys = sorted(ref)
+    a = np.array([got[k] for k in keys])
+    b = np.array([ref[k] for k in keys])
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)

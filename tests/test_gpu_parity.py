@@ -197,3 +197,53 @@ def test_geometry_and_state_errors():
         gs.solve()
     assert e.value.status == GS_ERR_STATE
     gs.close()
+
+
+def test_translate_c64_matches_oracle(small):
+    """complex64 translation: FP32 products and Hankel recurrence; the operator agrees with the
+    FP64 oracle to single-precision accuracy (1e-5 relative in norm, from ~1e-7 unit roundoff
+    accumulated over ~30 source images and up to 2p recurrence steps per pair)."""
+    from paper_1412_7466_gb300 import GS_C64
+    cfg, prob, gs = small
+    rng = np.random.default_rng(4)
+    n = prob.M * prob.nc
+    w = np.tile(0.3 ** np.abs(np.arange(-prob.disks["p"], prob.disks["p"] + 1)), prob.M)
+    beta = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * w
+    got = _np(gs.translate(beta, precision=GS_C64))
+    ref = prob.translate(beta)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_mixed_solve_small_bragg(small):
+    """Mixed form (complex64 inner GMRES + FP64 refinement) reaches the same 1e-9 Bragg target."""
+    from paper_1412_7466_gb300 import GS_C64
+    cfg, prob, gs = small
+    gs.solve(tol=cfg["tol"], maxit=2000, precision=GS_C64)
+    its, rr = gs.stats()
+    assert rr <= cfg["tol"]
+    assert gs.refinement_sweeps() >= 1
+    got = gs.bragg()
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, _ = prob.recover(beta)
+    a = np.concatenate([got["c"], got["d"]])
+    b = np.concatenate([ref["c"], ref["d"]])
+    assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b)
+
+
+def test_new_geometry_keeps_grating_factorisation():
+    """gs_set_inclusions after gs_factor keeps the per-angle grating factorisation: a second
+    geometry solved on the same context matches a fresh context."""
+    cfg = W.config("small")
+    g, th = cfg["grating"], cfg["theta"]
+    d2 = W.disks(7, 0.04, 0.02, 2.0, g["k"][0], seed=77, p=10)
+    gs = _setup_gpu(g, th, cfg["disks"])
+    gs.set_inclusions(d2)
+    gs.factor()
+    gs.solve(tol=1e-12, maxit=500)
+    a = gs.bragg()
+    gs.close()
+    gs2 = _setup_gpu(g, th, d2)
+    gs2.solve(tol=1e-12, maxit=500)
+    b = gs2.bragg()
+    gs2.close()
+    np.testing.assert_allclose(np.r_[a["c"], a["d"]], np.r_[b["c"], b["d"]], rtol=0, atol=1e-12)
