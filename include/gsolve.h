@@ -156,6 +156,29 @@ int gs_stats_refinement(gs_ctx *ctx, int angle, int *outer);
 int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
              int *n_bot, int *orders_bot, gs_c128 *d, double *flux_err);
 
+/* Allocation-free translation, for callers that cannot allocate device memory where they need it
+ * (a framework whose pool owns the device heap, a real-time loop that allows no allocation after
+ * start-up, code that runs without a gs_ctx).  The paper has no counterpart: it is the operation
+ * of gs_translate (alpha = T beta over all pairs and the +-d images) without a context.  Inputs and
+ * outputs are the caller's device buffers on the current device: xy_dev holds the M centres
+ * (x, y interleaved, FP64), beta_dev and alpha_dev hold M (2p+1) complex128 values each (layout
+ * of gs_translate), k2 is the middle-layer wavenumber, d the period, alpha_re + i alpha_im the
+ * Bloch phase exp(i k1 cos(theta) d); precision GS_FP64 or GS_C64; work is queued on cuda_stream
+ * (NULL = legacy default stream) and is asynchronous.
+ * Nothing is allocated: the chunk partials live in a fixed device array of 2^19 complex128 values
+ * (8 MiB) compiled into the library, which every GPU that loads the library holds until exit.
+ * Sizes: M (2p+1) must not exceed 2^19 (524288), else GS_ERR_ARG is returned before any device
+ * work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
+ * precision; GS_ERR_CUDA if the launch fails.  The first call on a device looks up the array's
+ * device address (once per device, with that device current); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's partials: every
+ * partial a call reads is written by that same call, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on the array and must be
+ * serialised by the caller. */
+int gs_translate_noalloc(int M, int p, const double *xy_dev, double k2, double d, double alpha_re,
+                         double alpha_im, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision,
+                         void *cuda_stream);
+
 /* ---- instrumentation (not part of the method) ------------------------------------------------ */
 /* Kernel launches issued by this context since gs_create (all calls). */
 int gs_launch_count(gs_ctx *ctx, unsigned long long *count);

@@ -80,6 +80,8 @@ _SIGS = {
     "gs_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
     "gs_stats_refinement": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
     "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
 }
 
 _lib = None
@@ -105,6 +107,19 @@ def load_library(path: str = LIB_PATH):
     if path == LIB_PATH:
         _lib = lib
     return lib
+
+
+def translate_noalloc(xy, beta, out, p, k2, d, alpha, precision=GS_FP64, stream=None):
+    """alpha = T beta through the allocation-free entry point (no context; for callers that
+    cannot allocate device memory).  xy: (M, 2) float64, beta/out: M (2p+1) complex128, all CUDA
+    tensors on the current device.  Returns the status code."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    a = complex(alpha)
+    return lib.gs_translate_noalloc(int(xy.shape[0]), int(p), _vp(xy.data_ptr()), float(k2), float(d), a.real,
+                                    a.imag, _vp(beta.data_ptr()), _vp(out.data_ptr()), int(precision),
+                                    _vp(st.cuda_stream))
 
 
 class GsError(RuntimeError):

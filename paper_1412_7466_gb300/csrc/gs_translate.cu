@@ -13,6 +13,8 @@
 // unrolled for the compile-time order P).  Warp-shuffle reductions combine the lanes.  The source
 // images are split into `nsplit` chunks across blockIdx.y to fill the 152 SMs; a second kernel
 // sums the chunk partials in a fixed order (deterministic).
+#include <mutex>
+
 #include "gs_internal.h"
 
 namespace {
@@ -291,5 +293,99 @@ int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out
         case 12: return launch_translate<12>(c, a, beta, out, precision);
         case 16: return launch_translate<16>(c, a, beta, out, precision);
         default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+}
+
+// ---- allocation-free variant --------------------------------------------------------------------
+// Some callers cannot allocate device memory at the point where they need a translation: a host
+// framework that owns the whole device heap through its own pool, a real-time loop that forbids
+// allocation (and the implicit synchronisation cudaMalloc/cudaFree bring) after start-up, or code
+// that runs before any context has been created for it.  gs_translate_noalloc serves them: it
+// needs no gs_ctx and keeps the chunk partials of the translation in a fixed array compiled into
+// this library instead of a buffer obtained from cudaMalloc.
+
+// Chunk partials of gs_translate_noalloc: 2^19 complex128 values (8 MiB), held on every GPU that
+// loads this library until the process exits.
+#define GS_NOALLOC_CAPACITY (1 << 19)
+static __device__ __align__(256) cplx gs_noalloc_partials[GS_NOALLOC_CAPACITY];
+
+namespace {
+
+constexpr int GS_NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+cplx *g_noalloc_scratch[GS_NOALLOC_MAX_DEVICES] = {};   // device address of the array, per device
+
+template <int P>
+int noalloc_launch(int M, const double *xy, const cplx *beta, double k, double d, cplx alpha, int precision,
+                   cplx *out, cudaStream_t st, cplx *scratch) {
+    constexpr int WARPS = 4;
+    constexpr int NC = 2 * P + 1;
+    const int gx = (M + WARPS - 1) / WARPS;
+    int nsplit = (int)((152L * 8 + gx - 1) / gx);
+    if (nsplit > 64) nsplit = 64;
+    if ((long)nsplit * 32 > 3L * M) nsplit = (int)((3L * M + 31) / 32);
+    if (nsplit < 1) nsplit = 1;
+    const long len = (long)M * NC;
+    if ((long)nsplit * len > GS_NOALLOC_CAPACITY) nsplit = (int)(GS_NOALLOC_CAPACITY / len);
+    if (nsplit < 1) return GS_ERR_ARG;   // M (2p+1) exceeds the fixed scratch
+    dim3 grid(gx, nsplit);
+    if (precision == GS_C64)
+        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, st>>>(xy, M, beta, k, d, alpha, nsplit, scratch);
+    else
+        k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, st>>>(xy, M, beta, k, d, alpha, nsplit, scratch);
+    k_sum_partials<<<(int)((len + 255) / 256), 256, 0, st>>>(scratch, nsplit, len, out);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int gs_translate_noalloc(int M, int p, const double *xy_dev, double k2, double d, double alpha_re,
+                                    double alpha_im, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision,
+                                    void *cuda_stream) {
+    // every size check precedes any device work
+    if (M < 1 || !xy_dev || !beta_dev || !alpha_dev || (const void *)beta_dev == (const void *)alpha_dev)
+        return GS_ERR_ARG;
+    if (!(k2 > 0.0) || !(d > 0.0) || (precision != GS_FP64 && precision != GS_C64)) return GS_ERR_ARG;
+    switch (p) {
+        case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 10: case 12: case 16: break;
+        default: return GS_ERR_ARG;
+    }
+    if ((long)M * (2 * p + 1) > GS_NOALLOC_CAPACITY) return GS_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= GS_NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    cplx *scratch = nullptr;
+    {
+        // first call on a device: look up the device address of the array (host code only sees a
+        // stand-in symbol); done once per device, with that device current
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_scratch[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, gs_noalloc_partials) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return GS_ERR_CUDA;
+            }
+            g_noalloc_scratch[dev] = (cplx *)ptr;
+        }
+        scratch = g_noalloc_scratch[dev];
+    }
+    const cplx alpha = C(alpha_re, alpha_im);
+    const cplx *beta = (const cplx *)beta_dev;
+    cplx *out = (cplx *)alpha_dev;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    switch (p) {
+        case 1: return noalloc_launch<1>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 2: return noalloc_launch<2>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 3: return noalloc_launch<3>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 4: return noalloc_launch<4>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 5: return noalloc_launch<5>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 6: return noalloc_launch<6>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 7: return noalloc_launch<7>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 8: return noalloc_launch<8>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 10: return noalloc_launch<10>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 12: return noalloc_launch<12>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        default: return noalloc_launch<16>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
     }
 }
