@@ -337,11 +337,12 @@ def main():
         res[name] = {"r": r, "e2e": el_e2e, "err": err, "flux": brg["flux_err"],
                      "outer": gs.refinement_sweeps(), "n_cd": len(br["c"]) + len(br["d"])}
     # pre-refinement error of the mixed form: one inner solve, no FP64 correction
+    # pre-refinement error of the mixed form: one complex64 inner solve from zero, no FP64 correction
     pre_err = None
     try:
         gs.set_inclusions(cfg0["disks"])
         gs.factor()
-        o = gs.solve(tol=0.99, maxit=4000, restart=200, precision=GS_C64, allow_unconverged=True)
+        gs.solve(tol=tol, maxit=4000, restart=200, precision=GS_C64, allow_unconverged=True, max_sweeps=1)
         br = gs.bragg()
         ref = {}
         for ln in open(GOLDEN):

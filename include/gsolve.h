@@ -81,7 +81,10 @@ typedef struct {
                          residual b - L beta, inner GMRES on the operator with the complex64
                          translation to relative residual inner_tol, FP64 correction; repeated until
                          the FP64 residual meets tol                                                 */
-    double inner_tol; /* inner GMRES tolerance of the GS_C64 refinement (ignored for GS_FP64)       */
+    double inner_tol; /* GS_C64: tightest inner GMRES tolerance; each correction is solved to
+                         max(inner_tol, tol / (2 * current relative residual)); <= 0 means 1e-6     */
+    int max_sweeps;   /* GS_C64: cap on the inner solves (1 = one complex64 solve from zero with no
+                         FP64 correction, the pre-refinement iterate); <= 0 means 30                 */
 } gs_solve_opts;
 
 /* ---- context --------------------------------------------------------------------------------- */
@@ -111,6 +114,12 @@ int gs_set_inclusions(gs_ctx *ctx, const gs_inclusions *inc);
  * geometry on the same grating re-runs only the coupling.  Must follow gs_set_layers,
  * gs_set_incidence and gs_set_inclusions. */
 int gs_factor(gs_ctx *ctx);
+
+/* The FP64 translation reads its coefficients H_q(k2 R) e^{i q Th} (all pairs and images) from a
+ * table built by gs_factor for each geometry, 3 M^2 (4p+1) complex128 values, when that fits the
+ * budget (default: half of the free device memory at gs_factor); otherwise it recomputes them in
+ * the kernel.  budget_gb < 0 restores the default, 0 disables the table. */
+int gs_set_table_budget(gs_ctx *ctx, double budget_gb);
 
 /* ---- sizes ----------------------------------------------------------------------------------- */
 /* rows, cols of A; n = M (2p+1) unknowns; nB = columns of B_phys (4N + 2 Q2 + 1); nC = rows of C
@@ -167,8 +176,8 @@ int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
  * (NULL = legacy default stream) and is asynchronous.
  * Nothing is allocated: the chunk partials live in a fixed device array of 2^19 complex128 values
  * (8 MiB) compiled into the library, which every GPU that loads the library holds until exit.
- * Sizes: M (2p+1) must not exceed 2^19 (524288), else GS_ERR_ARG is returned before any device
- * work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
+ * Sizes: M (2p+1) must not exceed 2^19 (524288) for GS_FP64 and 349525 for GS_C64 (whose complex64
+ * copy of beta shares the array), else GS_ERR_ARG is returned before any device work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
  * precision; GS_ERR_CUDA if the launch fails.  The first call on a device looks up the array's
  * device address (once per device, with that device current); make that first call before any
  * stream capture.  All calls share the one array and it keeps the last call's partials: every

@@ -50,7 +50,7 @@ class gs_inclusions(ctypes.Structure):
 
 class gs_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
-                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int)]
 
 
 _SIGS = {
@@ -80,6 +80,7 @@ _SIGS = {
     "gs_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
     "gs_stats_refinement": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
     "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "gs_set_table_budget": (ctypes.c_int, [_vp, ctypes.c_double]),
     "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
 }
@@ -272,8 +273,9 @@ class GratingSolver:
         return b
 
     def solve(self, angle=0, tol=1e-11, maxit=1000, restart=200, precision=GS_FP64, beta0=None,
-              allow_unconverged=False, inner_tol=1e-5):
-        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision, inner_tol=inner_tol)
+              allow_unconverged=False, inner_tol=1e-6, max_sweeps=0):
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision, inner_tol=inner_tol,
+                          max_sweeps=max_sweeps)
         b0 = _ptr(self._as_dev(beta0)) if beta0 is not None else None
         ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
         return self._check(self.lib.gs_solve(self.ctx, angle, ctypes.byref(o), b0), "gs_solve", ok=ok)
@@ -292,6 +294,9 @@ class GratingSolver:
         it, rr = ctypes.c_int(), ctypes.c_double()
         self._check(self.lib.gs_stats(self.ctx, angle, ctypes.byref(it), ctypes.byref(rr)), "gs_stats")
         return it.value, rr.value
+
+    def set_table_budget(self, gb):
+        self._check(self.lib.gs_set_table_budget(self.ctx, float(gb)), "gs_set_table_budget")
 
     # -- instrumentation ------------------------------------------------------------------------
     def launch_count(self):

@@ -91,6 +91,8 @@ void free_geometry(gs_ctx *c) {
     dfree(c->v4);
     dfree(c->v5);
     dfree(c->part);
+    dfree(c->b32);
+    dfree(c->htab);
     c->part_elems = 0;
     dfree(c->Vk);
     dfree(c->Hh);
@@ -425,6 +427,7 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->v5, n));
     c->part_elems = gs_translate_scratch_elems(c->M, c->p);
     GS_TRY(dalloc(c, &c->part, c->part_elems));
+    GS_TRY(dalloc(c, &c->b32, n));
     c->kdim = 200;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
     GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));
@@ -433,6 +436,21 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->gg, c->kdim + 1));
     GS_TRY(dalloc(c, &c->yy, c->kdim + 1));
     GS_TRY(gs_mie(c));
+    {
+        // translation coefficient table for the FP64 product, when it fits the memory budget
+        size_t bytes = sizeof(cplx) * gs_pair_table_elems(c->M, c->p);
+        size_t fr = 0, totm = 0;
+        GS_CUDA(c, cudaMemGetInfo(&fr, &totm));
+        double budget = c->table_budget_gb >= 0 ? c->table_budget_gb * 1e9 : 0.5 * (double)fr;
+        if ((double)bytes <= budget) {
+            if (cudaMalloc((void **)&c->htab, bytes) == cudaSuccess) {
+                GS_TRY(gs_build_pair_table(c));
+            } else {
+                cudaGetLastError();
+                c->htab = nullptr;
+            }
+        }
+    }
     for (auto &a : c->ang) {
         GS_TRY(dalloc(c, &a.B, (size_t)n * ly.nB()));
         GS_TRY(dalloc(c, &a.Cm, (size_t)ly.nC() * n));
@@ -600,6 +618,12 @@ int gs_bragg(gs_ctx *c, int angle, int *n_top, int *orders_top, gs_c128 *cc, int
     *n_bot = nbt;
     *flux_err = flux;
     return finite ? GS_OK : gs_fail(c, GS_ERR_NUMERIC, "non-finite Bragg amplitude");
+}
+
+int gs_set_table_budget(gs_ctx *c, double budget_gb) {
+    if (!c) return GS_ERR_ARG;
+    c->table_budget_gb = budget_gb;
+    return GS_OK;
 }
 
 int gs_launch_count(gs_ctx *c, unsigned long long *count) {

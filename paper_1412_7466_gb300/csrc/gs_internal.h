@@ -83,6 +83,9 @@ struct gs_ctx {
     int *perm = nullptr;                                 // cols, column pivots
     cplx *tau = nullptr;                                 // cols, reflector scalars
     cplx *part = nullptr;                                // translation partials
+    float2 *b32 = nullptr;                               // n, complex64 copy of the source coefficients
+    cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
+    double table_budget_gb = -1.0;                       // < 0: half of the free device memory
     size_t part_elems = 0;
     // GMRES workspace
     int kdim = 0;
@@ -135,6 +138,8 @@ int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm);
 int gs_factor_angle(gs_ctx *c, AngleData &a);
 // translation (gs_translate.cu)
 int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision);
+size_t gs_pair_table_elems(int M, int p);
+int gs_build_pair_table(gs_ctx *c);
 // low-rank, operator, GMRES, Bragg (gs_solve.cu)
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);

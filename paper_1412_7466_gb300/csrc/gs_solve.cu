@@ -150,46 +150,67 @@ __global__ void k_sub(const cplx *a, const cplx *b, long n, cplx *y) {
 }
 
 // Givens step for Hessenberg column j (column-major, leading dimension ld): applies the previous
-// rotations, forms the new one, updates g and writes the residual estimate |g[j+1]| to res.
+// rotations, forms the new one, updates g and writes the residual estimate |g[j+1]| to res.  The
+// column and the rotations are staged in shared memory; the sequential part runs on one thread.
+constexpr int GS_KMAX = 512;
 __global__ void k_givens(cplx *H, int ld, int j, cplx *cs, cplx *sn, cplx *g, double *res) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    cplx *h = H + (size_t)j * ld;
-    for (int i = 0; i < j; ++i) {
-        cplx t = cadd(cmul(cs[i], h[i]), cmul(sn[i], h[i + 1]));
-        h[i + 1] = cadd(cmul(cscale(cconj(sn[i]), -1.0), h[i]), cmul(cs[i], h[i + 1]));
-        h[i] = t;
+    __shared__ cplx h[GS_KMAX + 1], c_[GS_KMAX], s_[GS_KMAX];
+    cplx *col = H + (size_t)j * ld;
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) h[i] = col[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        c_[i] = cs[i];
+        s_[i] = sn[i];
     }
-    cplx a = h[j], b = h[j + 1];
-    double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
-    double rr = hypot(aa, bb);
-    cplx c, s;
-    if (rr == 0.0) {
-        c = C(1, 0);
-        s = C(0, 0);
-    } else if (aa == 0.0) {
-        c = C(0, 0);
-        s = cscale(cconj(b), 1.0 / bb);
-    } else {
-        c = C(aa / rr, 0.0);
-        s = cmul(cscale(a, 1.0 / aa), cscale(cconj(b), 1.0 / rr));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < j; ++i) {
+            cplx t = cadd(cmul(c_[i], h[i]), cmul(s_[i], h[i + 1]));
+            h[i + 1] = cadd(cmul(cscale(cconj(s_[i]), -1.0), h[i]), cmul(c_[i], h[i + 1]));
+            h[i] = t;
+        }
+        cplx a = h[j], b = h[j + 1];
+        double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
+        double rr = hypot(aa, bb);
+        cplx c, s;
+        if (rr == 0.0) {
+            c = C(1, 0);
+            s = C(0, 0);
+        } else if (aa == 0.0) {
+            c = C(0, 0);
+            s = cscale(cconj(b), 1.0 / bb);
+        } else {
+            c = C(aa / rr, 0.0);
+            s = cmul(cscale(a, 1.0 / aa), cscale(cconj(b), 1.0 / rr));
+        }
+        cs[j] = c;
+        sn[j] = s;
+        h[j] = cadd(cmul(c, a), cmul(s, b));
+        h[j + 1] = C(0, 0);
+        cplx gj = g[j];
+        g[j + 1] = cmul(cscale(cconj(s), -1.0), gj);
+        g[j] = cmul(c, gj);
+        res[0] = sqrt(cabs2(g[j + 1]));
     }
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = cadd(cmul(c, a), cmul(s, b));
-    h[j + 1] = C(0, 0);
-    cplx gj = g[j];
-    g[j + 1] = cmul(cscale(cconj(s), -1.0), gj);
-    g[j] = cmul(c, gj);
-    res[0] = sqrt(cabs2(g[j + 1]));
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = h[i];
 }
 
-// back substitution H[0:k,0:k] y = g[0:k] (upper triangular, single thread)
+// back substitution H[0:k,0:k] y = g[0:k] (upper triangular), column-oriented: one thread divides,
+// the block updates the remaining right-hand side
 __global__ void k_backsolve(const cplx *H, int ld, int kk, const cplx *g, cplx *y) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ cplx r[GS_KMAX];
+    __shared__ cplx yi;
+    for (int i = threadIdx.x; i < kk; i += blockDim.x) r[i] = g[i];
+    __syncthreads();
     for (int i = kk - 1; i >= 0; --i) {
-        cplx s = g[i];
-        for (int c = i + 1; c < kk; ++c) s = csub(s, cmul(H[(size_t)c * ld + i], y[c]));
-        y[i] = cdiv(s, H[(size_t)i * ld + i]);
+        if (threadIdx.x == 0) {
+            yi = cdiv(r[i], H[(size_t)i * ld + i]);
+            y[i] = yi;
+        }
+        __syncthreads();
+        const cplx v = yi;
+        for (int q = threadIdx.x; q < i; q += blockDim.x) r[q] = csub(r[q], cmul(H[(size_t)i * ld + q], v));
+        __syncthreads();
     }
 }
 
@@ -323,7 +344,7 @@ int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx 
             GS_COUNT_LAUNCH(c);
             k_scale_by_inv<<<eb, 256, 0, st>>>(w, n, ds + 3, w, h + j + 1);
             GS_COUNT_LAUNCH(c);
-            k_givens<<<1, 1, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
+            k_givens<<<1, 128, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
             GS_CHECK_LAUNCH(c);
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
@@ -332,7 +353,7 @@ int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx 
             if (est <= tol) break;
         }
         GS_COUNT_LAUNCH(c);
-        k_backsolve<<<1, 1, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
+        k_backsolve<<<1, 256, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
         GS_COUNT_LAUNCH(c);
         k_add_combo<<<eb, 256, 0, st>>>(x, c->Vk, n, c->yy, kk);
         GS_CHECK_LAUNCH(c);
@@ -390,10 +411,13 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
     // mixed precision refinement
     cplx *r = c->v4, *dx = c->v5;
     if (!x0) GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
-    const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
+    // inner tolerance: each correction only needs to bring the residual from rel down to tol, but
+    // no tighter than inner_tol (the accuracy the complex64 operator can support)
+    const double floor_tol = o.inner_tol > 0 ? o.inner_tol : 1e-6;
     double rel = 1.0;
     int total = 0;
-    for (int sweep = 0; sweep < 30; ++sweep) {
+    const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 30;
+    for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         if (sweep == 0 && !x0) {
             GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
         } else {
@@ -408,9 +432,10 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
         const double rnorm = c->hscal[5];
         rel = rnorm / bnorm;
         a.outer = sweep;
-        if (rel <= o.tol || total >= o.maxit) break;
+        if (rel <= o.tol || total >= o.maxit || sweep == max_sweeps) break;
         int its = 0;
         double rr = 1.0;
+        const double itol = std::max(floor_tol, 0.5 * o.tol / rel);
         GS_TRY(gmres_core(c, a, r, rnorm, dx, true, itol, o.maxit - total, o.restart, GS_C64, &its, &rr));
         total += its;
         GS_COUNT_LAUNCH(c);
