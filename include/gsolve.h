@@ -76,7 +76,7 @@ typedef struct {
 typedef struct {
     double tol;       /* stop when ||b - L beta|| <= tol ||b|| (relative residual, Sec. 5)            */
     int maxit;        /* total iteration cap                                                          */
-    int restart;      /* Krylov dimension before restart (<= 400)                                     */
+    int restart;      /* Krylov dimension before restart (capped at 512; the workspace grows on demand) */
     int precision;    /* GS_FP64: GMRES on the FP64 operator.  GS_C64: iterative refinement -- FP64
                          residual b - L beta, inner GMRES on the operator with the complex64
                          translation to relative residual inner_tol, FP64 correction; repeated until
@@ -187,6 +187,31 @@ int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
 int gs_translate_noalloc(int M, int p, const double *xy_dev, double k2, double d, double alpha_re,
                          double alpha_im, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision,
                          void *cuda_stream);
+
+/* ---- batched solves (many geometries on one grating) ----------------------------------------- */
+/* Batched form (north_star "Batching"): G geometries of uneven size, all with the same multipole
+ * order, share the per-angle grating factorisation; their translations run as one persistent launch
+ * (an atomic work queue over (geometry, 4 targets, chunk of source images) items, largest geometries
+ * first, chunk length and blocks per SM picked by timing candidates on the first factorisation),
+ * the low-rank products are grouped over the geometries, and GMRES advances all of them in
+ * lockstep, one CUDA-graph replay per Arnoldi step (the step reads its index from device memory).
+ * Host arrays are copied; each geometry is validated as by gs_set_inclusions.  The batch replaces
+ * the single-geometry inclusions of the context; gs_set_layers and gs_set_incidence discard it. */
+int gs_set_inclusions_batch(gs_ctx *ctx, int G, const gs_inclusions *geos);
+/* Grating factorisation (if not built) and S, B_phys, C of every geometry at every angle. */
+int gs_factor_batch(gs_ctx *ctx);
+/* y_g = L_g x_g for all g; x and y concatenate the geometries' vectors (geometry order). */
+int gs_apply_batch(gs_ctx *ctx, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision);
+/* Solves all geometries at `angle` (GS_FP64: lockstep GMRES; GS_C64: lockstep mixed refinement).
+ * GS_ERR_NOT_CONVERGED if any geometry misses tol; per-geometry results stay readable. */
+int gs_solve_batch(gs_ctx *ctx, int angle, const gs_solve_opts *opts);
+int gs_batch_stats(gs_ctx *ctx, int angle, int g, int *iters, double *relres);
+int gs_get_beta_batch(gs_ctx *ctx, int angle, int g, gs_c128 *beta_dev);
+/* Bragg amplitudes of geometry g (host outputs as in gs_bragg). */
+int gs_bragg_batch(gs_ctx *ctx, int angle, int g, int *n_top, int *orders_top, gs_c128 *c, int *n_bot,
+                   int *orders_bot, gs_c128 *d, double *flux_err);
+/* The autotuned source-image chunk length and blocks per SM of the batched translation. */
+int gs_batch_tuning(gs_ctx *ctx, int *chunk, int *blocks_per_sm);
 
 /* ---- instrumentation (not part of the method) ------------------------------------------------ */
 /* Kernel launches issued by this context since gs_create (all calls). */

@@ -81,6 +81,14 @@ _SIGS = {
     "gs_stats_refinement": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
     "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "gs_set_table_budget": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "gs_set_inclusions_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gs_inclusions)]),
+    "gs_factor_batch": (ctypes.c_int, [_vp]),
+    "gs_apply_batch": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
+    "gs_solve_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gs_solve_opts)]),
+    "gs_batch_stats": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _dp]),
+    "gs_get_beta_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "gs_bragg_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _vp, _ip, _ip, _vp, _dp]),
+    "gs_batch_tuning": (ctypes.c_int, [_vp, _ip, _ip]),
     "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
 }
@@ -272,7 +280,7 @@ class GratingSolver:
         self._check(self.lib.gs_rhs(self.ctx, angle, _ptr(b)), "gs_rhs")
         return b
 
-    def solve(self, angle=0, tol=1e-11, maxit=1000, restart=200, precision=GS_FP64, beta0=None,
+    def solve(self, angle=0, tol=1e-11, maxit=4000, restart=500, precision=GS_FP64, beta0=None,
               allow_unconverged=False, inner_tol=1e-6, max_sweeps=0):
         o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision, inner_tol=inner_tol,
                           max_sweeps=max_sweeps)
@@ -297,6 +305,64 @@ class GratingSolver:
 
     def set_table_budget(self, gb):
         self._check(self.lib.gs_set_table_budget(self.ctx, float(gb)), "gs_set_table_budget")
+
+    # -- batched solves (many geometries on one grating) -----------------------------------------
+    def set_inclusions_batch(self, geos):
+        keep, arr = [], (gs_inclusions * len(geos))()
+        for q, dk in enumerate(geos):
+            xy, pxy = _arr(dk["xy"])
+            r, pr = _arr(dk["radius"])
+            kp, pkp = _arr(dk["kp"])
+            keep += [xy, r, kp]
+            arr[q] = gs_inclusions(M=xy.shape[0], p=int(dk["p"]), xy=pxy, radius=pr, kp=pkp)
+        self._check(self.lib.gs_set_inclusions_batch(self.ctx, len(geos), arr), "gs_set_inclusions_batch")
+        self.batch_sizes = [np.asarray(dk["xy"]).shape[0] * (2 * int(dk["p"]) + 1) for dk in geos]
+        self.p = int(geos[0]["p"])
+
+    def factor_batch(self):
+        self._check(self.lib.gs_factor_batch(self.ctx), "gs_factor_batch")
+
+    def apply_batch(self, x, angle=0, precision=GS_FP64):
+        x = self._as_dev(x)
+        y = self._cvec(x.numel())
+        self._check(self.lib.gs_apply_batch(self.ctx, angle, _ptr(x), _ptr(y), precision), "gs_apply_batch")
+        return y
+
+    def solve_batch(self, angle=0, tol=1e-11, maxit=4000, restart=500, precision=GS_FP64, inner_tol=1e-6,
+                    max_sweeps=0, allow_unconverged=False):
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=precision, inner_tol=inner_tol,
+                          max_sweeps=max_sweeps)
+        ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
+        return self._check(self.lib.gs_solve_batch(self.ctx, angle, ctypes.byref(o)), "gs_solve_batch", ok=ok)
+
+    def batch_stats(self, g, angle=0):
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.gs_batch_stats(self.ctx, angle, g, ctypes.byref(it), ctypes.byref(rr)), "gs_batch_stats")
+        return it.value, rr.value
+
+    def get_beta_batch(self, g, angle=0):
+        t = self._cvec(self.batch_sizes[g])
+        self._check(self.lib.gs_get_beta_batch(self.ctx, angle, g, _ptr(t)), "gs_get_beta_batch")
+        return t
+
+    def bragg_batch(self, g, angle=0):
+        cap = 2 * self.grating["K_rb"] + 1
+        nt, nb = ctypes.c_int(), ctypes.c_int()
+        ot = (ctypes.c_int * cap)()
+        ob = (ctypes.c_int * cap)()
+        c = np.zeros(cap, dtype=np.complex128)
+        d = np.zeros(cap, dtype=np.complex128)
+        fe = ctypes.c_double()
+        self._check(self.lib.gs_bragg_batch(self.ctx, angle, g, ctypes.byref(nt), ot, c.ctypes.data_as(_vp),
+                                            ctypes.byref(nb), ob, d.ctypes.data_as(_vp), ctypes.byref(fe)),
+                    "gs_bragg_batch")
+        return {"n_top": np.array(ot[:nt.value]), "c": c[:nt.value].copy(),
+                "n_bot": np.array(ob[:nb.value]), "d": d[:nb.value].copy(), "flux_err": fe.value}
+
+    def batch_tuning(self):
+        ch, bp = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.gs_batch_tuning(self.ctx, ctypes.byref(ch), ctypes.byref(bp)), "gs_batch_tuning")
+        return ch.value, bp.value
 
     # -- instrumentation ------------------------------------------------------------------------
     def launch_count(self):

@@ -104,8 +104,10 @@ void free_geometry(gs_ctx *c) {
     c->factored = false;
 }
 
-// everything, including the per-angle factorisation of the empty grating
-void free_factor(gs_ctx *c) {
+// everything, including the per-angle factorisation of the empty grating; the batch too unless
+// keep_batch (rebuilding the grating factorisation for a batch must not discard that batch)
+void free_factor(gs_ctx *c, bool keep_batch = false) {
+    if (!keep_batch) gs_batch_destroy(c);
     free_geometry(c);
     for (auto &a : c->ang) free_angle(a);
     c->ang.clear();
@@ -148,6 +150,61 @@ int check_angle(gs_ctx *c, int angle) {
 }
 
 }  // namespace
+
+// Krylov workspace of the single-geometry solve for a restart length of up to 512
+int gs_ensure_krylov(gs_ctx *c, int restart) {
+    const int want = std::max(1, std::min(restart, 512));
+    if (c->Vk && c->kdim >= want) return GS_OK;
+    const long n = c->n();
+    c->kdim = want;
+    GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
+    GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));
+    GS_TRY(dalloc(c, &c->cs, c->kdim + 1));
+    GS_TRY(dalloc(c, &c->sn, c->kdim + 1));
+    GS_TRY(dalloc(c, &c->gg, c->kdim + 1));
+    GS_TRY(dalloc(c, &c->yy, c->kdim + 1));
+    return GS_OK;
+}
+
+int gs_ensure_grating(gs_ctx *c) {
+    const Layout &ly = c->lay;
+    // per-angle factorisation of the empty grating (kept across gs_set_inclusions)
+    if (!c->grating_ready) {
+        free_factor(c, true);
+        GS_TRY(dalloc(c, &c->g, ly.rows));
+        GS_TRY(dalloc(c, &c->w, ly.cols));
+        GS_TRY(dalloc(c, &c->x, ly.cols));
+        GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
+        GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->nrm2, ly.cols));
+        GS_TRY(dalloc(c, &c->perm, ly.cols));
+        GS_TRY(dalloc(c, &c->tau, ly.cols));
+        c->ang.resize(c->thetas.size());
+        for (size_t q = 0; q < c->thetas.size(); ++q) {
+            AngleData &a = c->ang[q];
+            a.theta = c->thetas[q];
+            int K2 = 2 * ly.K + 1;
+            GS_TRY(dalloc(c, &a.kappa, K2));
+            GS_TRY(dalloc(c, &a.k1n, K2));
+            GS_TRY(dalloc(c, &a.k3n, K2));
+            GS_TRY(dalloc(c, &a.f, ly.rows));
+            GS_TRY(dalloc(c, &a.W, (size_t)ly.rows * ly.cols));
+            GS_TRY(dalloc(c, &a.Vr, (size_t)ly.cols * ly.cols));
+            GS_TRY(dalloc(c, &a.dscale, ly.cols));
+            GS_TRY(dalloc(c, &a.coef, ly.cols));
+            GS_TRY(dalloc(c, &a.sigma, ly.cols));
+            GS_TRY(gs_angle_scalars(c, a));
+            GS_TRY(gs_factor_angle(c, a));
+        }
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        dfree(c->Vtmp);
+        dfree(c->Xtmp);
+        dfree(c->Vxtmp);
+        c->grating_ready = true;
+    }
+    return GS_OK;
+}
 
 extern "C" {
 
@@ -382,41 +439,7 @@ int gs_factor(gs_ctx *c) {
     if (!c->have_layers || !c->have_inc || c->thetas.empty())
         return gs_fail(c, GS_ERR_STATE, "set layers, incidence and inclusions before gs_factor");
     const Layout &ly = c->lay;
-    // 1. per-angle factorisation of the empty grating (kept across gs_set_inclusions)
-    if (!c->grating_ready) {
-        free_factor(c);
-        GS_TRY(dalloc(c, &c->g, ly.rows));
-        GS_TRY(dalloc(c, &c->w, ly.cols));
-        GS_TRY(dalloc(c, &c->x, ly.cols));
-        GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
-        GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
-        GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
-        GS_TRY(dalloc(c, &c->nrm2, ly.cols));
-        GS_TRY(dalloc(c, &c->perm, ly.cols));
-        GS_TRY(dalloc(c, &c->tau, ly.cols));
-        c->ang.resize(c->thetas.size());
-        for (size_t q = 0; q < c->thetas.size(); ++q) {
-            AngleData &a = c->ang[q];
-            a.theta = c->thetas[q];
-            int K2 = 2 * ly.K + 1;
-            GS_TRY(dalloc(c, &a.kappa, K2));
-            GS_TRY(dalloc(c, &a.k1n, K2));
-            GS_TRY(dalloc(c, &a.k3n, K2));
-            GS_TRY(dalloc(c, &a.f, ly.rows));
-            GS_TRY(dalloc(c, &a.W, (size_t)ly.rows * ly.cols));
-            GS_TRY(dalloc(c, &a.Vr, (size_t)ly.cols * ly.cols));
-            GS_TRY(dalloc(c, &a.dscale, ly.cols));
-            GS_TRY(dalloc(c, &a.coef, ly.cols));
-            GS_TRY(dalloc(c, &a.sigma, ly.cols));
-            GS_TRY(gs_angle_scalars(c, a));
-            GS_TRY(gs_factor_angle(c, a));
-        }
-        GS_CUDA(c, cudaStreamSynchronize(c->stream));
-        dfree(c->Vtmp);
-        dfree(c->Xtmp);
-        dfree(c->Vxtmp);
-        c->grating_ready = true;
-    }
+    GS_TRY(gs_ensure_grating(c));
     // 2. inclusion-dependent parts: S, B_phys, C, solver workspace
     free_geometry(c);
     const int n = c->n();

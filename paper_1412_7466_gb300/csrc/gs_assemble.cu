@@ -617,33 +617,37 @@ int gs_assemble_f(gs_ctx *c, const AngleData &a, cplx *f) {
     return GS_OK;
 }
 
-int gs_mie(gs_ctx *c) {
+int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, cplx *s) {
     GS_COUNT_LAUNCH(c);
-    k_mie<<<nblk(c->M * c->nc), TPB, 0, c->stream>>>(c->M, c->p, c->radius, c->kp, c->L.k2, c->s);
+    k_mie<<<nblk(M * c->nc), TPB, 0, c->stream>>>(M, c->p, radius, kp, c->L.k2, s);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
 
-int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B) {
+int gs_mie(gs_ctx *c) { return gs_mie_geo(c, c->M, c->radius, c->kp, c->s); }
+
+int gs_assemble_B_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *B) {
     const Layout &ly = c->lay;
     int N = c->L.N, nB = ly.nB();
     Curve c1 = curve_of(c->curve[0], N), c2 = curve_of(c->curve[1], N);
     GS_COUNT_LAUNCH(c);
-    k_B_layer<<<nblk((long)c->M * N, 128), 128, 0, c->stream>>>(c->M, c->p, c->xy, c1, N, c->L.k2, c->L.d,
+    k_B_layer<<<nblk((long)M * N, 128), 128, 0, c->stream>>>(M, c->p, xy, c1, N, c->L.k2, c->L.d,
                                                                a.alpha, B, nB, ly.col_mu1, ly.col_sig1);
     GS_COUNT_LAUNCH(c);
-    k_B_layer<<<nblk((long)c->M * N, 128), 128, 0, c->stream>>>(c->M, c->p, c->xy, c2, N, c->L.k2, c->L.d,
+    k_B_layer<<<nblk((long)M * N, 128), 128, 0, c->stream>>>(M, c->p, xy, c2, N, c->L.k2, c->L.d,
                                                                a.alpha, B, nB, ly.col_mu2, ly.col_sig2);
     GS_COUNT_LAUNCH(c);
-    k_B_a2<<<nblk((long)c->M * (2 * ly.Q2 + 1), 128), 128, 0, c->stream>>>(
-        c->M, c->p, c->xy, 0.0, 0.5 * (c->L.h1_0 + c->L.h2_0), c->L.k2, ly.Q2, B, nB, ly.col_a2);
+    k_B_a2<<<nblk((long)M * (2 * ly.Q2 + 1), 128), 128, 0, c->stream>>>(
+        M, c->p, xy, 0.0, 0.5 * (c->L.h1_0 + c->L.h2_0), c->L.k2, ly.Q2, B, nB, ly.col_a2);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
 
-int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm) {
+int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B) { return gs_assemble_B_geo(c, a, c->M, c->xy, B); }
+
+int gs_assemble_C_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *Cm) {
     const Layout &ly = c->lay;
-    int N = c->L.N, n = c->n();
+    int N = c->L.N, n = M * c->nc;
     double d = c->L.d;
     GS_CUDA(c, cudaMemsetAsync(Cm, 0, sizeof(cplx) * (size_t)ly.nC() * n, c->stream));
     Curve c1 = curve_of(c->curve[0], N), c2 = curve_of(c->curve[1], N);
@@ -651,16 +655,18 @@ int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm) {
     Targets t1 = curve_targets(c1, N), t2 = curve_targets(c2, N);
     Targets tw = wall_targets(c->wall_y[1], ly.nw2, -0.5 * d);
     GS_COUNT_LAUNCH(c);
-    k_C<<<nblk((long)N * c->M, 128), 128, 0, c->stream>>>(t1, c->M, c->p, c->xy, c->L.k2, 3, -d, 0.0, d, ai,
+    k_C<<<nblk((long)N * M, 128), 128, 0, c->stream>>>(t1, M, c->p, xy, c->L.k2, 3, -d, 0.0, d, ai,
                                                          one, al, -1.0, Cm, n, ly.row_g1v, ly.row_g1n);
     GS_COUNT_LAUNCH(c);
-    k_C<<<nblk((long)N * c->M, 128), 128, 0, c->stream>>>(t2, c->M, c->p, c->xy, c->L.k2, 3, -d, 0.0, d, ai,
+    k_C<<<nblk((long)N * M, 128), 128, 0, c->stream>>>(t2, M, c->p, xy, c->L.k2, 3, -d, 0.0, d, ai,
                                                          one, al, 1.0, Cm, n, ly.row_g2v, ly.row_g2n);
     GS_COUNT_LAUNCH(c);
-    k_C<<<nblk((long)ly.nw2 * c->M, 128), 128, 0, c->stream>>>(tw, c->M, c->p, c->xy, c->L.k2, 2, d,
+    k_C<<<nblk((long)ly.nw2 * M, 128), 128, 0, c->stream>>>(tw, M, c->p, xy, c->L.k2, 2, d,
                                                               -2.0 * d, 0.0, cmul(al, al),
                                                               cscale(ai, -1.0), one, 1.0, Cm, n,
                                                               ly.row_w2v, ly.row_w2n);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
+
+int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm) { return gs_assemble_C_geo(c, a, c->M, c->xy, Cm); }

@@ -41,6 +41,8 @@ struct AngleData {
     double relres = -1.0;
 };
 
+struct gs_batch;   // batched solves over many geometries (gs_batch.cu)
+
 struct gs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -103,8 +105,12 @@ struct gs_ctx {
     std::vector<int> prof_prec;         // precision of each timed launch
     size_t prof_used = 0;               // events used since the last reset
 
+    gs_batch *batch = nullptr;
+
     int n() const { return M * nc; }
 };
+
+void gs_batch_destroy(gs_ctx *c);
 
 #define GS_COUNT_LAUNCH(ctx) ((ctx)->nlaunch++)
 // returns a (start, stop) event pair for timing one launch, or false when profiling is off
@@ -134,6 +140,12 @@ int gs_angle_scalars(gs_ctx *c, AngleData &a);
 int gs_mie(gs_ctx *c);
 int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B);
 int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm);
+// the same for an explicit geometry (M disks at xy; the multipole order is the context's)
+int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, cplx *s);
+int gs_assemble_B_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *B);
+int gs_assemble_C_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *Cm);
+// per-angle grating factorisation if not built yet (gs_api.cu)
+int gs_ensure_grating(gs_ctx *c);
 // factorisation (gs_svd.cu)
 int gs_factor_angle(gs_ctx *c, AngleData &a);
 // translation (gs_translate.cu)

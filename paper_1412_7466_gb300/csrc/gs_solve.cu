@@ -380,7 +380,10 @@ int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx 
 // FP64: GMRES on L.  GS_C64: iterative refinement with FP64 residuals and inner GMRES on the
 // operator whose translation runs in complex64 (the correction equation L d = r is solved to
 // inner_tol, x += d), until the FP64 relative residual meets tol.
+int gs_ensure_krylov(gs_ctx *c, int restart);
+
 int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0) {
+    GS_TRY(gs_ensure_krylov(c, o.restart));
     const long n = c->n();
     cudaStream_t st = c->stream;
     const int eb = (int)((n + 255) / 256);
