@@ -43,6 +43,10 @@ WORKLOAD = ("headline: M=1000 disks r=0.008 gap 0.004 index 2 (kp=80), p=12 (250
             "3-layer grating y=+-0.5+0.05cos(2pi x), N=256, k=(40,60,80), theta=-pi/5, "
             "A 1904x1689, GMRES tol 1e-11, FP64")
 GOLDEN = os.path.join(ROOT, "tests", "golden", "headline_bragg.txt")
+# DRAM bytes per (target, source image) pair of the table-driven FP64 translation, from the ncu
+# capture of k_translate_f64_tab at M = 500 (599.58 MB over 3 * 500^2 - 500 pairs); the pair table
+# (49 complex128 per pair) is 784 B of it.  Update with a new capture whenever that kernel changes.
+TAB_DRAM_BYTES_PER_PAIR = 599.577344e6 / (3 * 500 ** 2 - 500)
 
 
 def parse():
@@ -204,7 +208,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GratingSolver
+    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GS_PROBE_F32X2, GratingSolver
 
     dist = None
     if world > 1:
@@ -422,7 +426,8 @@ def main():
         gb.close()
 
     peak64 = gs.probe_fma(GS_FP64)
-    peak32 = gs.probe_fma(GS_C64)
+    peak32_scalar = gs.probe_fma(GS_C64)
+    peak32 = gs.probe_fma(GS_PROBE_F32X2)   # the complex64 kernel issues packed two-wide FP32 FMAs
     gs.close()
     if rank != 0:
         if dist:
@@ -464,10 +469,13 @@ def main():
         "grating_factor_ms": grating_ms, "coupling_ms": couple_ms,
         "value_incl_grating_factor": 1.0 / (r64["elapsed"] / args.steps + per_step_grating),
         "pair_translations_per_s": (3 * M * M - M) * n64 / (ms64 * 1e-3) if ms64 > 0 else None,
-        "roofline": {"bound": "alu", "kernel": "k_translate_f64<12>", "achieved": ach64, "peak": peak64,
+        "roofline": {"bound": "alu", "kernel": "k_translate_f64_tab<12>", "achieved": ach64, "peak": peak64,
                      "unit": "TFLOP/s", "frac": ach64 / peak64,
                      "peak_source": "measured: FP64 FMA-chain probe (gs_probe_fma) in this process",
-                     "traffic": None, "flops_per_launch": flops_per_launch, "avg_launch_ms": avg64,
+                     "traffic": TAB_DRAM_BYTES_PER_PAIR * (3 * M * M - M),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_translate_f64_tab "
+                                       "at M=500 (599.6 MB), scaled per launch by the pair count",
+                     "flops_per_launch": flops_per_launch, "avg_launch_ms": avg64,
                      "launches_timed": n64},
         "clocks": r64["clocks"],
         "gpu_launches": r64["launches"],
@@ -479,7 +487,9 @@ def main():
                                  pre_refinement_bragg_rel_err=pre_err,
                                  roofline={"bound": "alu", "kernel": "k_translate_c64<12>", "achieved": ach32,
                                            "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                                           "peak_source": "measured: FP32 FMA-chain probe (gs_probe_fma)",
+                                           "peak_source": "measured: packed FP32 (fma.rn.f32x2) FMA-chain probe "
+                                                          "(gs_probe_fma); scalar FFMA probe "
+                                                          f"{peak32_scalar:.1f} TFLOP/s",
                                            "avg_launch_ms": avg32, "launches_timed": nmx32,
                                            "fp64_residual_launches": nmx64,
                                            "fp64_residual_ms": ms_mx64}),

@@ -176,8 +176,9 @@ int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
  * (NULL = legacy default stream) and is asynchronous.
  * Nothing is allocated: the chunk partials live in a fixed device array of 2^19 complex128 values
  * (8 MiB) compiled into the library, which every GPU that loads the library holds until exit.
- * Sizes: M (2p+1) must not exceed 2^19 (524288) for GS_FP64 and 349525 for GS_C64 (whose complex64
- * copy of beta shares the array), else GS_ERR_ARG is returned before any device work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
+ * Sizes: M (2p+1) must not exceed 2^19 (524288) for GS_FP64; for GS_C64, whose complex64 copy of
+ * beta and float image coordinates share the array, M (2p+1) + ceil(M (2p+1) / 2) + 3M must not
+ * exceed 2^19 (M <= 12945 at p = 12); else GS_ERR_ARG is returned before any device work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
  * precision; GS_ERR_CUDA if the launch fails.  The first call on a device looks up the array's
  * device address (once per device, with that device current); make that first call before any
  * stream capture.  All calls share the one array and it keeps the last call's partials: every
@@ -222,8 +223,10 @@ int gs_profile(gs_ctx *ctx, int enable);
 /* Number of timed translation launches of the given precision (GS_FP64 or GS_C64) and their
  * summed device time in ms (synchronises). */
 int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms);
-/* Measures the FMA throughput of this GPU with independent multiply-add chains (precision GS_FP64
- * or GS_C64 for FP32) over all SMs; writes the achieved TFLOP/s (2 flops per FMA). */
+/* Measures the FMA throughput of this GPU with independent multiply-add chains (precision GS_FP64,
+ * GS_C64 for scalar FP32, or GS_PROBE_F32X2 for packed two-wide FP32 multiply-adds) over all SMs;
+ * writes the achieved TFLOP/s (2 flops per FMA). */
+#define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
 
 #ifdef __cplusplus

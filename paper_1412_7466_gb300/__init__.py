@@ -26,6 +26,7 @@ GS_ERR_NOT_CONVERGED = 6
 GS_ERR_NUMERIC = 7
 GS_FP64 = 0
 GS_C64 = 1
+GS_PROBE_F32X2 = 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)

@@ -92,6 +92,7 @@ void free_geometry(gs_ctx *c) {
     dfree(c->v5);
     dfree(c->part);
     dfree(c->b32);
+    dfree(c->img32);
     dfree(c->htab);
     c->part_elems = 0;
     dfree(c->Vk);
@@ -451,6 +452,8 @@ int gs_factor(gs_ctx *c) {
     c->part_elems = gs_translate_scratch_elems(c->M, c->p);
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     GS_TRY(dalloc(c, &c->b32, n));
+    GS_TRY(dalloc(c, &c->img32, 3 * (size_t)c->M));
+    GS_TRY(gs_build_images_c64(c, c->xy, c->M, c->img32, c->stream));
     c->kdim = 200;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
     GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));

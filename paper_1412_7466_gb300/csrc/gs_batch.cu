@@ -66,21 +66,17 @@ __global__ void k_b_to_c64(const cplx *__restrict__ b, long n, float2 *__restric
     if (e < n) b32[e] = make_float2((float)b[e].x, (float)b[e].y);
 }
 
-__device__ __forceinline__ void split2f(double v, float &hi, float &lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
 template <int P, bool C64>
-__global__ void __launch_bounds__(BW * 32)
+__global__ void __launch_bounds__(BW * 32, (C64 && P <= 12) ? 3 : 1)
 k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, const Geo *__restrict__ geo,
-                  const int *__restrict__ active, const double *__restrict__ xy, const cplx *__restrict__ beta,
-                  const float2 *__restrict__ beta32, double k, double d, cplx alpha, cplx *__restrict__ part) {
+                  const int *__restrict__ active, const double *__restrict__ xy, const float4 *__restrict__ img,
+                  const cplx *__restrict__ beta, const float2 *__restrict__ beta32, double k, double d, cplx alpha,
+                  cplx *__restrict__ part) {
     constexpr int NC = 2 * P + 1;
     typedef typename std::conditional<C64, cplxf_t, cplx>::type T;
-    __shared__ T sb[NC][TILE];
+    __shared__ T sb[NC][TILE + 1];   // +1: the [n][u] stores of the staging loop spread over the banks
     __shared__ double sx[TILE], sy[TILE];
-    __shared__ float sxh[TILE], sxl[TILE], syh[TILE], syl[TILE];
+    __shared__ float4 sg[TILE];
     __shared__ int sid[TILE];
     __shared__ int cur;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -101,17 +97,20 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
         }
         const int i = w.i0 + warp;
         const double *gxy = xy + 2 * (size_t)G.moff;
+        const float4 *gimg = img + 3 * (size_t)G.moff;    // (hi, lo) float image coordinates (C64)
         double xi = 0.0, yi = 0.0;
+        float4 gi = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < G.M) {
-            xi = gxy[2 * i];
-            yi = gxy[2 * i + 1];
+            if constexpr (C64) {
+                gi = gimg[G.M + i];
+            } else {
+                xi = gxy[2 * i];
+                yi = gxy[2 * i + 1];
+            }
         }
-        float xih, xil, yih, yil;
-        split2f(xi, xih, xil);
-        split2f(yi, yih, yil);
-        T acc[NC];
+        T acc[NC], Qa[NC];   // complex64: acc and Qa are the packed accumulators of gs_pair_c64x2
 #pragma unroll
-        for (int m = 0; m < NC; ++m) acc[m] = T{0, 0};
+        for (int m = 0; m < NC; ++m) acc[m] = Qa[m] = T{0, 0};
         for (int t0 = w.s0; t0 < w.s1; t0 += TILE) {
             __syncthreads();
             for (int e = threadIdx.x; e < TILE * NC; e += BW * 32) {
@@ -119,8 +118,8 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
                 int s = t0 + u;
                 T v{0, 0};
                 if (s < w.s1) {
-                    int l = s / G.M - 1;
-                    int j = s - (l + 1) * G.M;
+                    const int l = (s >= G.M) + (s >= 2 * G.M) - 1;   // source image s = (l+1) M + j
+                    const int j = s - (l + 1) * G.M;
                     cplx ph = (l == 0) ? C(1.0, 0.0) : (l == 1 ? alpha : ainv);
                     if constexpr (C64) {
                         float2 b = beta32[(size_t)G.noff + (size_t)j * NC + n];
@@ -134,17 +133,19 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
             for (int u = threadIdx.x; u < TILE; u += BW * 32) {
                 int s = t0 + u;
                 if (s < w.s1) {
-                    int l = s / G.M - 1;
-                    int j = s - (l + 1) * G.M;
-                    sx[u] = gxy[2 * j] + l * d;
-                    sy[u] = gxy[2 * j + 1];
-                    split2f(sx[u], sxh[u], sxl[u]);
-                    split2f(sy[u], syh[u], syl[u]);
+                    const int l = (s >= G.M) + (s >= 2 * G.M) - 1;
+                    const int j = s - (l + 1) * G.M;
+                    if constexpr (C64) {
+                        sg[u] = gimg[s];
+                    } else {
+                        sx[u] = gxy[2 * j] + l * d;
+                        sy[u] = gxy[2 * j + 1];
+                    }
                     sid[u] = (l == 0) ? j : -1;
                 } else {
                     sid[u] = -2;
                     sx[u] = sy[u] = 0.0;
-                    sxh[u] = sxl[u] = syh[u] = syl[u] = 0.f;
+                    sg[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
             __syncthreads();
@@ -155,21 +156,27 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
 #pragma unroll
             for (int n = 0; n < NC; ++n) b[n] = sb[n][lane];
             if constexpr (C64) {
-                gs_pair_c64<P>((xih - sxh[lane]) + (xil - sxl[lane]), (yih - syh[lane]) + (yil - syl[lane]),
-                               (float)k, b, acc);
+                const float4 gs = sg[lane];
+                gs_pair_c64x2<P>((gi.x - gs.x) + (gi.y - gs.y), (gi.z - gs.z) + (gi.w - gs.w), (float)k, b, acc, Qa);
             } else {
                 gs_pair_f64<P>(xi - sx[lane], yi - sy[lane], k, b, acc);
             }
         }
-        double r[2 * NC];
+        if constexpr (C64) {
+            __shared__ float red[BW][2 * NC * 33];
+            T sum[NC];
+            gs_pq_combine<NC>(acc, Qa, sum);
+            gs_warp_sum_c64<NC>(sum, red[warp], lane, (double *)slot, true);
+        } else {
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            r[2 * m] = warp_sum((double)acc[m].x);
-            r[2 * m + 1] = warp_sum((double)acc[m].y);
+            for (int m = 0; m < NC; ++m) {
+                acc[m].x = warp_sum(acc[m].x);
+                acc[m].y = warp_sum(acc[m].y);
+            }
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+                if (lane == (m & 31)) slot[m] = acc[m];
         }
-#pragma unroll
-        for (int m = 0; m < NC; ++m)
-            if (lane == (m & 31)) slot[m] = C(r[2 * m], r[2 * m + 1]);
     }
 }
 
@@ -531,6 +538,7 @@ struct gs_batch {
     // scratch
     cplx *X = nullptr, *Y = nullptr, *T = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *xr = nullptr;
     float2 *b32 = nullptr;
+    float4 *img32 = nullptr;       // (hi, lo) float image coordinates, 3 M_g per geometry at 3 moff_g
     cplx *gC = nullptr, *w = nullptr, *xv = nullptr;   // G nC, G cols, G cols
     int *active = nullptr;
     // GMRES
@@ -576,6 +584,7 @@ void batch_free(gs_batch *b) {
     dfree_b(b->dx);
     dfree_b(b->xr);
     dfree_b(b->b32);
+    dfree_b(b->img32);
     dfree_b(b->gC);
     dfree_b(b->w);
     dfree_b(b->xv);
@@ -646,10 +655,12 @@ int launch_batch_translate(gs_ctx *c, gs_batch *b, const AngleData &a, const cpl
     GS_COUNT_LAUNCH(c);
     if (precision == GS_C64)
         k_batch_translate<P, true><<<sms * b->bpsm, BW * 32, 0, st>>>(b->items, b->n_items, b->counter, b->geo, active,
-                                                                      b->xy, x, b->b32, c->L.k2, c->L.d, a.alpha, b->part);
+                                                                      b->xy, b->img32, x, b->b32, c->L.k2, c->L.d, a.alpha,
+                                                                      b->part);
     else
         k_batch_translate<P, false><<<sms * b->bpsm, BW * 32, 0, st>>>(b->items, b->n_items, b->counter, b->geo, active,
-                                                                       b->xy, x, b->b32, c->L.k2, c->L.d, a.alpha, b->part);
+                                                                       b->xy, b->img32, x, b->b32, c->L.k2, c->L.d, a.alpha,
+                                                                       b->part);
     GS_COUNT_LAUNCH(c);
     k_batch_reduce<<<nblk(b->Ntot), 256, 0, st>>>(b->part, b->Ntot, b->nc, b->tbase, b->tchunks, b->tw, out);
     GS_CHECK_LAUNCH(c);
@@ -1063,6 +1074,10 @@ int gs_factor_batch(gs_ctx *c) {
     GS_TRY(dalloc_b(c, &b->dx, N));
     GS_TRY(dalloc_b(c, &b->xr, N));
     GS_TRY(dalloc_b(c, &b->b32, N));
+    GS_TRY(dalloc_b(c, &b->img32, 3 * (size_t)b->Mtot));
+    for (int g = 0; g < G; ++g)
+        GS_TRY(gs_build_images_c64(c, b->xy + 2 * (size_t)b->moff[g], b->M[g], b->img32 + 3 * (size_t)b->moff[g],
+                                   c->stream));
     GS_TRY(dalloc_b(c, &b->gC, (size_t)G * ly.nC()));
     GS_TRY(dalloc_b(c, &b->w, (size_t)G * ly.cols));
     GS_TRY(dalloc_b(c, &b->xv, (size_t)G * ly.cols));

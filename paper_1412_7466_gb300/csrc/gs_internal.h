@@ -86,6 +86,7 @@ struct gs_ctx {
     cplx *tau = nullptr;                                 // cols, reflector scalars
     cplx *part = nullptr;                                // translation partials
     float2 *b32 = nullptr;                               // n, complex64 copy of the source coefficients
+    float4 *img32 = nullptr;                             // 3M, (hi, lo) float image coordinates
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
     double table_budget_gb = -1.0;                       // < 0: half of the free device memory
     size_t part_elems = 0;
@@ -152,6 +153,8 @@ int gs_factor_angle(gs_ctx *c, AngleData &a);
 int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision);
 size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
+// (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st
+int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st);
 // low-rank, operator, GMRES, Bragg (gs_solve.cu)
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);

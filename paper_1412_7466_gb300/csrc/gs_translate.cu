@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "gs_internal.h"
+#include "gs_pair.cuh"
 
 namespace {
 
@@ -117,22 +118,21 @@ k_translate_f64(const double *__restrict__ xy, int M, const cplx *__restrict__ b
 
 
 // ---- complex64 variant (the inner operator of the mixed-precision solve) --------------------------
-// Same tiling as the FP64 kernel; the pair geometry (dx, dy) is formed in FP64 and rounded, the
-// Hankel seeds come from the single-precision Bessel functions and the recurrence, the Toeplitz
-// products and the per-lane accumulators are FP32; the warp and chunk sums are FP64.  Values stay
-// in their natural scale: for p <= 12 and k R >= 0.5 the largest Hankel order is below 1e36 and the
-// smallest coefficients of interest above the FP32 normal range.
-typedef float2 cplxf;
+// Same tiling as the FP64 kernel, with no FP64 arithmetic inside: the pair offsets come from the
+// (hi, lo) float image coordinates (differences of the hi parts are exact for nearby pairs, so
+// (dx, dy) carry FP32 rounding of the offset itself, not of the coordinates), the Hankel seeds
+// from FP32 polynomial approximations, the recurrence, the Toeplitz products (packed two-wide
+// multiply-adds, gs_pair_c64x2) and the per-lane accumulators are FP32, and the lanes are summed in
+// FP32 through shared memory; only the chunk
+// partials are stored (and summed by k_sum_partials) in FP64.  Values stay in their natural scale:
+// for p <= 12 and k R >= 0.5 the largest Hankel order is below 1e36 and the smallest coefficients
+// of interest above the FP32 normal range.
+typedef cplxf_t cplxf;
 __device__ __forceinline__ cplxf CF(float r, float i) { return make_float2(r, i); }
-__device__ __forceinline__ cplxf cmulf(cplxf a, cplxf b) { return CF(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ void cfmaf(cplxf &acc, cplxf a, cplxf b) {
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(a.y, b.x, acc.y);
-}
+__device__ __forceinline__ cplxf cmulf(cplxf a, cplxf b) { return gs_cmulf(a, b); }
+__device__ __forceinline__ void cfmaf(cplxf &acc, cplxf a, cplxf b) { gs_cfmaf(acc, a, b); }
 
-// beta (complex128) -> complex64 once per call; pair geometry as (hi, lo) float pairs
+// beta (complex128) -> complex64 once per call
 __global__ void k_beta_to_c64(const cplx *__restrict__ b, long n, cplxf *__restrict__ b32) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) b32[e] = CF((float)b[e].x, (float)b[e].y);
@@ -143,109 +143,96 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
     lo = (float)(v - (double)hi);
 }
 
+}  // namespace
+
+// Image coordinates of the complex64 kernels as (hi, lo) float pairs: img[(l+1) M + j] holds
+// x_j + l d and y_j, each split as hi = fl32(v), lo = fl32(v - hi).  Built once per geometry, so the
+// translation itself touches no FP64 value (the FP64 pipe runs at 1/64 of the FP32 rate).
+__global__ void k_images_c64(const double *__restrict__ xy, int M, double d, float4 *__restrict__ img) {
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= 3L * M) return;
+    const int l = (int)(s / M) - 1;
+    const int j = (int)(s - (long)(l + 1) * M);
+    float4 g;
+    split2(xy[2 * j] + l * d, g.x, g.y);
+    split2(xy[2 * j + 1], g.z, g.w);
+    img[s] = g;
+}
+
+int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st) {
+    if (M < 1) return GS_OK;
+    GS_COUNT_LAUNCH(c);
+    k_images_c64<<<(int)((3L * M + 255) / 256), 256, 0, st>>>(xy, M, c->L.d, img);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+namespace {
+
 template <int P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-k_translate_c64(const double *__restrict__ xy, int M, const cplxf *__restrict__ beta32, double k, double d,
-                cplx alpha, int nsplit, cplx *__restrict__ out) {
+__global__ void __launch_bounds__(WARPS * 32, (P <= 12 ? 3 : 1))
+k_translate_c64(const float4 *__restrict__ img, int M, const cplxf *__restrict__ beta32, float k, cplx alpha,
+                int nsplit, cplx *__restrict__ out) {
     constexpr int NC = 2 * P + 1;
-    __shared__ cplxf sb[NC][TILE];
-    __shared__ float sxh[TILE], sxl[TILE], syh[TILE], syl[TILE];
+    __shared__ cplxf sb[NC][TILE + 1];   // +1: the [n][u] stores of the staging loop spread over the banks
+    __shared__ float4 sg[TILE];
     __shared__ int sid[TILE];
     __shared__ cplxf sph[3];
+    __shared__ float red[WARPS][2 * NC * 33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * WARPS + warp;
-    const long total = 3L * M;
-    const long s0 = total * blockIdx.y / nsplit, s1 = total * (blockIdx.y + 1) / nsplit;
-    float xih = 0.f, xil = 0.f, yih = 0.f, yil = 0.f;
-    if (i < M) {
-        split2(xy[2 * i], xih, xil);
-        split2(xy[2 * i + 1], yih, yil);
-    }
+    const long total = 3L * M;   // source images; 3 M < 2^31 (M is an int count of unknowns / (2p+1))
+    const int s0 = (int)(total * blockIdx.y / nsplit), s1 = (int)(total * (blockIdx.y + 1) / nsplit);
+    float4 gi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < M) gi = img[M + i];   // image l = 0
     if (threadIdx.x == 0) {
         sph[0] = CF((float)alpha.x, (float)-alpha.y);   // alpha^{-1} = conj(alpha)
         sph[1] = CF(1.f, 0.f);
         sph[2] = CF((float)alpha.x, (float)alpha.y);
     }
-    cplxf acc[NC];
+    cplxf Pa[NC], Qa[NC];
 #pragma unroll
-    for (int m = 0; m < NC; ++m) acc[m] = CF(0.f, 0.f);
-    const float kf = (float)k;
+    for (int m = 0; m < NC; ++m) Pa[m] = Qa[m] = CF(0.f, 0.f);
 
-    for (long t0 = s0; t0 < s1; t0 += TILE) {
+    for (int t0 = s0; t0 < s1; t0 += TILE) {
         __syncthreads();
         for (int e = threadIdx.x; e < TILE * NC; e += WARPS * 32) {
-            int u = e / NC, n = e - u * NC;
-            long s = t0 + u;
+            const int u = e / NC, n = e - u * NC;
+            const int s = t0 + u;
             cplxf v = CF(0.f, 0.f);
             if (s < s1) {
-                int l = (int)(s / M) - 1;
-                int j = (int)(s - (long)(l + 1) * M);
-                v = cmulf(sph[l + 1], beta32[(size_t)j * NC + n]);
+                const int l1 = (s >= M) + (s >= 2 * M);   // image l + 1 of source image s = (l+1) M + j
+                v = cmulf(sph[l1], beta32[(size_t)(s - l1 * M) * NC + n]);
             }
             sb[n][u] = v;
         }
         for (int u = threadIdx.x; u < TILE; u += WARPS * 32) {
-            long s = t0 + u;
+            const int s = t0 + u;
             if (s < s1) {
-                int l = (int)(s / M) - 1;
-                int j = (int)(s - (long)(l + 1) * M);
-                split2(xy[2 * j] + l * d, sxh[u], sxl[u]);
-                split2(xy[2 * j + 1], syh[u], syl[u]);
+                const int l = (s >= M) + (s >= 2 * M) - 1;
+                const int j = s - (l + 1) * M;
+                sg[u] = img[s];
                 sid[u] = (l == 0) ? j : -1;
             } else {
                 sid[u] = -2;
-                sxh[u] = sxl[u] = syh[u] = syl[u] = 0.f;
+                sg[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         __syncthreads();
         if (i >= M) continue;
-        const long s = t0 + lane;
-        if (s >= s1 || sid[lane] == i) continue;
-        // differences of (hi, lo) pairs: accurate to FP32 rounding of the difference itself
-        const float dx = (xih - sxh[lane]) + (xil - sxl[lane]);
-        const float dy = (yih - syh[lane]) + (yil - syl[lane]);
-        const float R = hypotf(dx, dy);
-        const float z = kf * R;
-        const float twoz = 2.0f / z;
-        cplxf Hm1 = CF(j0f(z), y0f(z)), Hc = CF(j1f(z), y1f(z));
-        const float iR = 1.0f / R;
-        const cplxf u1 = CF(dx * iR, dy * iR);
-        cplxf up = u1;
+        if (t0 + lane >= s1 || sid[lane] == i) continue;
+        const float4 gs = sg[lane];
+        const float dx = (gi.x - gs.x) + (gi.y - gs.y);
+        const float dy = (gi.z - gs.z) + (gi.w - gs.w);
         cplxf b[NC];
 #pragma unroll
         for (int n = 0; n < NC; ++n) b[n] = sb[n][lane];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) cfmaf(acc[m], Hm1, b[m]);
-#pragma unroll
-        for (int q = 1; q <= 2 * P; ++q) {
-            const cplxf hq = cmulf(Hc, up);
-            cplxf hmq = cmulf(Hc, CF(up.x, -up.y));
-            if (q & 1) hmq = CF(-hmq.x, -hmq.y);
-#pragma unroll
-            for (int m = 0; m + q < NC; ++m) cfmaf(acc[m], hq, b[m + q]);
-#pragma unroll
-            for (int m = q; m < NC; ++m) cfmaf(acc[m], hmq, b[m - q]);
-            if (q < 2 * P) {
-                const float f = q * twoz;
-                const cplxf Hn = CF(fmaf(f, Hc.x, -Hm1.x), fmaf(f, Hc.y, -Hm1.y));
-                Hm1 = Hc;
-                Hc = Hn;
-                up = cmulf(up, u1);
-            }
-        }
+        gs_pair_c64x2<P>(dx, dy, k, b, Pa, Qa);
     }
-    double accd[2 * NC];
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-        accd[2 * m] = warp_sum((double)acc[m].x);
-        accd[2 * m + 1] = warp_sum((double)acc[m].y);
-    }
-    if (i < M) {
-        cplx *o = out + ((size_t)blockIdx.y * M + i) * NC;
-#pragma unroll
-        for (int m = 0; m < NC; ++m)
-            if (lane == (m & 31)) o[m] = C(accd[2 * m], accd[2 * m + 1]);
-    }
+    cplxf acc[NC];
+    gs_pq_combine<NC>(Pa, Qa, acc);
+    gs_warp_sum_c64<NC>(acc, red[warp], lane, (double *)(out + ((size_t)blockIdx.y * M + (i < M ? i : 0)) * NC),
+                        i < M);
 }
 
 
@@ -388,8 +375,8 @@ int launch_translate(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out,
     if (timed) cudaEventRecord(e0, c->stream);
     GS_COUNT_LAUNCH(c);
     if (precision == GS_C64)
-        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->xy, M, c->b32, c->L.k2, c->L.d, a.alpha,
-                                                                      nsplit, dst);
+        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->img32, M, c->b32, (float)c->L.k2,
+                                                                      a.alpha, nsplit, dst);
     else if (c->htab)
         k_translate_f64_tab<P, WARPS><<<grid, WARPS * 32, 0, c->stream>>>(c->htab, M, beta, a.alpha, nsplit, dst);
     else
@@ -484,16 +471,19 @@ int noalloc_launch(int M, const double *xy, const cplx *beta, double k, double d
     if ((long)nsplit * 32 > 3L * M) nsplit = (int)((3L * M + 31) / 32);
     if (nsplit < 1) nsplit = 1;
     const long len = (long)M * NC;
-    // complex64 coefficients take the last ceil(len/2) complex128 slots of the array
-    const long room = (precision == GS_C64) ? GS_NOALLOC_CAPACITY - (len + 1) / 2 : GS_NOALLOC_CAPACITY;
-    if (room < len) return GS_ERR_ARG;   // M (2p+1) exceeds the fixed scratch
+    // complex64 form: the converted coefficients take ceil(len/2) complex128 slots at the end of the
+    // array and the (hi, lo) float image coordinates 3M slots before them
+    const long room = (precision == GS_C64) ? GS_NOALLOC_CAPACITY - (len + 1) / 2 - 3L * M : GS_NOALLOC_CAPACITY;
+    if (room < len) return GS_ERR_ARG;   // exceeds the fixed scratch
     if ((long)nsplit * len > room) nsplit = (int)(room / len);
     if (nsplit < 1) return GS_ERR_ARG;
     dim3 grid(gx, nsplit);
     if (precision == GS_C64) {
-        cplxf *b32 = (cplxf *)(scratch + room);
+        float4 *img = (float4 *)(scratch + room);
+        cplxf *b32 = (cplxf *)(scratch + room + 3L * M);
+        k_images_c64<<<(int)((3L * M + 255) / 256), 256, 0, st>>>(xy, M, d, img);
         k_beta_to_c64<<<(int)((len + 255) / 256), 256, 0, st>>>(beta, len, b32);
-        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, st>>>(xy, M, b32, k, d, alpha, nsplit, scratch);
+        k_translate_c64<P, WARPS><<<grid, WARPS * 32, 0, st>>>(img, M, b32, (float)k, alpha, nsplit, scratch);
     } else
         k_translate_f64<P, WARPS><<<grid, WARPS * 32, 0, st>>>(xy, M, beta, k, d, alpha, nsplit, scratch);
     k_sum_partials<<<(int)((len + 255) / 256), 256, 0, st>>>(scratch, nsplit, len, out);
