@@ -229,6 +229,57 @@ int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms)
 #define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
 
+/* ---- learned warm start ----------------------------------------------------------------------
+ * The paper has no learned component: this is an addition to the iterative solve of Sec. 5 that
+ * only chooses where GMRES starts; the converged answer is that of the zero start.
+ * A per-inclusion network with weights shared by all inclusions maps 64 features to the part of the
+ * incoming coefficients (Sec. 4.1: beta_i = s_i (.) alpha_i) that the empty grating's field
+ * w = B_phys A^+ f does not give:
+ *   features X[i][0..63] (FP32): x_i, y_i, sin and cos(2 pi j x_i / d) for j = 1..4 (in that
+ *     order), theta, k1, Re and Im of w_i at order 0 (the empty grating's field at the centre),
+ *     zeros;
+ *   network: x0 = (X - mu) / sd, then Linear 64->128, SiLU, Linear 128->128, SiLU,
+ *     Linear 128->2(2p+1); weights and activations in bfloat16, products accumulated in FP32;
+ *     output row [Re of orders -p..p, Im of orders -p..p];
+ *   start: beta_0 = s (.) (w + scale (.) (Re + i Im)), used only if ||b - L beta_0|| < ||b||.
+ * Parameter vector (FP32, host, in this order): W1[64][128], b1[128], W2[128][128], b2[128],
+ * W3[128][2(2p+1)], b3[2(2p+1)] (the trained weights, W[in][out] row-major), then mu[64], sd[64]
+ * (feature standardisation, sd > 0) and scale[2p+1] (>= 0, per order; 0 leaves that order to the
+ * empty grating's field and makes its target 0).  Device row arrays are row-major FP32 and
+ * caller-owned. */
+/* Length of the parameter vector for multipole order p, or -1 for an unsupported p. */
+int gs_mlp_param_count(int p);
+/* Loads the network for order p (copies the host vector; resets the Adam state).  GS_ERR_ARG for a
+ * wrong length, non-finite values, sd <= 0 or scale < 0. */
+int gs_mlp_set_params(gs_ctx *ctx, int p, const float *params, long n);
+/* Copies the current parameters (trained weights + the fixed mu, sd, scale) to a host vector. */
+int gs_mlp_get_params(gs_ctx *ctx, float *params, long n);
+/* Y_dev[rows][2(2p+1)] = network(X_dev[rows][64]). */
+int gs_mlp_forward(gs_ctx *ctx, const float *X_dev, long rows, float *Y_dev);
+/* Mean squared error of network(X) against Y over all rows and outputs, and (grad_dev non-null)
+ * its gradient with respect to the trained weights, in the parameter order (FP32 device vector of
+ * the weights' length, caller-owned). */
+int gs_mlp_loss_grad(gs_ctx *ctx, const float *X_dev, const float *Y_dev, long rows, float *grad_dev,
+                     double *loss);
+/* One full-batch Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * the FP32 master weights; *loss is the loss before the step. */
+int gs_mlp_train_step(gs_ctx *ctx, const float *X_dev, const float *Y_dev, long rows, double lr, double *loss);
+/* Features of the current geometry at `angle` into X_dev[M][64] (needs gs_factor and a network of
+ * the context's order). */
+int gs_ws_features(gs_ctx *ctx, int angle, float *X_dev);
+/* Training targets from the last solution at `angle`: Y_dev[M][2(2p+1)] = t / scale split as
+ * [Re, Im], t = T beta - B_phys A^+ C beta (the incoming field from the other inclusions, their
+ * images and the layers' response; equal to beta/s - w at a converged beta). */
+int gs_ws_targets(gs_ctx *ctx, int angle, float *Y_dev);
+/* From the last solution at `angle`, per order n (t as for gs_ws_targets): ms_host[n] = mean over
+ * the inclusions of |t_n|^2 and ms_host[2p+1 + n] = mean of |s_n t_n|^2 (the order's share of
+ * beta), 2(2p+1) values, to choose `scale`. */
+int gs_ws_moments(gs_ctx *ctx, int angle, double *ms_host);
+/* The warm start at `angle`: writes beta_0 (or zeros when ||b - L beta_0|| >= ||b||, FP64 check)
+ * to beta0_dev (n complex128, caller-owned), its relative residual to *relres0 and 1/0 to *used.
+ * Pass beta0_dev to gs_solve. */
+int gs_warm_start(gs_ctx *ctx, int angle, gs_c128 *beta0_dev, double *relres0, int *used);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,16 @@ _SIGS = {
     "gs_batch_tuning": (ctypes.c_int, [_vp, _ip, _ip]),
     "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
+    "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
+    "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
+    "gs_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
+    "gs_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_long, _vp]),
+    "gs_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_long, _vp, _dp]),
+    "gs_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_long, ctypes.c_double, _dp]),
+    "gs_ws_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_ws_targets": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "gs_ws_moments": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "gs_warm_start": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _dp, _ip]),
 }
 
 _lib = None
@@ -379,6 +389,80 @@ class GratingSolver:
         self._check(self.lib.gs_profile_read(self.ctx, precision, ctypes.byref(n), ctypes.byref(ms)),
                     "gs_profile_read")
         return n.value, ms.value
+
+    # -- learned warm start ---------------------------------------------------------------------
+    def _fdev(self, x, cols):
+        t = self.torch.as_tensor(x).to(device=self.device, dtype=self.torch.float32).contiguous()
+        if t.dim() != 2 or t.shape[1] != cols:
+            raise ValueError(f"expected a (rows, {cols}) array")
+        return t
+
+    def mlp_param_count(self, p):
+        n = self.lib.gs_mlp_param_count(int(p))
+        if n < 0:
+            raise ValueError("unsupported multipole order")
+        return n
+
+    def mlp_set_params(self, p, params):
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        self._check(self.lib.gs_mlp_set_params(self.ctx, int(p), a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               a.size), "gs_mlp_set_params")
+        self._mlp_p = int(p)
+
+    def mlp_get_params(self):
+        a = np.empty(self.mlp_param_count(self._mlp_p), dtype=np.float32)
+        self._check(self.lib.gs_mlp_get_params(self.ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+                    "gs_mlp_get_params")
+        return a
+
+    def mlp_forward(self, X):
+        X = self._fdev(X, 64)
+        Y = self.torch.empty(X.shape[0], 2 * (2 * self._mlp_p + 1), dtype=self.torch.float32, device=self.device)
+        self._check(self.lib.gs_mlp_forward(self.ctx, _ptr(X), X.shape[0], _ptr(Y)), "gs_mlp_forward")
+        return Y
+
+    def mlp_loss_grad(self, X, Y):
+        X, Y = self._fdev(X, 64), self._fdev(Y, 2 * (2 * self._mlp_p + 1))
+        nw = self.mlp_param_count(self._mlp_p) - 128 - (2 * self._mlp_p + 1)
+        g = self.torch.empty(nw, dtype=self.torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        self._check(self.lib.gs_mlp_loss_grad(self.ctx, _ptr(X), _ptr(Y), X.shape[0], _ptr(g), ctypes.byref(loss)),
+                    "gs_mlp_loss_grad")
+        return loss.value, g
+
+    def mlp_train_step(self, X, Y, lr):
+        """One Adam step; X, Y must already be float32 device tensors of shapes (rows, 64), (rows, 2(2p+1))."""
+        loss = ctypes.c_double()
+        self._check(self.lib.gs_mlp_train_step(self.ctx, _ptr(X), _ptr(Y), X.shape[0], float(lr), ctypes.byref(loss)),
+                    "gs_mlp_train_step")
+        return loss.value
+
+    def ws_features(self, angle=0):
+        X = self.torch.empty(self.dims()["n"] // (2 * self._mlp_p + 1), 64, dtype=self.torch.float32,
+                             device=self.device)
+        self._check(self.lib.gs_ws_features(self.ctx, angle, _ptr(X)), "gs_ws_features")
+        return X
+
+    def ws_targets(self, angle=0):
+        nc = 2 * self._mlp_p + 1
+        Y = self.torch.empty(self.dims()["n"] // nc, 2 * nc, dtype=self.torch.float32, device=self.device)
+        self._check(self.lib.gs_ws_targets(self.ctx, angle, _ptr(Y)), "gs_ws_targets")
+        return Y
+
+    def ws_moments(self, angle=0):
+        """(mean |t_n|^2, mean |s_n t_n|^2) per order from the last solution."""
+        ms = np.empty(2 * (2 * self._mlp_p + 1))
+        self._check(self.lib.gs_ws_moments(self.ctx, angle, ms.ctypes.data_as(_dp)), "gs_ws_moments")
+        nc = 2 * self._mlp_p + 1
+        return ms[:nc], ms[nc:]
+
+    def warm_start(self, angle=0):
+        """(beta_0 device tensor, its relative residual, used); beta_0 is zero when not used."""
+        b0 = self._cvec(self.dims()["n"])
+        rel, used = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.gs_warm_start(self.ctx, angle, _ptr(b0), ctypes.byref(rel), ctypes.byref(used)),
+                    "gs_warm_start")
+        return b0, rel.value, bool(used.value)
 
     def probe_fma(self, precision=GS_FP64):
         v = ctypes.c_double()

@@ -252,6 +252,7 @@ void gs_destroy(gs_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    gs_mlp_destroy(c);
     free_factor(c);
     for (int q = 0; q < 2; ++q) dfree(c->curve[q]);
     for (int q = 0; q < 3; ++q) dfree(c->wall_y[q]);

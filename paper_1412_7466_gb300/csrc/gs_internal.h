@@ -42,6 +42,7 @@ struct AngleData {
 };
 
 struct gs_batch;   // batched solves over many geometries (gs_batch.cu)
+struct gs_mlp;     // network of the learned warm start (gs_warm.cu)
 
 struct gs_ctx {
     int device = 0;
@@ -107,11 +108,13 @@ struct gs_ctx {
     size_t prof_used = 0;               // events used since the last reset
 
     gs_batch *batch = nullptr;
+    gs_mlp *mlp = nullptr;
 
     int n() const { return M * nc; }
 };
 
 void gs_batch_destroy(gs_ctx *c);
+void gs_mlp_destroy(gs_ctx *c);
 
 #define GS_COUNT_LAUNCH(ctx) ((ctx)->nlaunch++)
 // returns a (start, stop) event pair for timing one launch, or false when profiling is off
@@ -159,5 +162,9 @@ int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStr
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);
 int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b);
+// w = B_phys A^+ f: incoming coefficients of the empty grating's field about every centre
+int gs_incoming_impl(gs_ctx *c, const AngleData &a, cplx *w);
+// z = B_phys A^+ C x: the layer response to the inclusions' field (no scattering diagonal)
+int gs_layer_response_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *z);
 int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0);
 int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux);

@@ -56,7 +56,7 @@ __global__ void k_B_combine(const cplx *__restrict__ B, int n, int nB, const cpl
     if (lane == 0) {
         cplx r = x ? x[warp] : C(0, 0);
         if (t) r = csub(r, cmul(s[warp], t[warp]));
-        r = cadd(r, cmul(s[warp], acc));
+        r = cadd(r, s ? cmul(s[warp], acc) : acc);
         y[warp] = r;
     }
 }
@@ -263,8 +263,26 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
     return GS_OK;
 }
 
+// z = B_phys A^+ C x (the layer response to the inclusions' field, without the diagonal s)
+int gs_layer_response_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *z) {
+    const Layout &ly = c->lay;
+    int n = c->n(), nB = ly.nB(), nC = ly.nC();
+    GS_COUNT_LAUNCH(c);
+    k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+    GS_COUNT_LAUNCH(c);
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
+    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    GS_COUNT_LAUNCH(c);
+    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, nullptr, nullptr, nullptr, z);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
 // b = s .* (B_phys A^+ f); f vanishes outside the Gamma1 rows
-int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
+namespace {
+// y = [s (.)] B_phys A^+ f (s null: no scattering diagonal)
+int incoming_f(gs_ctx *c, const AngleData &a, const cplx *s, cplx *y) {
     const Layout &ly = c->lay;
     int n = c->n(), nB = ly.nB();
     GS_COUNT_LAUNCH(c);
@@ -272,10 +290,15 @@ int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
     GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
     GS_COUNT_LAUNCH(c);
-    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, nullptr, nullptr, c->s, b);
+    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, nullptr, nullptr, s, y);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
+}  // namespace
+
+int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) { return incoming_f(c, a, c->s, b); }
+
+int gs_incoming_impl(gs_ctx *c, const AngleData &a, cplx *w) { return incoming_f(c, a, nullptr, w); }
 
 namespace {
 

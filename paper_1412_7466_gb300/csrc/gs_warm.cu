@@ -1,0 +1,721 @@
+// Learned warm start of the inclusion solve.  The paper has no learned component: this is an
+// addition to the iterative solve of Sec. 5 that only changes where GMRES starts.
+//
+//  * Features of inclusion i (64 floats): x, y; sin and cos of 2 pi j x / d, j = 1..4; theta; k1;
+//    Re and Im of the empty grating's field at the centre, which is the n = 0 entry of the incoming
+//    coefficients w = B_phys A^+ f (J_n(0) = delta_n0); zeros up to 64.
+//  * Network: x0 = (X - mu) / sd, Linear 64->128, SiLU, Linear 128->128, SiLU, Linear 128->2(2p+1);
+//    weights and activations stored in bfloat16, every product accumulated in FP32, the loss
+//    gradient, Adam moments and master weights in FP32.
+//  * Start: beta_0 = s (.) (w + scale (.) (Re + i Im) of the output) (scale_n = 0: order n is left
+//    to the empty grating's field), kept only if
+//    ||b - L beta_0|| < ||b|| (FP64), else the zero start; training targets are
+//    (T beta - B_phys A^+ C beta) / scale from converged solutions (= beta / s - w there).
+//
+// The GEMMs are small (rows = inclusions x solves, widths 64-128): plain shared-memory tiles of
+// 64 x 64 outputs per 256-thread block, 4 x 4 outputs per thread, FP32 FMAs.  Weight gradients are
+// summed per chunk of rows and the chunks added in a fixed order (deterministic).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gs_internal.h"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int NIN = 64, NHID = 128;
+constexpr int BM = 64, BN = 64, BK = 32;    // GEMM tile
+constexpr int WG_CHUNK = 512;               // rows per weight-gradient partial
+
+struct Offs {
+    long W1, b1, W2, b2, W3, b3, n;         // in the flat FP32 weights
+    long bW1, bW2, bW3, bn;                 // in the bfloat16 copies
+};
+Offs offsets(int no) {
+    Offs o;
+    o.W1 = 0;
+    o.b1 = o.W1 + (long)NIN * NHID;
+    o.W2 = o.b1 + NHID;
+    o.b2 = o.W2 + (long)NHID * NHID;
+    o.W3 = o.b2 + NHID;
+    o.b3 = o.W3 + (long)NHID * no;
+    o.n = o.b3 + no;
+    o.bW1 = 0;
+    o.bW2 = (long)NIN * NHID;
+    o.bW3 = o.bW2 + (long)NHID * NHID;
+    o.bn = o.bW3 + (long)NHID * no;
+    return o;
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+    const float g = 1.0f / (1.0f + expf(-z));
+    return g * (1.0f + z * (1.0f - g));
+}
+__device__ __forceinline__ float ld(const float *p) { return *p; }
+__device__ __forceinline__ float ld(const bf16 *p) { return __bfloat162float(*p); }
+
+// x0 = bf16((X - mu) / sd)
+__global__ void k_standardize(const float *__restrict__ X, long rows, const float *__restrict__ norm,
+                              bf16 *__restrict__ x0) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * NIN) return;
+    const int k = (int)(e % NIN);
+    x0[e] = __float2bfloat16_rn((X[e] - norm[k]) / norm[NIN + k]);
+}
+
+// Y[r][o] = sum_k A[r][k] W[k][o] + bias[o] (A rows x K, W K x O, both bfloat16); act: store
+// Z = Y (FP32) and silu(Y) as bfloat16 in Abf; else store Y (FP32) in Out.
+__global__ void __launch_bounds__(256)
+k_fwd(const bf16 *__restrict__ A, long rows, int K, const bf16 *__restrict__ W, const float *__restrict__ bias,
+      int O, int act, float *__restrict__ Z, bf16 *__restrict__ Abf, float *__restrict__ Out) {
+    __shared__ float As[BK][BM + 1], Ws[BK][BN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long r0 = (long)blockIdx.x * BM;
+    const int c0 = blockIdx.y * BN;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            const int r = e / BK, k = e % BK;
+            As[k][r] = (r0 + r < rows && k0 + k < K) ? ld(A + (r0 + r) * K + k0 + k) : 0.f;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += 256) {
+            const int k = e / BN, n = e % BN;
+            Ws[k][n] = (k0 + k < K && c0 + n < O) ? ld(W + (long)(k0 + k) * O + c0 + n) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < BK; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Ws[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long r = r0 + ty * 4 + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tx * 4 + j;
+            if (c >= O) continue;
+            const float y = acc[i][j] + bias[c];
+            if (act) {
+                Z[r * O + c] = y;
+                Abf[r * O + c] = __float2bfloat16_rn(silu_f(y));
+            } else {
+                Out[r * O + c] = y;
+            }
+        }
+    }
+}
+
+// Gp[r][k] = (sum_o G[r][o] W[k][o]) silu'(Z[r][k])  (G rows x O FP32, W K x O bfloat16)
+__global__ void __launch_bounds__(256)
+k_bwd_data(const float *__restrict__ G, long rows, int O, const bf16 *__restrict__ W, int K,
+           const float *__restrict__ Z, float *__restrict__ Gp) {
+    __shared__ float Gs[BK][BM + 1], Ws[BK][BN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long r0 = (long)blockIdx.x * BM;
+    const int c0 = blockIdx.y * BN;
+    float acc[4][4] = {};
+    for (int o0 = 0; o0 < O; o0 += BK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            const int r = e / BK, o = e % BK;
+            Gs[o][r] = (r0 + r < rows && o0 + o < O) ? G[(r0 + r) * O + o0 + o] : 0.f;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += 256) {
+            const int n = e / BK, o = e % BK;
+            Ws[o][n] = (o0 + o < O && c0 + n < K) ? __bfloat162float(W[(long)(c0 + n) * O + o0 + o]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int o = 0; o < BK; ++o) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Gs[o][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Ws[o][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long r = r0 + ty * 4 + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tx * 4 + j;
+            if (c >= K) continue;
+            Gp[r * K + c] = acc[i][j] * dsilu_f(Z[r * K + c]);
+        }
+    }
+}
+
+// part[chunk][k * O + o] = sum over the chunk's rows of A[r][k] G[r][o]; part[chunk][K O + o] =
+// sum of G[r][o] (bias), written by the blocks with blockIdx.x == 0
+__global__ void __launch_bounds__(256)
+k_wgrad(const bf16 *__restrict__ A, const float *__restrict__ G, long rows, int K, int O, float *__restrict__ part) {
+    __shared__ float As[BK][BM + 1], Gs[BK][BN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int k0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
+    const long rb = (long)blockIdx.z * WG_CHUNK, re = std::min(rows, rb + WG_CHUNK);
+    float acc[4][4] = {};
+    float bsum = 0.f;
+    for (long q0 = rb; q0 < re; q0 += BK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < BK * BM; e += 256) {
+            const int r = e / BM, k = e % BM;
+            As[r][k] = (q0 + r < re && k0 + k < K) ? __bfloat162float(A[(q0 + r) * K + k0 + k]) : 0.f;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += 256) {
+            const int r = e / BN, o = e % BN;
+            Gs[r][o] = (q0 + r < re && o0 + o < O) ? G[(q0 + r) * O + o0 + o] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < BK; ++r) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[r][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Gs[r][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (blockIdx.x == 0 && threadIdx.x < BN) {
+            for (int r = 0; r < BK; ++r) bsum += Gs[r][threadIdx.x];
+        }
+    }
+    float *P = part + (size_t)blockIdx.z * ((size_t)K * O + O);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = k0 + ty * 4 + i;
+        if (k >= K) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = o0 + tx * 4 + j;
+            if (o < O) P[(long)k * O + o] = acc[i][j];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < BN && o0 + threadIdx.x < O) P[(long)K * O + o0 + threadIdx.x] = bsum;
+}
+
+// dst[e] = sum_c part[c][e] in chunk order; the first K O values are the weight gradient (to dW),
+// the last O the bias gradient (to db)
+__global__ void k_sum_chunks(const float *__restrict__ part, int nch, int K, int O, float *__restrict__ dW,
+                             float *__restrict__ db) {
+    const long len = (long)K * O + O;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    float s = 0.f;
+    for (int c = 0; c < nch; ++c) s += part[(size_t)c * len + e];
+    if (e < (long)K * O)
+        dW[e] = s;
+    else
+        db[e - (long)K * O] = s;
+}
+
+// G = (2 / n) (out - Y); lpart[block] = sum of (out - Y)^2 over the block's elements (FP64)
+__global__ void k_loss_grad(const float *__restrict__ out, const float *__restrict__ Y, long n, float *__restrict__ G,
+                            double *__restrict__ lpart) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    const float c = 2.0f / (float)n;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float dlt = out[e] - Y[e];
+        G[e] = c * dlt;
+        s += (double)dlt * dlt;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) lpart[blockIdx.x] = s;
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float mm = b1 * m[e] + (1.f - b1) * g[e];
+    const float vv = b2 * v[e] + (1.f - b2) * g[e] * g[e];
+    m[e] = mm;
+    v[e] = vv;
+    w[e] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+}
+
+// bfloat16 copies of W1, W2, W3
+__global__ void k_refresh_bf16(const float *__restrict__ w, long oW1, long oW2, long oW3, long n1, long n2, long n3,
+                               bf16 *__restrict__ wb) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n1)
+        wb[e] = __float2bfloat16_rn(w[oW1 + e]);
+    else if (e < n1 + n2)
+        wb[e] = __float2bfloat16_rn(w[oW2 + e - n1]);
+    else if (e < n1 + n2 + n3)
+        wb[e] = __float2bfloat16_rn(w[oW3 + e - n1 - n2]);
+}
+
+__global__ void k_ws_features(const double *__restrict__ xy, int M, double theta, double k1, double d,
+                              const cplx *__restrict__ w, int nc, int p, float *__restrict__ X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    float *f = X + (size_t)i * NIN;
+    f[0] = (float)x;
+    f[1] = (float)y;
+    for (int j = 1; j <= 4; ++j) {
+        double s, c;
+        sincospi(2.0 * j * x / d, &s, &c);
+        f[2 * j] = (float)s;
+        f[2 * j + 1] = (float)c;
+    }
+    f[10] = (float)theta;
+    f[11] = (float)k1;
+    const cplx w0 = w[(size_t)i * nc + p];
+    f[12] = (float)w0.x;
+    f[13] = (float)w0.y;
+    for (int k = 14; k < NIN; ++k) f[k] = 0.f;
+}
+
+// training target t = T beta - B_phys A^+ C beta: the incoming field about each centre from the
+// other inclusions, their images and the layers' response (at a converged beta, beta = s (.) (w + t);
+// t is formed from its two products rather than as beta / s - w, which loses all digits where s is
+// tiny)
+__global__ void k_ws_targets(const cplx *__restrict__ tb, const cplx *__restrict__ zb, const float *__restrict__ scale,
+                             int M, int nc, float *__restrict__ Y) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * nc) return;
+    const int i = (int)(e / nc), n = (int)(e % nc);
+    const cplx t = csub(tb[e], zb[e]);
+    const double sc = scale[n];   // 0: order not predicted (target 0)
+    Y[(size_t)i * 2 * nc + n] = sc > 0.0 ? (float)(t.x / sc) : 0.f;
+    Y[(size_t)i * 2 * nc + nc + n] = sc > 0.0 ? (float)(t.y / sc) : 0.f;
+}
+
+// ms[n] = mean over the inclusions of |t|^2 and ms[nc + n] = mean of |s t|^2 at order n (one block
+// per order)
+__global__ void k_ws_moments(const cplx *__restrict__ tb, const cplx *__restrict__ zb, const cplx *__restrict__ s,
+                             int M, int nc, double *__restrict__ ms) {
+    __shared__ double sh[32];
+    const int n = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const long e = (long)i * nc + n;
+        const cplx t = csub(tb[e], zb[e]);
+        a += cabs2(t);
+        b += cabs2(cmul(s[e], t));
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        ms[n] = a / M;
+        ms[nc + n] = b / M;
+    }
+}
+
+__global__ void k_ws_guess(const float *__restrict__ out, const cplx *__restrict__ w, const cplx *__restrict__ s,
+                           const float *__restrict__ scale, int M, int nc, cplx *__restrict__ beta0) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * nc) return;
+    const int i = (int)(e / nc), n = (int)(e % nc);
+    const double sc = scale[n];
+    const cplx a = cadd(w[e], C(sc * out[(size_t)i * 2 * nc + n], sc * out[(size_t)i * 2 * nc + nc + n]));
+    beta0[e] = cmul(s[e], a);
+}
+
+// out[0] = ||b - y||^2, out[1] = ||b||^2
+__global__ void k_res_norms(const cplx *__restrict__ b, const cplx *__restrict__ y, long n, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double r = 0.0, q = 0.0;
+    for (long e = threadIdx.x; e < n; e += blockDim.x) {
+        r += cabs2(csub(b[e], y[e]));
+        q += cabs2(b[e]);
+    }
+    r = block_sum(r, sh);
+    q = block_sum(q, sh);
+    if (threadIdx.x == 0) {
+        out[0] = r;
+        out[1] = q;
+    }
+}
+
+template <typename T>
+int walloc(gs_ctx *c, T **p, size_t n) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * n);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (warm start): ") + cudaGetErrorString(e));
+    }
+    return GS_OK;
+}
+template <typename T>
+void wfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+inline int nblk(long n, int t = 256) { return (int)((n + t - 1) / t); }
+
+bool valid_p(int p) {
+    switch (p) {
+        case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 10: case 12: case 16: return true;
+        default: return false;
+    }
+}
+
+}  // namespace
+
+struct gs_mlp {
+    int p = -1, nc = 0, no = 0;
+    Offs off{};
+    float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    float *norm = nullptr;         // mu[64], sd[64], scale[nc]
+    bf16 *wb = nullptr;            // W1, W2, W3 in bfloat16
+    int t = 0;                     // Adam steps taken
+    long cap = 0;                  // rows of the activation buffers
+    bf16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr;
+    float *z1 = nullptr, *z2 = nullptr, *out = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+    float *part = nullptr;
+    size_t part_elems = 0;
+    double *lpart = nullptr, *lhost = nullptr;
+    float *X = nullptr;            // features of one geometry (M x 64)
+    cplx *w = nullptr, *t1 = nullptr, *t2 = nullptr;   // n each
+    long nvec = 0;
+};
+
+void gs_mlp_destroy(gs_ctx *c) {
+    gs_mlp *q = c->mlp;
+    if (!q) return;
+    wfree(q->master); wfree(q->m); wfree(q->v); wfree(q->grad); wfree(q->norm); wfree(q->wb);
+    wfree(q->x0); wfree(q->a1); wfree(q->a2); wfree(q->z1); wfree(q->z2); wfree(q->out);
+    wfree(q->g3); wfree(q->g2); wfree(q->g1); wfree(q->part); wfree(q->lpart); wfree(q->X);
+    wfree(q->w); wfree(q->t1); wfree(q->t2);
+    if (q->lhost) cudaFreeHost(q->lhost);
+    delete q;
+    c->mlp = nullptr;
+}
+
+namespace {
+
+int guard(gs_ctx *c) {
+    if (!c) return GS_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, cudaGetErrorString(e));
+    return GS_OK;
+}
+
+int need_model(gs_ctx *c) {
+    if (!c->mlp) return gs_fail(c, GS_ERR_STATE, "gs_mlp_set_params has not run");
+    return GS_OK;
+}
+
+int ensure_rows(gs_ctx *c, long rows) {
+    gs_mlp *q = c->mlp;
+    if (rows <= q->cap) return GS_OK;
+    const long r = std::max(rows, 1024L);
+    GS_TRY(walloc(c, &q->x0, (size_t)r * NIN));
+    GS_TRY(walloc(c, &q->a1, (size_t)r * NHID));
+    GS_TRY(walloc(c, &q->a2, (size_t)r * NHID));
+    GS_TRY(walloc(c, &q->z1, (size_t)r * NHID));
+    GS_TRY(walloc(c, &q->z2, (size_t)r * NHID));
+    GS_TRY(walloc(c, &q->out, (size_t)r * q->no));
+    GS_TRY(walloc(c, &q->g3, (size_t)r * q->no));
+    GS_TRY(walloc(c, &q->g2, (size_t)r * NHID));
+    GS_TRY(walloc(c, &q->g1, (size_t)r * NHID));
+    const long nch = (r + WG_CHUNK - 1) / WG_CHUNK;
+    q->part_elems = (size_t)nch * ((size_t)NHID * NHID + NHID);
+    GS_TRY(walloc(c, &q->part, q->part_elems));
+    q->cap = r;
+    return GS_OK;
+}
+
+int ensure_vectors(gs_ctx *c) {
+    gs_mlp *q = c->mlp;
+    const long n = c->n();
+    if (q->nvec == n && q->X) return GS_OK;
+    GS_TRY(walloc(c, &q->w, n));
+    GS_TRY(walloc(c, &q->t1, n));
+    GS_TRY(walloc(c, &q->t2, n));
+    GS_TRY(walloc(c, &q->X, (size_t)c->M * NIN));
+    q->nvec = n;
+    return GS_OK;
+}
+
+// forward pass of `rows` standardised feature rows into q->out (FP32)
+int forward(gs_ctx *c, const float *X, long rows) {
+    gs_mlp *q = c->mlp;
+    cudaStream_t st = c->stream;
+    GS_TRY(ensure_rows(c, rows));
+    const int gr = (int)((rows + BM - 1) / BM);
+    GS_COUNT_LAUNCH(c);
+    k_standardize<<<nblk(rows * NIN), 256, 0, st>>>(X, rows, q->norm, q->x0);
+    GS_COUNT_LAUNCH(c);
+    k_fwd<<<dim3(gr, NHID / BN), 256, 0, st>>>(q->x0, rows, NIN, q->wb + q->off.bW1, q->master + q->off.b1, NHID, 1,
+                                               q->z1, q->a1, nullptr);
+    GS_COUNT_LAUNCH(c);
+    k_fwd<<<dim3(gr, NHID / BN), 256, 0, st>>>(q->a1, rows, NHID, q->wb + q->off.bW2, q->master + q->off.b2, NHID, 1,
+                                               q->z2, q->a2, nullptr);
+    GS_COUNT_LAUNCH(c);
+    k_fwd<<<dim3(gr, (q->no + BN - 1) / BN), 256, 0, st>>>(q->a2, rows, NHID, q->wb + q->off.bW3, q->master + q->off.b3,
+                                                           q->no, 0, nullptr, nullptr, q->out);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+int wgrad(gs_ctx *c, const bf16 *A, const float *G, long rows, int K, int O, float *dW, float *db) {
+    gs_mlp *q = c->mlp;
+    cudaStream_t st = c->stream;
+    const int nch = (int)((rows + WG_CHUNK - 1) / WG_CHUNK);
+    GS_COUNT_LAUNCH(c);
+    k_wgrad<<<dim3((K + BM - 1) / BM, (O + BN - 1) / BN, nch), 256, 0, st>>>(A, G, rows, K, O, q->part);
+    GS_COUNT_LAUNCH(c);
+    k_sum_chunks<<<nblk((long)K * O + O), 256, 0, st>>>(q->part, nch, K, O, dW, db);
+    return GS_OK;
+}
+
+// loss (mean squared error) and the weight gradient into q->grad
+int loss_grad(gs_ctx *c, const float *X, const float *Y, long rows, double *loss) {
+    gs_mlp *q = c->mlp;
+    cudaStream_t st = c->stream;
+    GS_TRY(forward(c, X, rows));
+    const long n = rows * q->no;
+    const int lb = 152;
+    GS_COUNT_LAUNCH(c);
+    k_loss_grad<<<lb, 256, 0, st>>>(q->out, Y, n, q->g3, q->lpart);
+    const int gr = (int)((rows + BM - 1) / BM);
+    float *g = q->grad;
+    GS_TRY(wgrad(c, q->a2, q->g3, rows, NHID, q->no, g + q->off.W3, g + q->off.b3));
+    GS_COUNT_LAUNCH(c);
+    k_bwd_data<<<dim3(gr, NHID / BN), 256, 0, st>>>(q->g3, rows, q->no, q->wb + q->off.bW3, NHID, q->z2, q->g2);
+    GS_TRY(wgrad(c, q->a1, q->g2, rows, NHID, NHID, g + q->off.W2, g + q->off.b2));
+    GS_COUNT_LAUNCH(c);
+    k_bwd_data<<<dim3(gr, NHID / BN), 256, 0, st>>>(q->g2, rows, NHID, q->wb + q->off.bW2, NHID, q->z1, q->g1);
+    GS_TRY(wgrad(c, q->x0, q->g1, rows, NIN, NHID, g + q->off.W1, g + q->off.b1));
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(q->lhost, q->lpart, sizeof(double) * lb, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int b = 0; b < lb; ++b) s += q->lhost[b];
+    if (loss) *loss = s / (double)n;
+    return GS_OK;
+}
+
+int refresh_bf16(gs_ctx *c) {
+    gs_mlp *q = c->mlp;
+    const long n1 = (long)NIN * NHID, n2 = (long)NHID * NHID, n3 = (long)NHID * q->no;
+    GS_COUNT_LAUNCH(c);
+    k_refresh_bf16<<<nblk(n1 + n2 + n3), 256, 0, c->stream>>>(q->master, q->off.W1, q->off.W2, q->off.W3, n1, n2, n3,
+                                                              q->wb);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+int angle_ready(gs_ctx *c, int angle) {
+    if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
+    if (angle < 0 || angle >= (int)c->ang.size()) return gs_fail(c, GS_ERR_ARG, "angle index out of range");
+    if (!c->mlp || c->mlp->p != c->p)
+        return gs_fail(c, GS_ERR_STATE, "no network for this multipole order (gs_mlp_set_params)");
+    return ensure_vectors(c);
+}
+
+}  // namespace
+
+extern "C" int gs_mlp_param_count(int p) {
+    if (!valid_p(p)) return -1;
+    const Offs o = offsets(2 * (2 * p + 1));
+    return (int)(o.n + 2 * NIN + (2 * p + 1));
+}
+
+extern "C" int gs_mlp_set_params(gs_ctx *c, int p, const float *params, long n) {
+    GS_TRY(guard(c));
+    if (!params || !valid_p(p)) return gs_fail(c, GS_ERR_ARG, "null parameters or unsupported p");
+    if (n != gs_mlp_param_count(p)) return gs_fail(c, GS_ERR_ARG, "parameter count does not match p");
+    const int nc = 2 * p + 1;
+    for (long e = 0; e < n; ++e)
+        if (!std::isfinite(params[e])) return gs_fail(c, GS_ERR_ARG, "non-finite parameter");
+    const Offs o = offsets(2 * nc);
+    for (int k = 0; k < NIN; ++k)
+        if (!(params[o.n + NIN + k] > 0.f)) return gs_fail(c, GS_ERR_ARG, "sd must be positive");
+    for (int k = 0; k < nc; ++k)
+        if (!(params[o.n + 2 * NIN + k] >= 0.f)) return gs_fail(c, GS_ERR_ARG, "scale must be >= 0");
+    if (c->mlp && c->mlp->p != p) gs_mlp_destroy(c);
+    if (!c->mlp) {
+        c->mlp = new gs_mlp();
+        gs_mlp *q = c->mlp;
+        q->p = p;
+        q->nc = nc;
+        q->no = 2 * nc;
+        q->off = o;
+        GS_TRY(walloc(c, &q->master, o.n));
+        GS_TRY(walloc(c, &q->m, o.n));
+        GS_TRY(walloc(c, &q->v, o.n));
+        GS_TRY(walloc(c, &q->grad, o.n));
+        GS_TRY(walloc(c, &q->norm, 2 * NIN + nc));
+        GS_TRY(walloc(c, &q->wb, o.bn));
+        GS_TRY(walloc(c, &q->lpart, 152));
+        GS_CUDA(c, cudaMallocHost((void **)&q->lhost, sizeof(double) * 152));
+    }
+    gs_mlp *q = c->mlp;
+    GS_CUDA(c, cudaMemcpyAsync(q->master, params, sizeof(float) * o.n, cudaMemcpyHostToDevice, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(q->norm, params + o.n, sizeof(float) * (2 * NIN + nc), cudaMemcpyHostToDevice,
+                               c->stream));
+    GS_CUDA(c, cudaMemsetAsync(q->m, 0, sizeof(float) * o.n, c->stream));
+    GS_CUDA(c, cudaMemsetAsync(q->v, 0, sizeof(float) * o.n, c->stream));
+    q->t = 0;
+    GS_TRY(refresh_bf16(c));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_get_params(gs_ctx *c, float *params, long n) {
+    GS_TRY(guard(c));
+    GS_TRY(need_model(c));
+    gs_mlp *q = c->mlp;
+    if (!params || n != gs_mlp_param_count(q->p)) return gs_fail(c, GS_ERR_ARG, "null output or wrong count");
+    GS_CUDA(c, cudaMemcpyAsync(params, q->master, sizeof(float) * q->off.n, cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(params + q->off.n, q->norm, sizeof(float) * (2 * NIN + q->nc), cudaMemcpyDeviceToHost,
+                               c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_forward(gs_ctx *c, const float *X_dev, long rows, float *Y_dev) {
+    GS_TRY(guard(c));
+    GS_TRY(need_model(c));
+    if (!X_dev || !Y_dev || rows < 1) return gs_fail(c, GS_ERR_ARG, "null pointer or rows < 1");
+    GS_TRY(forward(c, X_dev, rows));
+    gs_mlp *q = c->mlp;
+    GS_CUDA(c, cudaMemcpyAsync(Y_dev, q->out, sizeof(float) * rows * q->no, cudaMemcpyDeviceToDevice, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_loss_grad(gs_ctx *c, const float *X_dev, const float *Y_dev, long rows, float *grad_dev,
+                                double *loss) {
+    GS_TRY(guard(c));
+    GS_TRY(need_model(c));
+    if (!X_dev || !Y_dev || rows < 1) return gs_fail(c, GS_ERR_ARG, "null pointer or rows < 1");
+    GS_TRY(loss_grad(c, X_dev, Y_dev, rows, loss));
+    gs_mlp *q = c->mlp;
+    if (grad_dev) {
+        GS_CUDA(c, cudaMemcpyAsync(grad_dev, q->grad, sizeof(float) * q->off.n, cudaMemcpyDeviceToDevice, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_train_step(gs_ctx *c, const float *X_dev, const float *Y_dev, long rows, double lr,
+                                 double *loss) {
+    GS_TRY(guard(c));
+    GS_TRY(need_model(c));
+    if (!X_dev || !Y_dev || rows < 1 || !(lr > 0.0)) return gs_fail(c, GS_ERR_ARG, "null pointer, rows < 1 or lr <= 0");
+    GS_TRY(loss_grad(c, X_dev, Y_dev, rows, loss));
+    gs_mlp *q = c->mlp;
+    q->t += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, q->t))), c2 = (float)(1.0 / (1.0 - std::pow(b2, q->t)));
+    GS_COUNT_LAUNCH(c);
+    k_adam<<<nblk(q->off.n), 256, 0, c->stream>>>(q->master, q->grad, q->m, q->v, q->off.n, (float)lr, (float)b1,
+                                                  (float)b2, 1e-8f, c1, c2);
+    GS_CHECK_LAUNCH(c);
+    return refresh_bf16(c);
+}
+
+extern "C" int gs_ws_features(gs_ctx *c, int angle, float *X_dev) {
+    GS_TRY(guard(c));
+    GS_TRY(angle_ready(c, angle));
+    if (!X_dev) return gs_fail(c, GS_ERR_ARG, "null output");
+    const AngleData &a = c->ang[angle];
+    gs_mlp *q = c->mlp;
+    GS_TRY(gs_incoming_impl(c, a, q->w));
+    GS_COUNT_LAUNCH(c);
+    k_ws_features<<<nblk(c->M), 256, 0, c->stream>>>(c->xy, c->M, a.theta, c->L.k1, c->L.d, q->w, c->nc, c->p, X_dev);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_ws_moments(gs_ctx *c, int angle, double *ms_host) {
+    GS_TRY(guard(c));
+    GS_TRY(angle_ready(c, angle));
+    if (!ms_host) return gs_fail(c, GS_ERR_ARG, "null output");
+    const AngleData &a = c->ang[angle];
+    gs_mlp *q = c->mlp;
+    GS_TRY(gs_translate_impl(c, a, a.beta, q->t1, GS_FP64));
+    GS_TRY(gs_layer_response_impl(c, a, a.beta, q->t2));
+    GS_COUNT_LAUNCH(c);
+    k_ws_moments<<<c->nc, 256, 0, c->stream>>>(q->t1, q->t2, c->s, c->M, c->nc, (double *)q->w);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(ms_host, q->w, sizeof(double) * 2 * c->nc, cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_ws_targets(gs_ctx *c, int angle, float *Y_dev) {
+    GS_TRY(guard(c));
+    GS_TRY(angle_ready(c, angle));
+    if (!Y_dev) return gs_fail(c, GS_ERR_ARG, "null output");
+    const AngleData &a = c->ang[angle];
+    gs_mlp *q = c->mlp;
+    GS_TRY(gs_translate_impl(c, a, a.beta, q->t1, GS_FP64));
+    GS_TRY(gs_layer_response_impl(c, a, a.beta, q->t2));
+    GS_COUNT_LAUNCH(c);
+    k_ws_targets<<<nblk((long)c->M * c->nc), 256, 0, c->stream>>>(q->t1, q->t2, q->norm + 2 * NIN, c->M, c->nc, Y_dev);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_warm_start(gs_ctx *c, int angle, gs_c128 *beta0_dev, double *relres0, int *used) {
+    GS_TRY(guard(c));
+    GS_TRY(angle_ready(c, angle));
+    if (!beta0_dev) return gs_fail(c, GS_ERR_ARG, "null output");
+    const AngleData &a = c->ang[angle];
+    gs_mlp *q = c->mlp;
+    cudaStream_t st = c->stream;
+    cplx *beta0 = (cplx *)beta0_dev;
+    const long n = c->n();
+    GS_TRY(gs_incoming_impl(c, a, q->w));
+    GS_COUNT_LAUNCH(c);
+    k_ws_features<<<nblk(c->M), 256, 0, st>>>(c->xy, c->M, a.theta, c->L.k1, c->L.d, q->w, c->nc, c->p, q->X);
+    GS_TRY(forward(c, q->X, c->M));
+    GS_COUNT_LAUNCH(c);
+    k_ws_guess<<<nblk(n), 256, 0, st>>>(q->out, q->w, c->s, q->norm + 2 * NIN, c->M, c->nc, beta0);
+    // the judge: ||b - L beta_0|| against ||b|| (the zero start), in FP64
+    GS_TRY(gs_rhs_impl(c, a, q->t1));
+    GS_TRY(gs_apply_impl(c, a, beta0, q->t2, GS_FP64));
+    GS_COUNT_LAUNCH(c);
+    k_res_norms<<<1, 1024, 0, st>>>(q->t1, q->t2, n, c->dscal + 6);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(c->hscal + 6, c->dscal + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    const double rel = c->hscal[7] > 0.0 ? std::sqrt(c->hscal[6] / c->hscal[7]) : 0.0;
+    const int keep = std::isfinite(rel) && rel < 1.0;
+    if (!keep) GS_CUDA(c, cudaMemsetAsync(beta0, 0, sizeof(cplx) * n, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    if (relres0) *relres0 = rel;
+    if (used) *used = keep;
+    return GS_OK;
+}

@@ -1,0 +1,247 @@
+"""GPU parity of the learned warm start (through the C-ABI) against the oracle, and what the
+trained network gains over the zero start.
+
+Tolerances: the network runs with bfloat16 weights and activations and FP32 accumulation; the
+oracle emulates that storage (rounding the same quantities to bfloat16), so the remaining
+difference is FP32 accumulation order (~1e-6) plus the rare value that lands on the other side of a
+bfloat16 rounding boundary (2^-8 relative for that value): 2e-3 relative in norm.  Against the
+oracle's plain FP64 network the difference is the bfloat16 storage itself, a few 2^-9 per layer:
+3e-2.  Features and targets are FP64 quantities rounded once to FP32: 1e-6."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import solver as S
+from oracle import warmstart as WS
+
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _params(p, seed=3):
+    rng = np.random.default_rng(seed)
+    w = W.mlp_init(p, seed).astype(np.float64)
+    w[WS.n_weights(p) - WS.n_out(p):] = 0.1 * rng.standard_normal(WS.n_out(p))
+    mu = 0.1 * rng.standard_normal(64)
+    sd = 0.5 + rng.random(64)
+    scale = np.exp(rng.uniform(-2, 2, 2 * p + 1))
+    scale[0] = 0.0                                   # one order not predicted
+    return np.concatenate([w, mu, sd, scale]).astype(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def small():
+    from paper_1412_7466_gb300 import GratingSolver
+    cfg = W.config("small")
+    prob = S.setup(cfg["grating"], cfg["theta"], cfg["disks"])
+    beta, _, _ = S.solve_dense(prob)
+    gs = GratingSolver(0)
+    gs.set_layers(cfg["grating"])
+    gs.set_incidence([cfg["theta"]])
+    gs.set_inclusions(cfg["disks"])
+    gs.factor()
+    p = cfg["disks"]["p"]
+    prm = _params(p)
+    gs.mlp_set_params(p, prm)
+    yield cfg, prob, beta, gs, prm
+    gs.close()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_param_roundtrip_and_count(small):
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    assert gs.mlp_param_count(p) == WS.n_params(p)
+    np.testing.assert_array_equal(gs.mlp_get_params(), prm.astype(np.float32))
+
+
+def test_features_match_oracle(small):
+    cfg, prob, beta, gs, prm = small
+    X = _np(gs.ws_features())
+    w = WS.incoming_empty(prob)
+    Xo = WS.features(prob.disks["xy"], cfg["theta"], prob.eg.k[0], w[:, prob.disks["p"]], prob.eg.d)
+    np.testing.assert_allclose(X, Xo, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("rows", [1, 65, 700])
+def test_forward_matches_oracle(small, rows):
+    """Row counts: one row, a ragged second tile, and more than one weight-gradient chunk."""
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    X = np.random.default_rng(rows).standard_normal((rows, 64)).astype(np.float32)
+    got = _np(gs.mlp_forward(X))
+    ref_bf, _ = WS.forward(prm, X.astype(np.float64), p, bf16_storage=True)
+    ref64, _ = WS.forward(prm, X.astype(np.float64), p)
+    assert _rel(got, ref_bf) <= 2e-3
+    assert _rel(got, ref64) <= 3e-2
+
+
+@pytest.mark.parametrize("rows", [65, 1100])
+def test_gradient_matches_oracle(small, rows):
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    rng = np.random.default_rng(10 + rows)
+    X = rng.standard_normal((rows, 64)).astype(np.float32)
+    Y = rng.standard_normal((rows, WS.n_out(p))).astype(np.float32)
+    loss, g = gs.mlp_loss_grad(X, Y)
+    g = _np(g)
+    lo, go = WS.loss_and_grad(prm, X.astype(np.float64), Y.astype(np.float64), p, bf16_storage=True)
+    assert abs(loss - lo) <= 2e-3 * lo
+    # per tensor (W1, b1, W2, b2, W3, b3)
+    o = 0
+    for shp in WS.weight_shapes(p):
+        n = int(np.prod(shp))
+        assert _rel(g[o:o + n], go[o:o + n]) <= 2e-3, shp
+        o += n
+    _, g64 = WS.loss_and_grad(prm, X.astype(np.float64), Y.astype(np.float64), p)
+    assert _rel(g, g64) <= 3e-2
+
+
+def test_adam_step_matches_oracle(small):
+    from paper_1412_7466_gb300 import GratingSolver
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((300, 64)).astype(np.float32)
+    Y = rng.standard_normal((300, WS.n_out(p))).astype(np.float32)
+    g2 = GratingSolver(0)
+    g2.mlp_set_params(p, prm)
+    import torch
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    g2.mlp_train_step(Xd, Yd, 1e-3)
+    g2.mlp_train_step(Xd, Yd, 1e-3)
+    got = g2.mlp_get_params().astype(np.float64)
+    g2.close()
+    nw = WS.n_weights(p)
+    ref, m, v = prm.copy(), np.zeros(nw), np.zeros(nw)
+    for t in (1, 2):
+        _, gr = WS.loss_and_grad(ref, X.astype(np.float64), Y.astype(np.float64), p, bf16_storage=True)
+        ref, m, v = WS.adam_step(ref, gr, m, v, t, p, lr=1e-3)
+    step = ref[:nw] - prm[:nw]
+    # Adam's first steps move each weight by about lr sign(g): weights whose gradient is near zero
+    # can move differently, so compare in norm against the step itself
+    assert np.linalg.norm(got[:nw] - ref[:nw]) <= 0.02 * np.linalg.norm(step)
+    np.testing.assert_array_equal(got[nw:], prm[nw:].astype(np.float32))
+
+
+def test_targets_and_moments_match_oracle(small):
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    gs.solve(tol=cfg["tol"], maxit=500)
+    _, _, _, scale = WS.unpack(prm, p)
+    Y = _np(gs.ws_targets())
+    Yo = WS.targets(prob, beta, scale)
+    assert _rel(Y, Yo) <= 1e-6
+    # the two solutions agree to ~1e-9 (GMRES to 1e-12 against LU): moments to 1e-6
+    for got, ref in zip(gs.ws_moments(), WS.moments(prob, beta)):
+        np.testing.assert_allclose(got, ref, rtol=1e-6)
+
+
+def _solver_for(cfg, params, p):
+    from paper_1412_7466_gb300 import GratingSolver
+    g2 = GratingSolver(0)
+    g2.set_layers(cfg["grating"])
+    g2.set_incidence([cfg["theta"]])
+    g2.set_inclusions(cfg["disks"])
+    g2.factor()
+    g2.mlp_set_params(p, params)
+    return g2
+
+
+def test_warm_start_matches_oracle_and_falls_back(small):
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    nw, no = WS.n_weights(p), WS.n_out(p)
+    # a network whose output is exactly zero: beta_0 = s (.) w = b, no bfloat16 effect
+    zero = prm.copy()
+    zero[WS.n_weights(p) - no - 128 * no:nw] = 0.0
+    g2 = _solver_for(cfg, zero, p)
+    b0, rel, used = g2.warm_start()
+    b0o, relo, _ = WS.guess(prob, zero, cfg["theta"], prob.eg.k[0])
+    assert np.linalg.norm(b0o - prob.rhs()) <= 1e-13 * np.linalg.norm(prob.rhs())
+    assert relo < 1.0 and used
+    assert _rel(_np(b0), b0o) <= 1e-10 and abs(rel - relo) <= 1e-8 * relo
+    g2.close()
+    # the random network of the fixture: same decision and residual to bfloat16 accuracy
+    b0, rel, used = gs.warm_start()
+    b0o, relo, _ = WS.guess(prob, prm, cfg["theta"], prob.eg.k[0])
+    assert abs(rel - relo) <= 3e-2 * relo
+    assert used == (relo < 1.0)
+    if used:
+        assert _rel(_np(b0), b0o) <= 3e-2
+    # a planted network with huge outputs: rejected, zero start, and the solve from it is the
+    # plain solve
+    bad = prm.copy()
+    bad[nw - no:nw] = 1e30
+    g2 = _solver_for(cfg, bad, p)
+    b0, rel, used = g2.warm_start()
+    assert not used and rel > 1.0 and float(b0.abs().max()) == 0.0
+    g2.solve(tol=1e-12, maxit=500, beta0=b0)
+    assert _rel(_np(g2.get_beta()), beta) <= 1e-9
+    g2.close()
+
+
+def test_trained_network_gains_over_zero_start():
+    """A fixed geometry under a (phi, k_top) sweep: train on solutions of the first points, then on
+    held-out points compare the zero start, the untrained network and the trained network by their
+    initial residual and GMRES iterations to 1e-12; the converged answer is the same."""
+    from paper_1412_7466_gb300 import GratingSolver
+    from paper_1412_7466_gb300.warmstart import SweepTrainer, pack
+    p, M, r = 8, 120, 0.02
+    n_train, n_test = 48, 10
+    pts = W.sweep_points(n_train + n_test, seed=21, k_range=(9.0, 11.0))
+    base = W.disks(M, r, r / 2, 2.0, 10.0, seed=3, p=p)
+    gs = GratingSolver(0)
+    tr = SweepTrainer(gs, p)
+    w0 = W.mlp_init(p, 11)
+
+    def load(phi, kt):
+        g = W.scaled_grating("small", kt)
+        dk = dict(base)
+        dk["kp"] = np.full(M, 2.0 * kt)
+        th = -math.pi / 2 + phi
+        gs.set_layers(g)
+        gs.set_incidence([th])
+        gs.set_inclusions(dk)
+        gs.factor()
+
+    for q in range(n_train):
+        load(*pts[q])
+        gs.solve(tol=1e-12, maxit=1000)
+        if q == 0:
+            tr.begin(w0, (-math.pi / 2 - math.pi / 3, -math.pi / 2 + math.pi / 3), (9.0, 11.0))
+            untrained = gs.mlp_get_params()
+        tr.add()
+    hist = tr.fit(3000, 3e-3, 1e-4)
+    print("loss", hist[0], hist[-1])
+    assert hist[-1] < 0.5 * hist[0]
+    trained = gs.mlp_get_params()
+    res = {"zero": [], "untrained": [], "trained": []}
+    its = {"zero": [], "untrained": [], "trained": []}
+    for q in range(n_train, n_train + n_test):
+        load(*pts[q])
+        gs.solve(tol=1e-12, maxit=1000)
+        its["zero"].append(gs.stats()[0])
+        res["zero"].append(1.0)
+        ref = _np(gs.get_beta())
+        for name, prm in (("untrained", untrained), ("trained", trained)):
+            gs.mlp_set_params(p, prm)
+            b0, rel, used = gs.warm_start()
+            gs.solve(tol=1e-12, maxit=1000, beta0=b0)
+            its[name].append(gs.stats()[0])
+            res[name].append(rel if used else 1.0)
+            assert _rel(_np(gs.get_beta()), ref) <= 1e-9
+    gs.close()
+    mean = {k: float(np.mean(v)) for k, v in its.items()}
+    r0 = {k: float(np.mean(v)) for k, v in res.items()}
+    print("iterations", mean, "initial residual", r0)
+    assert r0["trained"] < r0["untrained"] and r0["trained"] < 1.0
+    assert mean["trained"] <= mean["zero"]

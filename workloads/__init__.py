@@ -149,11 +149,12 @@ def batched_geometries(n_geom: int = 64, seed: int = 4, k_top: float = 40.0, p: 
     return out
 
 
-def sweep_points(n: int = 4096, seed: int = 5) -> np.ndarray:
-    """(phi, k_top) pairs, iid uniform in [-pi/3, pi/3] x [35, 45]."""
+def sweep_points(n: int = 4096, seed: int = 5, phi_range=(-math.pi / 3, math.pi / 3),
+                 k_range=(35.0, 45.0)) -> np.ndarray:
+    """(phi, k_top) pairs, iid uniform in phi_range x k_range (default [-pi/3, pi/3] x [35, 45])."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    phi = rng.uniform(-math.pi / 3, math.pi / 3, n)
-    kt = rng.uniform(35.0, 45.0, n)
+    phi = rng.uniform(phi_range[0], phi_range[1], n)
+    kt = rng.uniform(k_range[0], k_range[1], n)
     return np.stack([phi, kt], axis=1)
 
 
@@ -181,3 +182,16 @@ def config(name: str, seed: int = 1) -> dict:
                 "disks": disks(4000, 0.004, 0.002, 2.0, g["k"][0], seed=seed, p=12), "tol": 1e-11,
                 "bragg_target": 1e-9}
     raise KeyError(name)
+
+
+def mlp_init(p: int, seed: int = 11) -> np.ndarray:
+    """Seeded initial weights of the warm-start network for multipole order p, flat float32 in the
+    order W1[64][128], b1[128], W2[128][128], b2[128], W3[128][2(2p+1)], b3[2(2p+1)]: weights
+    N(0, 1/fan_in), biases zero."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    no = 2 * (2 * p + 1)
+    parts = []
+    for fan_in, fan_out in ((64, 128), (128, 128), (128, no)):
+        parts.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), (fan_in, fan_out)).ravel())
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
