@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
+    ap.add_argument("--no-big", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="factor once, then run `steps` FP64 translation launches only (for ncu captures)")
     return ap.parse_args()
@@ -367,6 +368,32 @@ def main():
     except Exception:
         pass
 
+    # the mixed-precision workload at its own size: M = 4000 disks of radius 0.004 on the same
+    # grating and angle (100 000 unknowns); one warm-up geometry, one timed geometry
+    bigres = None
+    if not args.no_big:
+        gbig = [W.config("mixed4000", seed=sd)["disks"] for sd in (1, 2)]
+        gs.set_inclusions(gbig[0])
+        gs.factor()
+        gs.solve(tol=tol, maxit=8000, restart=500, precision=GS_C64)
+        gs.bragg()
+        barrier()
+        gs.set_inclusions(gbig[1])
+        a_, b_ = ev(), ev()
+        a_.record(stream)
+        gs.factor()
+        gs.solve(tol=tol, maxit=8000, restart=500, precision=GS_C64)
+        brb = gs.bragg()
+        b_.record(stream)
+        b_.synchronize()
+        tb = a_.elapsed_time(b_) / 1e3
+        bigres = {"value": 1.0 / tb, "unit": "solves/s", "dtype": "c64 translation + f64 refinement",
+                  "M": 4000, "unknowns": 4000 * nc, "inner_iters": gs.stats()[0],
+                  "refinement_sweeps": gs.refinement_sweeps(), "relres": gs.stats()[1],
+                  "flux_err": brb["flux_err"],
+                  "step": "set_inclusions + factor (S, B, C, pair table) + mixed solve to 1e-11 + Bragg; "
+                          "Bragg agreement with the FP64 solve at this size: tests/test_gpu_mixed4000.py"}
+
     # batched form: geometries of uneven size from the batched workload generator, one grating
     # factorisation at the k1 = 40 Wood-anomaly angle, solved together (one persistent translation
     # per product, lockstep GMRES from a CUDA graph) against the same geometries one at a time
@@ -565,6 +592,7 @@ def main():
                                            "avg_launch_ms": avg32, "launches_timed": nmx32,
                                            "fp64_residual_launches": nmx64,
                                            "fp64_residual_ms": ms_mx64}),
+            "mixed_c64_ir_M4000": bigres,
             "batched_c64_ir": bres,
             "warm_start_fp64": wres,
         },
