@@ -31,6 +31,7 @@ extern "C" {
 #define GS_ERR_GEOMETRY 5        /* overlapping disks (minimum-image), disk crossing an interface    */
 #define GS_ERR_NOT_CONVERGED 6   /* GMRES hit maxit; the iterate and its residual remain readable    */
 #define GS_ERR_NUMERIC 7         /* a NaN or Inf appeared in a result                                */
+#define GS_ERR_TIMEOUT 8         /* a device-side wait gave up (bounded); the result is not valid   */
 
 typedef struct gs_ctx gs_ctx;
 typedef struct { double re, im; } gs_c128;
@@ -228,6 +229,14 @@ int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms)
  * writes the achieved TFLOP/s (2 flops per FMA). */
 #define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
+
+/* ---- tensor-core product ---------------------------------------------------------------------
+ * C[M][N] = A[M][K] B[N][K]^T with A, B bfloat16 (row-major, K contiguous) and C FP32 (row-major),
+ * accumulated in FP32 on the tensor cores (tcgen05).  The paper has no such routine: it is the dense
+ * contraction under the multi-right-hand-side translation (Sec. 4.2 Eq. trans applied to many
+ * angles at once).  M % 128 == 0, N % 256 == 0, K % 64 == 0, 16-byte aligned device pointers
+ * (caller-owned), else GS_ERR_ARG; GS_ERR_TIMEOUT if a device wait gave up.  Synchronous. */
+int gs_tc_gemm_bf16(gs_ctx *ctx, const void *A_dev, const void *B_dev, float *C_dev, long M, long N, long K);
 
 /* ---- learned warm start ----------------------------------------------------------------------
  * The paper has no learned component: this is an addition to the iterative solve of Sec. 5 that

@@ -24,6 +24,7 @@ GS_ERR_OOM = 4
 GS_ERR_GEOMETRY = 5
 GS_ERR_NOT_CONVERGED = 6
 GS_ERR_NUMERIC = 7
+GS_ERR_TIMEOUT = 8
 GS_FP64 = 0
 GS_C64 = 1
 GS_PROBE_F32X2 = 2
@@ -92,6 +93,7 @@ _SIGS = {
     "gs_batch_tuning": (ctypes.c_int, [_vp, _ip, _ip]),
     "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
+    "gs_tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_long, ctypes.c_long, ctypes.c_long]),
     "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
     "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "gs_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -463,6 +465,15 @@ class GratingSolver:
         self._check(self.lib.gs_warm_start(self.ctx, angle, _ptr(b0), ctypes.byref(rel), ctypes.byref(used)),
                     "gs_warm_start")
         return b0, rel.value, bool(used.value)
+
+    def tc_gemm_bf16(self, A, B):
+        """C = A B^T on the tensor cores: A (M, K) and B (N, K) bfloat16 device tensors, C (M, N) FP32."""
+        A = A.contiguous()
+        B = B.contiguous()
+        C = self.torch.empty(A.shape[0], B.shape[0], dtype=self.torch.float32, device=self.device)
+        self._check(self.lib.gs_tc_gemm_bf16(self.ctx, _ptr(A), _ptr(B), _ptr(C), A.shape[0], B.shape[0], A.shape[1]),
+                    "gs_tc_gemm_bf16")
+        return C
 
     def probe_fma(self, precision=GS_FP64):
         v = ctypes.c_double()

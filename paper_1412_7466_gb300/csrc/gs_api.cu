@@ -219,6 +219,7 @@ const char *gs_strerror(int s) {
         case GS_ERR_GEOMETRY: return "invalid geometry";
         case GS_ERR_NOT_CONVERGED: return "GMRES did not converge";
         case GS_ERR_NUMERIC: return "non-finite result";
+        case GS_ERR_TIMEOUT: return "device wait timed out";
         default: return "unknown status";
     }
 }

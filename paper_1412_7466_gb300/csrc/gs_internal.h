@@ -158,6 +158,9 @@ size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
 // (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st
 int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st);
+// tensor-core product C[M][N] = A[M][K] B[N][K]^T, bfloat16 in, FP32 out (gs_tc.cu)
+int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
+                    cudaStream_t st);
 // low-rank, operator, GMRES, Bragg (gs_solve.cu)
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);

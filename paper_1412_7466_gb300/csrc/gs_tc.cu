@@ -1,0 +1,284 @@
+// Tensor-core (tcgen05) matrix product for the multi-right-hand-side translation.
+//
+// The translation of R coefficient vectors at once (R incidence angles of one geometry, Sec. 4.2
+// Eq. trans with the image phases of each angle) is a dense contraction: with the image-separated
+// blocks T_l (l = -1, 0, 1; T_l[(i,m),(j,n)] = H_{n-m}(k R) e^{i(n-m) Th} of the pair (i, j, l)),
+//   alpha_r = [T_-1  T_0  T_1] [a_r^-1 beta_r; beta_r; a_r beta_r]     (a_r = e^{i k1 cos(theta_r) d}),
+// and in real arithmetic [Re; Im] rows against [Re; Im] columns of 2x2 blocks [[Re, -Im], [Im, Re]].
+// That product, C[M][N] = A[M][K] B[N][K]^T with A (the operator, bfloat16), B (the stacked
+// right-hand sides, bfloat16) and C in FP32, runs here on the 5th-generation tensor cores:
+//
+//   * one CTA per 128 x 256 tile of C, four warps; thread 0 of warp 0 streams the K dimension in
+//     64-wide slices through a 4-stage ring of shared-memory buffers with TMA (128-byte swizzle),
+//     thread 0 of warp 1 issues tcgen05.mma (M 128, N 256, K 16, BF16 in, FP32 accumulate) into a
+//     256-column tensor-memory accumulator and releases each stage with tcgen05.commit; after the
+//     last slice all four warps read their 32 TMEM lanes with tcgen05.ld and write C.
+//   * every wait on an mbarrier is bounded (about 2 s); a wait that gives up sets *err, the kernel
+//     still waits (bounded) for its own tensor-core work, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <mutex>
+#include <string>
+
+#include "gs_internal.h"
+
+namespace {
+
+constexpr int TBM = 128, TBN = 256, TBK = 64, TST = 4;
+constexpr int TA_BYTES = TBM * TBK * 2;               // 16 KB
+constexpr int TB_BYTES = TBN * TBK * 2;               // 32 KB
+constexpr int TSTAGE = TA_BYTES + TB_BYTES;           // 48 KB
+constexpr int TSMEM = TST * TSTAGE + 1024 + 256;      // stages (1024-aligned) + barriers
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_CYCLES = 4000000000LL;      // ~2 s at 2 GHz
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B bfloat16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                           ((uint32_t)(TBM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// waits for the phase of the given parity to complete; false after WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset (unused for this layout; 16 B), stride byte
+// offset 1024 B between 8-row groups (bits 32-45), descriptor version 1 (bits 46-47), layout
+// SWIZZLE_128B = 2 (bits 61-63)
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
+          int M, int N, int K, int *__restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + TST * TSTAGE);   // full[TST], empty[TST], accum
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * TST + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
+    const int nk = K / TBK;
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + TST), b_acc = smem_u32(bars + 2 * TST);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TST; ++s) {
+            mbar_init(b_full + 8 * s, 1);
+            mbar_init(b_empty + 8 * s, 1);
+        }
+        mbar_init(b_acc, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        // producer: K slices of A (128 x 64) and B (256 x 64) into the stage ring
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            if (!mbar_wait(b_empty + 8 * stage, phase ^ 1)) {
+                ok = false;
+                break;
+            }
+            const uint32_t sa = s_base + stage * TSTAGE;
+            mbar_expect_tx(b_full + 8 * stage, TSTAGE);
+            tma_load_2d(sa, &tmA, b_full + 8 * stage, kb * TBK, m0);
+            tma_load_2d(sa + TA_BYTES, &tmB, b_full + 8 * stage, kb * TBK, n0);
+            if (++stage == TST) {
+                stage = 0;
+                phase ^= 1;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // tensor-core issue: four K = 16 steps per slice (32 bytes along the swizzled rows)
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            if (!mbar_wait(b_full + 8 * stage, phase)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = s_base + stage * TSTAGE, sb = sa + TA_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TBK / 16; ++kk)
+                umma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), (kb | kk) != 0);
+            umma_commit(b_empty + 8 * stage);
+            if (++stage == TST) {
+                stage = 0;
+                phase ^= 1;
+            }
+        }
+        umma_commit(b_acc);   // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
+    const bool acc_ok = mbar_wait(b_acc, 0);
+    tc_fence_after();
+    if (acc_ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < TBN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < M) {
+                float4 *dst = (float4 *)(C + (size_t)row * N + n0 + c0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                         __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+            }
+        }
+    }
+    if (!ok || !acc_ok) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D bfloat16 tensor map of a row-major rows x cols matrix, box 64 (cols) x box_rows, 128-byte swizzle
+int make_map(gs_ctx *c, CUtensorMap *m, const void *base, long rows, long cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return gs_fail(c, GS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gs_fail(c, GS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return GS_OK;
+}
+
+}  // namespace
+
+// C[M][N] = A[M][K] B[N][K]^T (bfloat16 in, FP32 out) on stream st; M % 128, N % 256, K % 64 == 0,
+// 16-byte aligned rows.  err_dev: device int, set to 1 if a wait gave up.
+int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
+                    cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % TBM || N % TBN || K % TBK)
+        return gs_fail(c, GS_ERR_ARG, "tensor-core product needs M % 128 == 0, N % 256 == 0, K % 64 == 0");
+    if (M / TBM > 2147483647L || N / TBN > 65535 || K > 2147483647L) return gs_fail(c, GS_ERR_ARG, "size out of range");
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15) return gs_fail(c, GS_ERR_ARG, "pointers must be 16-byte aligned");
+    CUtensorMap ma, mb;
+    GS_TRY(make_map(c, &ma, A, M, K, TBM));
+    GS_TRY(make_map(c, &mb, B, N, K, TBN));
+    static bool attr = false;
+    if (!attr) {
+        GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
+        attr = true;
+    }
+    GS_COUNT_LAUNCH(c);
+    k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN)), 128, TSMEM, st>>>(ma, mb, C, (int)M, (int)N, (int)K,
+                                                                                 err_dev);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+extern "C" int gs_tc_gemm_bf16(gs_ctx *c, const void *A_dev, const void *B_dev, float *C_dev, long M, long N,
+                               long K) {
+    if (!c) return GS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, "cudaSetDevice");
+    if (!A_dev || !B_dev || !C_dev) return gs_fail(c, GS_ERR_ARG, "null pointer");
+    int *err = nullptr;
+    GS_CUDA(c, cudaMalloc((void **)&err, sizeof(int)));
+    cudaMemsetAsync(err, 0, sizeof(int), c->stream);
+    int st = gs_tc_gemm_impl(c, A_dev, B_dev, C_dev, M, N, K, err, c->stream);
+    int herr = 0;
+    if (st == GS_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = gs_fail(c, GS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFree(err);
+    if (st == GS_OK && herr) st = gs_fail(c, GS_ERR_TIMEOUT, "tensor-core product: a device wait gave up");
+    return st;
+}
