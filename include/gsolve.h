@@ -230,6 +230,17 @@ int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms)
 #define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
 
+/* alpha_r = T(theta_r) beta_r for R right-hand sides at once (R incidence angles of the current
+ * geometry; Sec. 4.2 Eq. trans with each angle's image phase a_r = exp(i k1 cos(theta_r) d), passed
+ * in alpha_host[r]).  beta_dev and out_dev hold R consecutive vectors of length n (caller-owned
+ * device memory).  The translation runs on the tensor cores in bfloat16 with FP32 accumulation:
+ * the operator [T_-1 T_0 T_1] is built once per geometry in real 2x2 form (2n x 6n bfloat16,
+ * 15 GB at M = 1000, p = 12; GS_ERR_OOM if it does not fit) and kept until the geometry changes.
+ * Relative accuracy ~3e-3 (bfloat16 operands) -- an inner operator, not a final one.  Needs
+ * gs_factor; GS_ERR_TIMEOUT if a device wait gave up.  Synchronous. */
+int gs_translate_multi(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev, gs_c128 *out_dev);
+#define GS_TC_BF16 3             /* gs_profile_read tag of the tensor-core product in gs_translate_multi */
+
 /* ---- tensor-core product ---------------------------------------------------------------------
  * C[M][N] = A[M][K] B[N][K]^T with A, B bfloat16 (row-major, K contiguous) and C FP32 (row-major),
  * accumulated in FP32 on the tensor cores (tcgen05).  The paper has no such routine: it is the dense

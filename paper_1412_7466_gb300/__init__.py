@@ -28,6 +28,7 @@ GS_ERR_TIMEOUT = 8
 GS_FP64 = 0
 GS_C64 = 1
 GS_PROBE_F32X2 = 2
+GS_TC_BF16 = 3
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -94,6 +95,7 @@ _SIGS = {
     "gs_translate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
     "gs_tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_long, ctypes.c_long, ctypes.c_long]),
+    "gs_translate_multi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
     "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "gs_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -465,6 +467,18 @@ class GratingSolver:
         self._check(self.lib.gs_warm_start(self.ctx, angle, _ptr(b0), ctypes.byref(rel), ctypes.byref(used)),
                     "gs_warm_start")
         return b0, rel.value, bool(used.value)
+
+    def translate_multi(self, alphas, betas):
+        """Translations of R right-hand sides (rows of betas, (R, n) complex) with image phases
+        alphas (R complex), on the tensor cores (bfloat16 in, FP32 accumulate); returns (R, n)."""
+        a = np.ascontiguousarray(np.asarray(alphas, dtype=np.complex128))
+        B = self._as_dev(betas)
+        if B.dim() != 2 or B.shape[0] != a.size:
+            raise ValueError("betas must be (R, n) with R = len(alphas)")
+        out = self.torch.empty_like(B)
+        self._check(self.lib.gs_translate_multi(self.ctx, a.size, a.ctypes.data_as(_vp), _ptr(B), _ptr(out)),
+                    "gs_translate_multi")
+        return out
 
     def tc_gemm_bf16(self, A, B):
         """C = A B^T on the tensor cores: A (M, K) and B (N, K) bfloat16 device tensors, C (M, N) FP32."""

@@ -94,6 +94,12 @@ void free_geometry(gs_ctx *c) {
     dfree(c->b32);
     dfree(c->img32);
     dfree(c->htab);
+    if (c->tcA) cudaFree(c->tcA);
+    c->tcA = nullptr;
+    c->tcA_rows = c->tcA_cols = 0;
+    if (c->tc_scratch) cudaFree(c->tc_scratch);
+    c->tc_scratch = nullptr;
+    c->tc_scratch_bytes = 0;
     c->part_elems = 0;
     dfree(c->Vk);
     dfree(c->Hh);

@@ -89,6 +89,11 @@ struct gs_ctx {
     float2 *b32 = nullptr;                               // n, complex64 copy of the source coefficients
     float4 *img32 = nullptr;                             // 3M, (hi, lo) float image coordinates
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
+    void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
+    long tcA_rows = 0, tcA_cols = 0;
+    double tc_gamma = 1.0;                               // order rescaling of tcA (min(1, k2 r_min))
+    void *tc_scratch = nullptr;                          // multi-right-hand-side scratch
+    size_t tc_scratch_bytes = 0;
     double table_budget_gb = -1.0;                       // < 0: half of the free device memory
     size_t part_elems = 0;
     // GMRES workspace

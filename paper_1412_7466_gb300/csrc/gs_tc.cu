@@ -17,6 +17,10 @@
 //     still waits (bounded) for its own tensor-core work, frees its tensor memory and returns.
 #include <cuda.h>
 
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -260,6 +264,219 @@ int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, l
     k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN)), 128, TSMEM, st>>>(ma, mb, C, (int)M, (int)N, (int)K,
                                                                                  err_dev);
     GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+namespace {
+
+// A[2(i nc + m) + a][2(s nc + n) + b] for the source image s = (l+1) M + j of target i: the real
+// 2x2 form [[Re h, -Im h], [Im h, Re h]] of h = H_{n-m}(k R) e^{i(n-m) Th}, (R, Th) = polar(c_i -
+// c_j - l d) (zero for the particle itself, l = 0, j = i).  One thread per (target, source image):
+// H_0, H_1 seeded in FP64, orders by upward recurrence, rounded to bfloat16 on the way out.
+// Entries are stored rescaled, h gamma^(|m| + |n|) (orders m, n in -p..p): with gamma = min(1, k r_min)
+// and R >= 2 r_min (disks do not overlap), |H_q(k R)| (2 gamma / (k R))^q <= (q - 1)!/pi keeps every
+// entry inside the bfloat16 range (23!/pi = 8e21 at p = 12); the coefficients are divided by
+// gamma^|n| on the way in and the results by gamma^|m| on the way out.
+template <int P>
+__global__ void k_tc_build_A(const double *__restrict__ xy, int M, double k, double d, double gamma, long lda,
+                             __nv_bfloat16 *__restrict__ A) {
+    constexpr int NC = 2 * P + 1, NQ = 4 * P + 1;
+    const long S = 3L * M;
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)M * S) return;
+    const int i = (int)(id / S);
+    const long s = id - (long)i * S;
+    const int l = (int)(s / M) - 1;
+    const int j = (int)(s - (long)(l + 1) * M);
+    if (l == 0 && j == i) return;   // stays zero
+    const double dx = xy[2 * i] - (xy[2 * j] + l * d), dy = xy[2 * i + 1] - xy[2 * j + 1];
+    const double R = hypot(dx, dy), z = k * R, twoz = 2.0 / z;
+    cplx h[NQ];                       // h[q + 2P] = H_q(z) e^{i q Th}
+    cplx Hm1, Hc;
+    hankel01(z, Hm1, Hc);
+    const cplx u1 = C(dx / R, dy / R);
+    cplx up = u1;
+    h[2 * P] = Hm1;
+#pragma unroll
+    for (int q = 1; q <= 2 * P; ++q) {
+        h[2 * P + q] = cmul(Hc, up);
+        const cplx hm = cmul(Hc, cconj(up));
+        h[2 * P - q] = (q & 1) ? C(-hm.x, -hm.y) : hm;
+        if (q < 2 * P) {
+            const cplx Hn = csub(cscale(Hc, q * twoz), Hm1);
+            Hm1 = Hc;
+            Hc = Hn;
+            up = cmul(up, u1);
+        }
+    }
+    double gp[P + 1];   // gamma^e
+    gp[0] = 1.0;
+#pragma unroll
+    for (int e = 1; e <= P; ++e) gp[e] = gp[e - 1] * gamma;
+    const long col0 = 2 * s * NC;
+#pragma unroll 1
+    for (int m = 0; m < NC; ++m) {
+        const double gm = gp[m < P ? P - m : m - P];
+        __nv_bfloat162 *re_row = (__nv_bfloat162 *)(A + (2 * ((long)i * NC + m)) * lda + col0);
+        __nv_bfloat162 *im_row = (__nv_bfloat162 *)(A + (2 * ((long)i * NC + m) + 1) * lda + col0);
+#pragma unroll
+        for (int n = 0; n < NC; ++n) {
+            const cplx v = cscale(h[n - m + 2 * P], gm * gp[n < P ? P - n : n - P]);
+            re_row[n] = __floats2bfloat162_rn((float)v.x, (float)-v.y);
+            im_row[n] = __floats2bfloat162_rn((float)v.y, (float)v.x);
+        }
+    }
+}
+
+// Bt[r][2(s nc + n) + b] = part b of a_r^l beta_r[j nc + n], s = (l+1) M + j (a_r^-1 = conj(a_r))
+__global__ void k_tc_pack_B(const cplx *__restrict__ beta, const cplx *__restrict__ alpha, int R, int M, int nc,
+                            double gamma, long ldb, __nv_bfloat16 *__restrict__ Bt) {
+    const long n = (long)M * nc;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over R x 3n complex entries
+    if (e >= (long)R * 3 * n) return;
+    const int r = (int)(e / (3 * n));
+    const long q = e - (long)r * 3 * n;      // = s nc + n_order
+    const int l = (int)(q / n) - 1;
+    const cplx b = beta[(long)r * n + (q - (long)(l + 1) * n)];
+    const cplx a = alpha[r];
+    const int p = nc / 2, o = (int)(q % nc) - p;
+    const cplx v = cscale(l == 0 ? b : (l == 1 ? cmul(a, b) : cmul(cconj(a), b)), pow(gamma, -(double)abs(o)));
+    ((__nv_bfloat162 *)(Bt + (long)r * ldb))[q] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+}
+
+// out_r[e] = (C[2e][r] + i C[2e+1][r]) / gamma^|m|, e = i nc + m
+__global__ void k_tc_unpack(const float *__restrict__ Cm, long ldc, int R, long n, int nc, double gamma,
+                            cplx *__restrict__ out) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)R * n) return;
+    const int r = (int)(e / n);
+    const long q = e - (long)r * n;
+    const int o = (int)(q % nc) - nc / 2;
+    const double sc = pow(gamma, -(double)abs(o));
+    out[e] = C(sc * (double)Cm[(2 * q) * ldc + r], sc * (double)Cm[(2 * q + 1) * ldc + r]);
+}
+
+// out[0] = min over the inclusions of the radius (one block)
+__global__ void k_min_radius(const double *__restrict__ radius, int M, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double v = 1e300;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) v = fmin(v, radius[i]);
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 1e300;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) out[0] = v;
+    }
+}
+
+template <int P>
+int build_A(gs_ctx *c, long lda) {
+    const long tot = 3L * c->M * c->M;
+    GS_COUNT_LAUNCH(c);
+    k_tc_build_A<P><<<(int)((tot + 127) / 128), 128, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d, c->tc_gamma, lda,
+                                                                     (__nv_bfloat16 *)c->tcA);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+inline long round_up(long v, long m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+// the bfloat16 operator [T_-1 T_0 T_1] of the current geometry in real 2x2 form (built on first use)
+int gs_tc_operator(gs_ctx *c) {
+    const long n = c->n();
+    const long rows = round_up(2 * n, TBM), cols = round_up(6 * n, TBK);
+    if (c->tcA && c->tcA_rows == rows && c->tcA_cols == cols) return GS_OK;
+    if (c->tcA) cudaFree(c->tcA);
+    c->tcA = nullptr;
+    cudaError_t e = cudaMalloc((void **)&c->tcA, sizeof(__nv_bfloat16) * (size_t)rows * cols);
+    if (e != cudaSuccess) {
+        c->tcA = nullptr;
+        cudaGetLastError();
+        return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (tensor-core operator): ") + cudaGetErrorString(e));
+    }
+    c->tcA_rows = rows;
+    c->tcA_cols = cols;
+    GS_CUDA(c, cudaMemsetAsync(c->tcA, 0, sizeof(__nv_bfloat16) * (size_t)rows * cols, c->stream));
+    GS_COUNT_LAUNCH(c);
+    k_min_radius<<<1, 1024, 0, c->stream>>>(c->radius, c->M, c->dscal + 10);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(c->hscal + 10, c->dscal + 10, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->tc_gamma = std::min(1.0, c->L.k2 * c->hscal[10]);
+    switch (c->p) {
+        case 1: return build_A<1>(c, cols);
+        case 2: return build_A<2>(c, cols);
+        case 3: return build_A<3>(c, cols);
+        case 4: return build_A<4>(c, cols);
+        case 5: return build_A<5>(c, cols);
+        case 6: return build_A<6>(c, cols);
+        case 7: return build_A<7>(c, cols);
+        case 8: return build_A<8>(c, cols);
+        case 10: return build_A<10>(c, cols);
+        case 12: return build_A<12>(c, cols);
+        case 16: return build_A<16>(c, cols);
+        default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+}
+
+extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev,
+                                  gs_c128 *out_dev) {
+    if (!c) return GS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, "cudaSetDevice");
+    if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
+    if (R < 1 || R > 65536 || !alpha_host || !beta_dev || !out_dev)
+        return gs_fail(c, GS_ERR_ARG, "need 1..65536 right-hand sides and non-null pointers");
+    cudaStream_t st = c->stream;
+    const long n = c->n();
+    GS_TRY(gs_tc_operator(c));
+    const long K = c->tcA_cols, Mr = c->tcA_rows, Rp = round_up(R, TBN);
+    // scratch: alphas, stacked right-hand sides (bfloat16), product (FP32), wait flag
+    const size_t need = sizeof(cplx) * R + sizeof(__nv_bfloat16) * (size_t)Rp * K + 256 + sizeof(float) * (size_t)Mr * Rp +
+                        256 + 256;
+    if (need > c->tc_scratch_bytes) {
+        if (c->tc_scratch) cudaFree(c->tc_scratch);
+        c->tc_scratch = nullptr;
+        c->tc_scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->tc_scratch, need);
+        if (e != cudaSuccess) {
+            c->tc_scratch = nullptr;
+            cudaGetLastError();
+            return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (tensor-core scratch): ") + cudaGetErrorString(e));
+        }
+        c->tc_scratch_bytes = need;
+    }
+    uint8_t *p = (uint8_t *)c->tc_scratch;
+    cplx *al = (cplx *)p;
+    p += round_up(sizeof(cplx) * R, 256);
+    __nv_bfloat16 *Bt = (__nv_bfloat16 *)p;
+    p += round_up(sizeof(__nv_bfloat16) * (size_t)Rp * K, 256);
+    float *Cm = (float *)p;
+    p += round_up(sizeof(float) * (size_t)Mr * Rp, 256);
+    int *err = (int *)p;
+    GS_CUDA(c, cudaMemcpyAsync(al, alpha_host, sizeof(cplx) * R, cudaMemcpyHostToDevice, st));
+    GS_CUDA(c, cudaMemsetAsync(Bt, 0, sizeof(__nv_bfloat16) * (size_t)Rp * K, st));
+    GS_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
+    GS_COUNT_LAUNCH(c);
+    k_tc_pack_B<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>((const cplx *)beta_dev, al, R, c->M, c->nc,
+                                                                 c->tc_gamma, K, Bt);
+    GS_CHECK_LAUNCH(c);
+    cudaEvent_t e0, e1;
+    const bool timed = gs_prof_pair(c, &e0, &e1, GS_TC_BF16);
+    if (timed) cudaEventRecord(e0, st);
+    GS_TRY(gs_tc_gemm_impl(c, c->tcA, Bt, Cm, Mr, Rp, K, err, st));
+    if (timed) cudaEventRecord(e1, st);
+    GS_COUNT_LAUNCH(c);
+    k_tc_unpack<<<(int)((n * R + 255) / 256), 256, 0, st>>>(Cm, Rp, R, n, c->nc, c->tc_gamma, (cplx *)out_dev);
+    GS_CHECK_LAUNCH(c);
+    int herr = 0;
+    GS_CUDA(c, cudaMemcpyAsync(c->hscal + 8, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(c, cudaStreamSynchronize(st));
+    std::memcpy(&herr, c->hscal + 8, sizeof(int));
+    if (herr) return gs_fail(c, GS_ERR_TIMEOUT, "tensor-core product: a device wait gave up");
     return GS_OK;
 }
 

@@ -36,3 +36,36 @@ def test_tc_gemm_rejects_bad_shapes():
         gs.tc_gemm_bf16(A, B)
     assert e.value.status == GS_ERR_ARG
     gs.close()
+
+
+@pytest.mark.parametrize("M,p,R", [(37, 8, 5), (130, 12, 300)])
+def test_translate_multi_matches_oracle(M, p, R):
+    """R angles of one geometry through the tensor-core translation, against the oracle's dense
+    translation per angle.  bfloat16 operands (2^-9 relative rounding of each operator entry and
+    coefficient, FP32 accumulation): ~3e-3 relative in norm; bound 1e-2.  R = 300 spans two
+    256-column tiles; M = 130, p = 12 gives ragged row and column tails."""
+    import math
+    import workloads as W
+    from oracle import inclusions as I
+    from paper_1412_7466_gb300 import GratingSolver
+    g = W.grating("tiny")
+    dk = W.disks(M, 0.01, 0.005, 2.0, g["k"][0], seed=50 + M, p=p)
+    gs = GratingSolver(0)
+    gs.set_layers(g)
+    gs.set_incidence([-1.0])
+    gs.set_inclusions(dk)
+    gs.factor()
+    rng = np.random.default_rng(M)
+    nc = 2 * p + 1
+    n = M * nc
+    thetas = -math.pi / 2 + rng.uniform(-math.pi / 3, math.pi / 3, R)
+    alphas = np.exp(1j * g["k"][0] * np.cos(thetas) * g["d"])
+    w = np.tile(0.5 ** np.abs(np.arange(-p, p + 1)), M)
+    betas = (rng.standard_normal((R, n)) + 1j * rng.standard_normal((R, n))) * w
+    got = gs.translate_multi(alphas, betas).cpu().numpy()
+    gs.close()
+    for r in sorted({0, 1, R // 2, R - 1}):
+        T = I.translation_matrix(dk["xy"], g["k"][1], p, g["d"], alphas[r])
+        ref = T @ betas[r]
+        err = np.linalg.norm(got[r] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-2, (r, err)
