@@ -43,6 +43,13 @@ WORKLOAD = ("headline: M=1000 disks r=0.008 gap 0.004 index 2 (kp=80), p=12 (250
             "3-layer grating y=+-0.5+0.05cos(2pi x), N=256, k=(40,60,80), theta=-pi/5, "
             "A 1904x1689, GMRES tol 1e-11, FP64")
 GOLDEN = os.path.join(ROOT, "tests", "golden", "headline_bragg.txt")
+# measured HBM copy bandwidth and bf16 GEMM throughput of this machine's GPUs; the recipe's fallback
+# (one earlier GB300 measurement) when the file is absent
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        PEAKS = dict(json.load(_f), source="measured")
+except (OSError, ValueError):
+    PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 # DRAM bytes per (target, source image) pair of the table-driven FP64 translation, from the ncu
 # capture of k_translate_f64_tab at M = 500 (599.58 MB over 3 * 500^2 - 500 pairs); the pair table
 # (49 complex128 per pair) is 784 B of it.  Update with a new capture whenever that kernel changes.
@@ -59,6 +66,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
     ap.add_argument("--no-big", action="store_true")
+    ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="factor once, then run `steps` FP64 translation launches only (for ncu captures)")
     return ap.parse_args()
@@ -210,7 +218,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GS_PROBE_F32X2, GratingSolver
+    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GS_PROBE_F32X2, GS_TC_BF16, GratingSolver
 
     dist = None
     if world > 1:
@@ -244,6 +252,19 @@ def main():
     torch.cuda.synchronize()
     couple_ms = e[1].elapsed_time(e[2])
     grating_ms = e[0].elapsed_time(e[1]) - couple_ms
+
+    if args.kernel_only and os.environ.get("GS_BENCH_PRECISION") == "tc":
+        # tensor-core multi-right-hand-side translation, R = 256 angles
+        R = 256
+        ths = W.batched_angles(k1=g["k"][0], n=R)
+        alphas = np.exp(1j * g["k"][0] * np.cos(ths) * g["d"])
+        betas = torch.randn(R, M * nc, dtype=torch.complex128, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            gs.translate_multi(alphas, betas)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": True, "translate_multi_launches": args.warmup + args.steps, "R": R}))
+        gs.close()
+        return
 
     if args.kernel_only:
         beta = torch.randn(M * nc, dtype=torch.complex128, device="cuda")
@@ -367,6 +388,67 @@ def main():
                         / np.linalg.norm(np.array([ref[k] for k in keys])))
     except Exception:
         pass
+
+    # tensor-core multi-right-hand-side translation: the headline geometry at R = 256 incidence
+    # angles (the batched workload's angle list) in one product, bfloat16 operands, FP32 accumulation
+    tcres = None
+    if not args.no_tc:
+        gs.set_inclusions(cfg0["disks"])
+        gs.factor()
+        R = 256
+        ths = W.batched_angles(k1=g["k"][0], n=R)
+        alphas = np.exp(1j * g["k"][0] * np.cos(ths) * g["d"])
+        rngt = np.random.default_rng(12)
+        wt = np.tile(0.3 ** np.abs(np.arange(-p, p + 1)), M)
+        betas = torch.from_numpy((rngt.standard_normal((R, M * nc)) + 1j * rngt.standard_normal((R, M * nc))) * wt
+                                 ).to("cuda")
+        a_, b_ = ev(), ev()
+        a_.record(stream)
+        out_tc = gs.translate_multi(alphas, betas)   # first call builds the operator
+        b_.record(stream)
+        torch.cuda.synchronize()
+        first_ms = a_.elapsed_time(b_)
+        for _ in range(2):
+            gs.translate_multi(alphas, betas)
+        n_tc = 5
+        gs.profile(True)
+        a_, b_ = ev(), ev()
+        a_.record(stream)
+        for _ in range(n_tc):
+            out_tc = gs.translate_multi(alphas, betas)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        call_ms = a_.elapsed_time(b_) / n_tc
+        ntc, ms_tc = gs.profile_read(GS_TC_BF16)
+        gs.profile(False)
+        gemm_ms = ms_tc / max(ntc, 1)
+        errs = []
+        for r in (0, R // 2, R - 1):
+            gs.set_incidence([float(ths[r])])
+            gs.factor()
+            ref = gs.translate(betas[r])
+            errs.append(float(torch.linalg.norm(out_tc[r] - ref) / torch.linalg.norm(ref)))
+        gs.set_incidence([theta])
+        flops_alg = 8.0 * nc * nc * (3.0 * M * M - M) * R
+        rows, cols = 2 * M * nc, 6 * M * nc
+        rows_p, cols_p = -(-rows // 128) * 128, -(-cols // 64) * 64
+        a_bytes = 2.0 * rows_p * cols_p
+        tcres = {"R": R, "unit": "pair-translations/s",
+                 "value": (3 * M * M - M) * R / (call_ms * 1e-3),
+                 "call_ms": call_ms, "gemm_ms": gemm_ms, "first_call_ms_incl_operator_build": first_ms,
+                 "rel_err_vs_fp64_translate": errs,
+                 "roofline": {"bound": "hbm", "kernel": "k_tc_gemm (tcgen05, bf16 in, fp32 accumulate)",
+                              "achieved": a_bytes / (gemm_ms * 1e-3) / 1e9, "peak": PEAKS.get("hbm_gbs"),
+                              "unit": "GB/s", "frac": a_bytes / (gemm_ms * 1e-3) / 1e9 / PEAKS.get("hbm_gbs", 1.0),
+                              "peak_source": PEAKS["source"] + " copy bandwidth",
+                              "traffic": None, "bytes_per_launch": a_bytes},
+                 "tensor": {"achieved_tflops_algorithmic": flops_alg / (gemm_ms * 1e-3) / 1e12,
+                            "achieved_tflops_issued": 2.0 * rows_p * cols_p * R / (gemm_ms * 1e-3) / 1e12,
+                            "peak": PEAKS.get("bf16_tflops"),
+                            "peak_source": PEAKS["source"] + " cuBLAS bf16 burst"},
+                 "operator_gb": a_bytes / 1e9,
+                 "note": "operator [T_-1 T_0 T_1] in real 2x2 form, bfloat16, built once per geometry; "
+                         "the product streams it once for all R right-hand sides"}
 
     # the mixed-precision workload at its own size: M = 4000 disks of radius 0.004 on the same
     # grating and angle (100 000 unknowns); one warm-up geometry, one timed geometry
@@ -593,6 +675,7 @@ def main():
                                            "fp64_residual_launches": nmx64,
                                            "fp64_residual_ms": ms_mx64}),
             "mixed_c64_ir_M4000": bigres,
+            "translate_multi_tc_bf16": tcres,
             "batched_c64_ir": bres,
             "warm_start_fp64": wres,
         },

@@ -100,6 +100,7 @@ void free_geometry(gs_ctx *c) {
     if (c->tc_scratch) cudaFree(c->tc_scratch);
     c->tc_scratch = nullptr;
     c->tc_scratch_bytes = 0;
+    c->tc_zeroed_rp = c->tc_zeroed_k = c->tc_zeroed_R = -1;
     c->part_elems = 0;
     dfree(c->Vk);
     dfree(c->Hh);

@@ -94,6 +94,7 @@ struct gs_ctx {
     double tc_gamma = 1.0;                               // order rescaling of tcA (min(1, k2 r_min))
     void *tc_scratch = nullptr;                          // multi-right-hand-side scratch
     size_t tc_scratch_bytes = 0;
+    long tc_zeroed_rp = -1, tc_zeroed_k = -1, tc_zeroed_R = -1;   // padding of the scratch already zero
     double table_budget_gb = -1.0;                       // < 0: half of the free device memory
     size_t part_elems = 0;
     // GMRES workspace

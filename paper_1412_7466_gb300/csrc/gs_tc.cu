@@ -329,8 +329,12 @@ __global__ void k_tc_build_A(const double *__restrict__ xy, int M, double k, dou
 }
 
 // Bt[r][2(s nc + n) + b] = part b of a_r^l beta_r[j nc + n], s = (l+1) M + j (a_r^-1 = conj(a_r))
+struct GammaPow {
+    double inv[17];   // gamma^-e, e = 0..p (p <= 16)
+};
+
 __global__ void k_tc_pack_B(const cplx *__restrict__ beta, const cplx *__restrict__ alpha, int R, int M, int nc,
-                            double gamma, long ldb, __nv_bfloat16 *__restrict__ Bt) {
+                            GammaPow gpw, long ldb, __nv_bfloat16 *__restrict__ Bt) {
     const long n = (long)M * nc;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over R x 3n complex entries
     if (e >= (long)R * 3 * n) return;
@@ -340,19 +344,19 @@ __global__ void k_tc_pack_B(const cplx *__restrict__ beta, const cplx *__restric
     const cplx b = beta[(long)r * n + (q - (long)(l + 1) * n)];
     const cplx a = alpha[r];
     const int p = nc / 2, o = (int)(q % nc) - p;
-    const cplx v = cscale(l == 0 ? b : (l == 1 ? cmul(a, b) : cmul(cconj(a), b)), pow(gamma, -(double)abs(o)));
+    const cplx v = cscale(l == 0 ? b : (l == 1 ? cmul(a, b) : cmul(cconj(a), b)), gpw.inv[abs(o)]);
     ((__nv_bfloat162 *)(Bt + (long)r * ldb))[q] = __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
 
 // out_r[e] = (C[2e][r] + i C[2e+1][r]) / gamma^|m|, e = i nc + m
-__global__ void k_tc_unpack(const float *__restrict__ Cm, long ldc, int R, long n, int nc, double gamma,
+__global__ void k_tc_unpack(const float *__restrict__ Cm, long ldc, int R, long n, int nc, GammaPow gpw,
                             cplx *__restrict__ out) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)R * n) return;
     const int r = (int)(e / n);
     const long q = e - (long)r * n;
     const int o = (int)(q % nc) - nc / 2;
-    const double sc = pow(gamma, -(double)abs(o));
+    const double sc = gpw.inv[abs(o)];
     out[e] = C(sc * (double)Cm[(2 * q) * ldc + r], sc * (double)Cm[(2 * q + 1) * ldc + r]);
 }
 
@@ -448,6 +452,7 @@ extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, c
             return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (tensor-core scratch): ") + cudaGetErrorString(e));
         }
         c->tc_scratch_bytes = need;
+        c->tc_zeroed_rp = c->tc_zeroed_k = c->tc_zeroed_R = -1;
     }
     uint8_t *p = (uint8_t *)c->tc_scratch;
     cplx *al = (cplx *)p;
@@ -458,11 +463,20 @@ extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, c
     p += round_up(sizeof(float) * (size_t)Mr * Rp, 256);
     int *err = (int *)p;
     GS_CUDA(c, cudaMemcpyAsync(al, alpha_host, sizeof(cplx) * R, cudaMemcpyHostToDevice, st));
-    GS_CUDA(c, cudaMemsetAsync(Bt, 0, sizeof(__nv_bfloat16) * (size_t)Rp * K, st));
+    if (c->tc_zeroed_rp != Rp || c->tc_zeroed_k != K || c->tc_zeroed_R != R) {
+        // padding rows (r >= R) and columns (>= 6n) stay zero; the packing overwrites the rest
+        GS_CUDA(c, cudaMemsetAsync(Bt, 0, sizeof(__nv_bfloat16) * (size_t)Rp * K, st));
+        c->tc_zeroed_rp = Rp;
+        c->tc_zeroed_k = K;
+        c->tc_zeroed_R = R;
+    }
     GS_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), st));
+    GammaPow gpw;
+    gpw.inv[0] = 1.0;
+    for (int e = 1; e <= 16; ++e) gpw.inv[e] = gpw.inv[e - 1] / c->tc_gamma;
     GS_COUNT_LAUNCH(c);
-    k_tc_pack_B<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>((const cplx *)beta_dev, al, R, c->M, c->nc,
-                                                                 c->tc_gamma, K, Bt);
+    k_tc_pack_B<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>((const cplx *)beta_dev, al, R, c->M, c->nc, gpw, K,
+                                                                 Bt);
     GS_CHECK_LAUNCH(c);
     cudaEvent_t e0, e1;
     const bool timed = gs_prof_pair(c, &e0, &e1, GS_TC_BF16);
@@ -470,7 +484,7 @@ extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, c
     GS_TRY(gs_tc_gemm_impl(c, c->tcA, Bt, Cm, Mr, Rp, K, err, st));
     if (timed) cudaEventRecord(e1, st);
     GS_COUNT_LAUNCH(c);
-    k_tc_unpack<<<(int)((n * R + 255) / 256), 256, 0, st>>>(Cm, Rp, R, n, c->nc, c->tc_gamma, (cplx *)out_dev);
+    k_tc_unpack<<<(int)((n * R + 255) / 256), 256, 0, st>>>(Cm, Rp, R, n, c->nc, gpw, (cplx *)out_dev);
     GS_CHECK_LAUNCH(c);
     int herr = 0;
     GS_CUDA(c, cudaMemcpyAsync(c->hscal + 8, err, sizeof(int), cudaMemcpyDeviceToHost, st));
