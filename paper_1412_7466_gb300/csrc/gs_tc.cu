@@ -255,11 +255,8 @@ int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, l
     CUtensorMap ma, mb;
     GS_TRY(make_map(c, &ma, A, M, K, TBM));
     GS_TRY(make_map(c, &mb, B, N, K, TBN));
-    static bool attr = false;
-    if (!attr) {
-        GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
-        attr = true;
-    }
+    // the function attribute is per device: set it on every call (cheap, host-side only)
+    GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
     GS_COUNT_LAUNCH(c);
     k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN)), 128, TSMEM, st>>>(ma, mb, C, (int)M, (int)N, (int)K,
                                                                                  err_dev);
