@@ -125,6 +125,7 @@ void free_factor(gs_ctx *c, bool keep_batch = false) {
     dfree(c->Vtmp);
     dfree(c->Xtmp);
     dfree(c->Vxtmp);
+    dfree(c->X32tmp);
     dfree(c->nrm2);
     dfree(c->perm);
     dfree(c->tau);
@@ -185,6 +186,7 @@ int gs_ensure_grating(gs_ctx *c) {
         GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
         GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
         GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->X32tmp, (size_t)ly.cols * ly.cols));
         GS_TRY(dalloc(c, &c->nrm2, ly.cols));
         GS_TRY(dalloc(c, &c->perm, ly.cols));
         GS_TRY(dalloc(c, &c->tau, ly.cols));
@@ -209,6 +211,7 @@ int gs_ensure_grating(gs_ctx *c) {
         dfree(c->Vtmp);
         dfree(c->Xtmp);
         dfree(c->Vxtmp);
+        dfree(c->X32tmp);
         c->grating_ready = true;
     }
     return GS_OK;

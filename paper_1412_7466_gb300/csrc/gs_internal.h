@@ -35,7 +35,8 @@ struct AngleData {
     cplx *B = nullptr;           // n x nB row-major (physical sign)
     cplx *Cm = nullptr;          // nC x n row-major
     cplx *beta = nullptr;        // n, last solution
-    int sweeps = 0;
+    int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
+    int sweeps32 = 0;            // FP32-guided sweeps before them
     int iters = 0;               // GMRES iterations (all inner iterations for the mixed solve)
     int outer = 0;               // refinement sweeps of the mixed solve (0 for FP64)
     double relres = -1.0;
@@ -82,6 +83,7 @@ struct gs_ctx {
     cplx *w = nullptr, *x = nullptr;                     // cols
     cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
     cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
+    float2 *X32tmp = nullptr;                            // cols x cols, FP32 copy of R^* (guided sweeps)
     double *nrm2 = nullptr;                              // cols, trailing column norms
     int *perm = nullptr;                                 // cols, column pivots
     cplx *tau = nullptr;                                 // cols, reflector scalars

@@ -7,7 +7,13 @@
 //      recomputes that column's trailing norm);
 //   2. one-sided (Hestenes) Jacobi on X = R^*: column pairs of X are rotated until every pair is
 //      orthogonal to relative precision tol, giving X V_x = W_x with orthogonal columns; pairs
-//      follow the round-robin (circle) schedule, n/2 disjoint pairs per launch, one block per pair;
+//      follow the round-robin (circle) schedule, n/2 disjoint pairs per launch, one block per pair.
+//      The sweeps run in two phases: first the rotations are chosen from an FP32 copy of R^*
+//      (dot products and the copy's own rotation in FP32) and accumulated into V_x in FP64 with
+//      exactly orthogonal FP64 cosines and sines; then X = R^* V_x is formed in FP64 and ordinary
+//      FP64 sweeps take its nearly orthogonal columns (1e-5) to tol in a few quadratically
+//      convergent sweeps.  The result is the FP64 one-sided Jacobi SVD; FP32 only decides most
+//      of the rotations, at 64 times the FP64 rate;
 //   3. R = V_x W_x^*, hence A D = (Q V_x) Sigma (P W_x Sigma^{-1})^*: U = Q V_x is formed by
 //      applying the reflectors to V_x, and V Sigma = P W_x.
 // U is orthonormal to working precision by construction (reflectors and rotations), which keeps
@@ -97,6 +103,137 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
         cplx x = vp[i], y = cmul(vq[i], e);
         vp[i] = csub(cscale(x, cc), cscale(y, ss));
         vq[i] = cadd(cscale(x, ss), cscale(y, cc));
+    }
+}
+
+// FP32 copy of a complex128 array
+__global__ void k_to_c64(const cplx *__restrict__ X, long n, float2 *__restrict__ Y) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) Y[e] = make_float2((float)X[e].x, (float)X[e].y);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float block_sum_f(float v, float *sh) {
+    v = warp_sum_f(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    float t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.f;
+    if (w == 0) t = warp_sum_f(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const float r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Guided round: the rotation of each pair is chosen from the FP32 copy W32 (dot products and the
+// rotation of W32 in FP32) and applied to the accumulated rotations V in FP64 with cosine and sine
+// recomputed in FP64 (c = 1/sqrt(1 + t^2), s = c t), so V stays orthonormal to FP64 precision.
+__global__ void __launch_bounds__(JTPB) k_jacobi_round_guided(float2 *W32, int m, cplx *V, int n, int r, int npad,
+                                                              float tol, unsigned long long *nrot) {
+    int k = blockIdx.x;
+    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
+    int a = player(k), b = player(npad - 1 - k);
+    if (a >= n || b >= n) return;
+    int pc = a < b ? a : b, qc = a < b ? b : a;
+    float2 *wp = W32 + (size_t)pc * m, *wq = W32 + (size_t)qc * m;
+    __shared__ float sh[32];
+    __shared__ double rot[4];
+    float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 x = wp[i], y = wq[i];
+        al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
+        be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
+        gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));   // conj(x) y
+        gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+    }
+    al = block_sum_f(al, sh);
+    be = block_sum_f(be, sh);
+    gr = block_sum_f(gr, sh);
+    gi = block_sum_f(gi, sh);
+    if (threadIdx.x == 0) {
+        const double g = hypot((double)gr, (double)gi);
+        if (g == 0.0 || g <= (double)tol * sqrt((double)al * (double)be)) {
+            rot[0] = 0.0;
+        } else {
+            const double zeta = ((double)be - (double)al) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cc = 1.0 / sqrt(1.0 + t * t);
+            rot[0] = 1.0;
+            rot[1] = cc;
+            rot[2] = cc * t;
+            rot[3] = atan2((double)gi, (double)gr);
+            atomicAdd(nrot, 1ull);
+        }
+    }
+    __syncthreads();
+    if (rot[0] == 0.0) return;
+    const double cc = rot[1], ss = rot[2];
+    const cplx e = cexpi(-rot[3]);   // e^{-i phi}, phi = arg(conj(w_p) w_q)
+    const float cf = (float)cc, sf = (float)ss, er = (float)e.x, ei = (float)e.y;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 x = wp[i], y0 = wq[i];
+        const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+        wp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
+        wq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
+    }
+    cplx *vp = V + (size_t)pc * n, *vq = V + (size_t)qc * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        cplx x = vp[i], y = cmul(vq[i], e);
+        vp[i] = csub(cscale(x, cc), cscale(y, ss));
+        vq[i] = cadd(cscale(x, ss), cscale(y, cc));
+    }
+}
+
+// C = A B, complex128, all n x n column-major (64 x 64 tile per block, 4 x 4 per thread)
+constexpr int ZG = 64, ZK = 8;
+__global__ void __launch_bounds__(256) k_zgemm_nn(const cplx *__restrict__ A, const cplx *__restrict__ B,
+                                                  cplx *__restrict__ Cm, int n) {
+    __shared__ cplx As[ZK][ZG + 1], Bs[ZK][ZG + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * ZG, j0 = blockIdx.y * ZG;
+    cplx acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = C(0.0, 0.0);
+    for (int k0 = 0; k0 < n; k0 += ZK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ZG * ZK; e += 256) {
+            const int i = e % ZG, k = e / ZG;
+            As[k][i] = (i0 + i < n && k0 + k < n) ? A[(size_t)(k0 + k) * n + i0 + i] : C(0.0, 0.0);
+            const int kk = e % ZK, j = e / ZK;
+            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? B[(size_t)(j0 + j) * n + k0 + kk] : C(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ZK; ++k) {
+            cplx a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = i0 + ty + 16 * i;
+        if (row >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = j0 + tx + 16 * j;
+            if (col < n) Cm[(size_t)col * n + row] = acc[i][j];
+        }
     }
 }
 
@@ -351,6 +488,31 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     k_identity<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(Vx, n);
     GS_CHECK_LAUNCH(c);
     int npad = n + (n & 1);
+    // 2a. rotations chosen in FP32 (64x the FP64 rate) on a copy of R^*, accumulated in FP64 into V_x,
+    //     until no pair is further than 1e-5 from orthogonal at FP32 resolution
+    const long nn = (long)n * n;
+    GS_COUNT_LAUNCH(c);
+    k_to_c64<<<(int)((nn + 255) / 256), 256, 0, st>>>(X, nn, c->X32tmp);
+    GS_CHECK_LAUNCH(c);
+    a.sweeps32 = 0;
+    for (int sweep = 0; sweep < 20; ++sweep) {
+        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
+        for (int r = 0; r < npad - 1; ++r) {
+            GS_COUNT_LAUNCH(c);
+            k_jacobi_round_guided<<<npad / 2, JTPB, 0, st>>>(c->X32tmp, n, Vx, n, r, npad, 1e-5f, c->dcount);
+        }
+        GS_CHECK_LAUNCH(c);
+        unsigned long long h = 0;
+        GS_CUDA(c, cudaMemcpyAsync(&h, c->dcount, sizeof(h), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(c, cudaStreamSynchronize(st));
+        a.sweeps32 = sweep + 1;
+        if (h == 0) break;
+    }
+    // 2b. X = R^* V_x in FP64 (its columns are orthogonal to ~1e-6), then FP64 sweeps finish
+    GS_COUNT_LAUNCH(c);
+    k_zgemm_nn<<<dim3((n + ZG - 1) / ZG, (n + ZG - 1) / ZG), 256, 0, st>>>(X, Vx, a.Vr, n);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaMemcpyAsync(X, a.Vr, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
     const double tol = 1e-14;
     a.sweeps = 0;
     for (int sweep = 0; sweep < 30; ++sweep) {
