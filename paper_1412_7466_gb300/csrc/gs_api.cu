@@ -186,7 +186,7 @@ int gs_ensure_grating(gs_ctx *c) {
         GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
         GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
         GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
-        GS_TRY(dalloc(c, &c->X32tmp, (size_t)ly.cols * ly.cols));
+        GS_TRY(dalloc(c, &c->X32tmp, 2 * (size_t)ly.cols * ly.cols));
         GS_TRY(dalloc(c, &c->nrm2, ly.cols));
         GS_TRY(dalloc(c, &c->perm, ly.cols));
         GS_TRY(dalloc(c, &c->tau, ly.cols));

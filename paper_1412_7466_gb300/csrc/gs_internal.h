@@ -83,7 +83,7 @@ struct gs_ctx {
     cplx *w = nullptr, *x = nullptr;                     // cols
     cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
     cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
-    float2 *X32tmp = nullptr;                            // cols x cols, FP32 copy of R^* (guided sweeps)
+    float2 *X32tmp = nullptr;                            // 2 x cols x cols: FP32 copy of R^* and its rotations
     double *nrm2 = nullptr;                              // cols, trailing column norms
     int *perm = nullptr;                                 // cols, column pivots
     cplx *tau = nullptr;                                 // cols, reflector scalars

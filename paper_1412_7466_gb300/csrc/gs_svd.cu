@@ -8,18 +8,21 @@
 //   2. one-sided (Hestenes) Jacobi on X = R^*: column pairs of X are rotated until every pair is
 //      orthogonal to relative precision tol, giving X V_x = W_x with orthogonal columns; pairs
 //      follow the round-robin (circle) schedule, n/2 disjoint pairs per launch, one block per pair.
-//      The sweeps run in two phases: first the rotations are chosen from an FP32 copy of R^*
-//      (dot products and the copy's own rotation in FP32) and accumulated into V_x in FP64 with
-//      exactly orthogonal FP64 cosines and sines; then X = R^* V_x is formed in FP64 and ordinary
-//      FP64 sweeps take its nearly orthogonal columns (1e-5) to tol in a few quadratically
-//      convergent sweeps.  The result is the FP64 one-sided Jacobi SVD; FP32 only decides most
-//      of the rotations, at 64 times the FP64 rate;
+//      The sweeps run in two phases: first an FP32 copy of R^* is swept in FP32 (64 times the FP64
+//      rate) with its rotations accumulated in FP32; their product is made orthonormal to FP64
+//      precision by Newton-Schulz steps V <- V (3I - V^H V)/2 (quadratic convergence from the
+//      ~1e-5 defect); then X = R^* V is formed in FP64 and ordinary FP64 sweeps take its nearly
+//      orthogonal columns to tol in a few quadratically convergent sweeps, continuing to
+//      accumulate into V.  The result is an FP64 one-sided Jacobi SVD; FP32 only does the bulk of
+//      the rotating;
 //   3. R = V_x W_x^*, hence A D = (Q V_x) Sigma (P W_x Sigma^{-1})^*: U = Q V_x is formed by
 //      applying the reflectors to V_x, and V Sigma = P W_x.
 // U is orthonormal to working precision by construction (reflectors and rotations), which keeps
 // the clipped pseudo-inverse safe in the near-null directions.  A^+ g = D V Sigma^+ U^* g with
 // Sigma^+ = min(1/sigma, 1/eps) (Eq. applypA) is applied as D (P W_x) (coef .* (U^* g)) with
 // coef_j = 1/(sigma_j max(sigma_j, eps)), sigma_j = ||W_x e_j||.
+#include <cstring>
+
 #include "gs_internal.h"
 
 namespace {
@@ -132,11 +135,11 @@ __device__ __forceinline__ float block_sum_f(float v, float *sh) {
     return r;
 }
 
-// Guided round: the rotation of each pair is chosen from the FP32 copy W32 (dot products and the
-// rotation of W32 in FP32) and applied to the accumulated rotations V in FP64 with cosine and sine
-// recomputed in FP64 (c = 1/sqrt(1 + t^2), s = c t), so V stays orthonormal to FP64 precision.
-__global__ void __launch_bounds__(JTPB) k_jacobi_round_guided(float2 *W32, int m, cplx *V, int n, int r, int npad,
-                                                              float tol, unsigned long long *nrot) {
+// FP32 round on the copy W32 with the rotations accumulated in V (FP32), one block per pair: the
+// pair's rotation is computed in FP64 from FP32 dot products and applied in FP32.  (One warp per
+// pair was measured slower: a round then has too few blocks to hide the memory latency.)
+__global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, float2 *V, int n, int r, int npad,
+                                                           float tol, unsigned long long *nrot) {
     int k = blockIdx.x;
     auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
     int a = player(k), b = player(npad - 1 - k);
@@ -176,20 +179,59 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_guided(float2 *W32, int m
     if (rot[0] == 0.0) return;
     const double cc = rot[1], ss = rot[2];
     const cplx e = cexpi(-rot[3]);   // e^{-i phi}, phi = arg(conj(w_p) w_q)
-    const float cf = (float)cc, sf = (float)ss, er = (float)e.x, ei = (float)e.y;
+    const float cf = (float)cc, sf = (float)ss, er = (float)e.x, ei = (float)e.y;   // applied in FP32
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const float2 x = wp[i], y0 = wq[i];
         const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
         wp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
         wq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
     }
-    cplx *vp = V + (size_t)pc * n, *vq = V + (size_t)qc * n;
+    float2 *vp = V + (size_t)pc * n, *vq = V + (size_t)qc * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        cplx x = vp[i], y = cmul(vq[i], e);
-        vp[i] = csub(cscale(x, cc), cscale(y, ss));
-        vq[i] = cadd(cscale(x, ss), cscale(y, cc));
+        const float2 x = vp[i], y0 = vq[i];
+        const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+        vp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
+        vq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
     }
 }
+
+__global__ void k_identity_f32(float2 *V, int n) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    int r = (int)(id % n), c = (int)(id / n);
+    V[id] = make_float2(r == c ? 1.f : 0.f, 0.f);
+}
+
+__global__ void k_to_c128(const float2 *__restrict__ X, long n, cplx *__restrict__ Y) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) Y[e] = C((double)X[e].x, (double)X[e].y);
+}
+
+// G <- 1.5 I - 0.5 G (Newton-Schulz step towards the orthogonal polar factor)
+__global__ void k_ns_step(cplx *G, int n) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    int r = (int)(id % n), c = (int)(id / n);
+    const cplx g = G[id];
+    G[id] = C((r == c ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+}
+
+// out = max |G - I| (non-negative doubles order like their bit patterns)
+__global__ void k_offdiag_max(const cplx *G, int n, unsigned long long *out) {
+    long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (id < (long)n * n) {
+        int r = (int)(id % n), c = (int)(id / n);
+        const cplx g = G[id];
+        v = hypot(g.x - (r == c ? 1.0 : 0.0), g.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+// C = A^H B, complex128, all n x n column-major
+__global__ void __launch_bounds__(256) k_zgemm_hn(const cplx *__restrict__ A, const cplx *__restrict__ B,
+                                                  cplx *__restrict__ Cm, int n);
 
 // C = A B, complex128, all n x n column-major (64 x 64 tile per block, 4 x 4 per thread)
 constexpr int ZG = 64, ZK = 8;
@@ -210,6 +252,50 @@ __global__ void __launch_bounds__(256) k_zgemm_nn(const cplx *__restrict__ A, co
             As[k][i] = (i0 + i < n && k0 + k < n) ? A[(size_t)(k0 + k) * n + i0 + i] : C(0.0, 0.0);
             const int kk = e % ZK, j = e / ZK;
             Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? B[(size_t)(j0 + j) * n + k0 + kk] : C(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ZK; ++k) {
+            cplx a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = i0 + ty + 16 * i;
+        if (row >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = j0 + tx + 16 * j;
+            if (col < n) Cm[(size_t)col * n + row] = acc[i][j];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_zgemm_hn(const cplx *__restrict__ A, const cplx *__restrict__ B,
+                                                  cplx *__restrict__ Cm, int n) {
+    __shared__ cplx As[ZK][ZG + 1], Bs[ZK][ZG + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * ZG, j0 = blockIdx.y * ZG;
+    cplx acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = C(0.0, 0.0);
+    for (int k0 = 0; k0 < n; k0 += ZK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ZG * ZK; e += 256) {
+            const int kk = e % ZK, idx = e / ZK;
+            // (A^H)[i][k] = conj(A[k][i]); column i of A is contiguous in k
+            As[kk][idx] = (i0 + idx < n && k0 + kk < n) ? cconj(A[(size_t)(i0 + idx) * n + k0 + kk]) : C(0.0, 0.0);
+            Bs[kk][idx] = (k0 + kk < n && j0 + idx < n) ? B[(size_t)(j0 + idx) * n + k0 + kk] : C(0.0, 0.0);
         }
         __syncthreads();
 #pragma unroll
@@ -488,18 +574,22 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     k_identity<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(Vx, n);
     GS_CHECK_LAUNCH(c);
     int npad = n + (n & 1);
-    // 2a. rotations chosen in FP32 (64x the FP64 rate) on a copy of R^*, accumulated in FP64 into V_x,
-    //     until no pair is further than 1e-5 from orthogonal at FP32 resolution
+    // 2a. FP32 sweeps on a copy of R^*, rotations accumulated in FP32, until no pair is further
+    //     than 1e-5 from orthogonal at FP32 resolution
     const long nn = (long)n * n;
+    const int eb = (int)((nn + 255) / 256);
+    float2 *X32 = c->X32tmp, *V32 = c->X32tmp + nn;
     GS_COUNT_LAUNCH(c);
-    k_to_c64<<<(int)((nn + 255) / 256), 256, 0, st>>>(X, nn, c->X32tmp);
+    k_to_c64<<<eb, 256, 0, st>>>(X, nn, X32);
+    GS_COUNT_LAUNCH(c);
+    k_identity_f32<<<eb, 256, 0, st>>>(V32, n);
     GS_CHECK_LAUNCH(c);
     a.sweeps32 = 0;
     for (int sweep = 0; sweep < 20; ++sweep) {
         GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
         for (int r = 0; r < npad - 1; ++r) {
             GS_COUNT_LAUNCH(c);
-            k_jacobi_round_guided<<<npad / 2, JTPB, 0, st>>>(c->X32tmp, n, Vx, n, r, npad, 1e-5f, c->dcount);
+            k_jacobi_round_f32<<<npad / 2, JTPB, 0, st>>>(X32, n, V32, n, r, npad, 1e-5f, c->dcount);
         }
         GS_CHECK_LAUNCH(c);
         unsigned long long h = 0;
@@ -508,11 +598,36 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         a.sweeps32 = sweep + 1;
         if (h == 0) break;
     }
-    // 2b. X = R^* V_x in FP64 (its columns are orthogonal to ~1e-6), then FP64 sweeps finish
+    // 2b. V_x = the FP64 orthogonal polar factor of V32 (Newton-Schulz, V <- V (3I - V^H V)/2,
+    //     quadratic from an orthogonality defect of ~1e-5), then X = R^* V_x in FP64
+    const dim3 zg((n + ZG - 1) / ZG, (n + ZG - 1) / ZG);
+    cplx *G = a.Vr, *T = a.W;   // n x n scratch (both are written later)
     GS_COUNT_LAUNCH(c);
-    k_zgemm_nn<<<dim3((n + ZG - 1) / ZG, (n + ZG - 1) / ZG), 256, 0, st>>>(X, Vx, a.Vr, n);
+    k_to_c128<<<eb, 256, 0, st>>>(V32, nn, Vx);
+    for (int it = 0; it < 6; ++it) {
+        GS_COUNT_LAUNCH(c);
+        k_zgemm_hn<<<zg, 256, 0, st>>>(Vx, Vx, G, n);
+        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
+        GS_COUNT_LAUNCH(c);
+        k_offdiag_max<<<eb, 256, 0, st>>>(G, n, c->dcount);
+        GS_CHECK_LAUNCH(c);
+        unsigned long long hb = 0;
+        GS_CUDA(c, cudaMemcpyAsync(&hb, c->dcount, sizeof(hb), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(c, cudaStreamSynchronize(st));
+        double defect;
+        std::memcpy(&defect, &hb, sizeof(defect));
+        if (!(defect < 0.5)) return gs_fail(c, GS_ERR_NUMERIC, "grating factorisation: FP32 rotations not orthogonal");
+        if (defect < 1e-14) break;
+        GS_COUNT_LAUNCH(c);
+        k_ns_step<<<eb, 256, 0, st>>>(G, n);
+        GS_COUNT_LAUNCH(c);
+        k_zgemm_nn<<<zg, 256, 0, st>>>(Vx, G, T, n);
+        GS_CUDA(c, cudaMemcpyAsync(Vx, T, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
+    }
+    GS_COUNT_LAUNCH(c);
+    k_zgemm_nn<<<zg, 256, 0, st>>>(X, Vx, T, n);
     GS_CHECK_LAUNCH(c);
-    GS_CUDA(c, cudaMemcpyAsync(X, a.Vr, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(c, cudaMemcpyAsync(X, T, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
     const double tol = 1e-14;
     a.sweeps = 0;
     for (int sweep = 0; sweep < 30; ++sweep) {
