@@ -56,6 +56,27 @@ except (OSError, ValueError):
 TAB_DRAM_BYTES_PER_PAIR = 599.577344e6 / (3 * 500 ** 2 - 500)
 
 
+def geometry_seeds(rank: int, n_geo: int) -> list:
+    """Seeds of the geometries rank `rank` solves: distinct across ranks (replicas do independent
+    work; nothing is exchanged on the data path)."""
+    return [1000 * (rank + 1) + s for s in range(n_geo)]
+
+
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The job's time for a quantity every rank measured: the maximum over the ranks."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, elapsed_max: float) -> float:
+    """Whole-job solves/s: every rank solves `steps` geometries; the job ends with the slowest."""
+    return world * steps / elapsed_max
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,7 +300,7 @@ def main():
 
     # seeded geometries, one per step (distinct per rank); host arrays prepared before timing
     n_geo = args.warmup + args.steps
-    geos = [W.config("headline", seed=1000 * (rank + 1) + s)["disks"] for s in range(n_geo)]
+    geos = [W.config("headline", seed=sd)["disks"] for sd in geometry_seeds(rank, n_geo)]
 
     def barrier():
         if dist:
@@ -318,10 +339,7 @@ def main():
         if gather_profile:
             prof = {"fp64": gs.profile_read(GS_FP64), "c64": gs.profile_read(GS_C64)}
             gs.profile(False)
-        if dist:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(tot, dist, "cuda")
         return {"elapsed": tot, "launches": int(l1 - l0), "iters": its, "clocks": clk.summary(), "prof": prof}
 
     def e2e(precision):
@@ -333,11 +351,7 @@ def main():
             gs.solve(tol=tol, maxit=4000, restart=500, precision=precision)
             br = gs.bragg()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         return el, br
 
     def golden_error(precision):
@@ -625,8 +639,8 @@ def main():
     nmx64, ms_mx64 = rmx["prof"]["fp64"]
     avg32 = ms_mx32 / max(nmx32, 1)
     ach32 = flops_per_launch / (avg32 * 1e-3) / 1e12
-    value = world * args.steps / r64["elapsed"]
-    value_mx = world * args.steps / rmx["elapsed"]
+    value = job_throughput(world, args.steps, r64["elapsed"])
+    value_mx = job_throughput(world, args.steps, rmx["elapsed"])
     d2h = res["fp64"]["n_cd"] * (16 + 4) + 8
 
     def variant(name, vv, rr, dtype):
@@ -634,7 +648,7 @@ def main():
         return {"value": vv, "unit": "solves/s", "dtype": dtype, "ms_per_step": 1e3 * rr["elapsed"] / args.steps,
                 "gmres_iters_per_step": rr["iters"], "bragg_rel_err_vs_oracle": x["err"], "flux_err": x["flux"],
                 "refinement_sweeps": x["outer"], "gpu_launches": rr["launches"], "clocks": rr["clocks"],
-                "e2e": {"value": world * args.steps / x["e2e"], "unit": "solves/s",
+                "e2e": {"value": job_throughput(world, args.steps, x["e2e"]), "unit": "solves/s",
                         "h2d_bytes_per_step": M * 4 * 8, "d2h_bytes_per_step": d2h}}
 
     per_step_grating = grating_ms / 1e3
@@ -660,7 +674,7 @@ def main():
                      "launches_timed": n64},
         "clocks": r64["clocks"],
         "gpu_launches": r64["launches"],
-        "e2e": {"value": world * args.steps / res["fp64"]["e2e"], "unit": "solves/s",
+        "e2e": {"value": job_throughput(world, args.steps, res["fp64"]["e2e"]), "unit": "solves/s",
                 "h2d_bytes_per_step": M * 4 * 8, "d2h_bytes_per_step": d2h},
         "variants": {
             "plain_fp64": variant("fp64", value, r64, "f64"),
