@@ -230,6 +230,15 @@ int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms)
 #define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
 
+/* Total field in the layer holding the inclusions at npts points (the paper's field plots; Sec. 3
+ * Eq. repre3 and Sec. 5 Eq. repre3_mod with the last solution at `angle`): interface potentials
+ * (k2, +-d copies), the far-copy J-expansion and the inclusions' outgoing fields (+-d copies).
+ * xy_dev holds (x, y) pairs, u_dev receives complex128 values (device arrays, caller-owned).
+ * Points outside one period of the middle layer (|x| > d/2 or not strictly between the
+ * interfaces) or inside an inclusion give NaN; accuracy is that of the trapezoid rule, i.e. a few
+ * node spacings (d/N) away from the interfaces.  Needs gs_solve at this angle (GS_ERR_STATE). */
+int gs_field(gs_ctx *ctx, int angle, long npts, const double *xy_dev, gs_c128 *u_dev);
+
 /* alpha_r = T(theta_r) beta_r for R right-hand sides at once (R incidence angles of the current
  * geometry; Sec. 4.2 Eq. trans with each angle's image phase a_r = exp(i k1 cos(theta_r) d), passed
  * in alpha_host[r]).  beta_dev and out_dev hold R consecutive vectors of length n (caller-owned

@@ -96,6 +96,7 @@ _SIGS = {
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
     "gs_tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_long, ctypes.c_long, ctypes.c_long]),
     "gs_translate_multi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "gs_field": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_long, _vp, _vp]),
     "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
     "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "gs_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -467,6 +468,16 @@ class GratingSolver:
         self._check(self.lib.gs_warm_start(self.ctx, angle, _ptr(b0), ctypes.byref(rel), ctypes.byref(used)),
                     "gs_warm_start")
         return b0, rel.value, bool(used.value)
+
+    def field(self, pts, angle=0):
+        """Total field in the middle layer at points pts ((npts, 2) array) from the last solution;
+        NaN outside one period of the layer or inside an inclusion.  Returns a complex128 tensor."""
+        P = self.torch.as_tensor(pts).to(device=self.device, dtype=self.torch.float64).contiguous()
+        if P.dim() != 2 or P.shape[1] != 2:
+            raise ValueError("pts must be (npts, 2)")
+        u = self._cvec(P.shape[0])
+        self._check(self.lib.gs_field(self.ctx, angle, P.shape[0], _ptr(P), _ptr(u)), "gs_field")
+        return u
 
     def translate_multi(self, alphas, betas):
         """Translations of R right-hand sides (rows of betas, (R, n) complex) with image phases

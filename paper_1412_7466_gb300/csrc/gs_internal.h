@@ -179,3 +179,5 @@ int gs_incoming_impl(gs_ctx *c, const AngleData &a, cplx *w);
 int gs_layer_response_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *z);
 int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x0);
 int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux);
+// a = A^+ (f - C beta) for the last solution at this angle (cols)
+int gs_layer_unknowns_impl(gs_ctx *c, const AngleData &a, cplx *x);

@@ -474,6 +474,15 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
 }
 
 // Bragg amplitudes: x_cd = D_cd .* V[cd rows] (coef .* W^* (f - C beta)); flux error on the device.
+// a = A^+ (f - C beta): every layer unknown of the last solution (cols)
+int gs_layer_unknowns_impl(gs_ctx *c, const AngleData &a, cplx *x) {
+    const Layout &ly = c->lay;
+    GS_COUNT_LAUNCH(c);
+    k_f_minus_Cx<<<warps_blocks(ly.rows), 256, 0, c->stream>>>(a.Cm, ly.nC(), c->n(), a.beta, a.f, ly.rows, c->g);
+    GS_CHECK_LAUNCH(c);
+    return gs_pinv_impl(c, a, c->g, x);
+}
+
 int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux) {
     const Layout &ly = c->lay;
     int n = c->n();
