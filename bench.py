@@ -85,6 +85,7 @@ def run_study(device: int) -> dict:
     500), time per solve (device events) and the flux error; the grating factorisation per
     configuration is reported separately."""
     import torch
+    import workloads as W
     from paper_1412_7466_gb300 import GratingSolver
 
     def one(g, theta, dk):
