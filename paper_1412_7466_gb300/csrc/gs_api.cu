@@ -63,6 +63,7 @@ void dfree(T *&p) {
 void free_angle_geometry(AngleData &a) {
     dfree(a.B);
     dfree(a.Cm);
+    dfree(a.B32);
     dfree(a.beta);
     a.iters = 0;
     a.outer = 0;

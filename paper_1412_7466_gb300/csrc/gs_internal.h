@@ -34,6 +34,7 @@ struct AngleData {
     double *sigma = nullptr;     // cols
     cplx *B = nullptr;           // n x nB row-major (physical sign)
     cplx *Cm = nullptr;          // nC x n row-major
+    mutable float2 *B32 = nullptr;   // complex64 copy of B for the mixed inner operator (on first use)
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
     int sweeps32 = 0;            // FP32-guided sweeps before them

@@ -61,6 +61,41 @@ __global__ void k_B_combine(const cplx *__restrict__ B, int n, int nB, const cpl
     }
 }
 
+// ---- complex64 low rank (inner operator of the mixed solve) ----------------------------------------
+// A complex FP64 matrix-vector product needs 0.5 flop per byte, above the GB300's FP64 ridge
+// (1.26 TFLOP/s / 6.7 TB/s = 0.19): the FP64 products with B_phys and C are bound by the FP64
+// pipe.  The inner operator of the mixed solve (whose translation is complex64 anyway) reads a
+// complex64 copy of B_phys instead: half the bytes, FP32 arithmetic, HBM-bound.  B_phys acts last
+// (after A^+), so its FP32 rounding is not amplified; C x stays FP64 (see gs_apply_impl).
+
+__global__ void k_to_c64_vec(const cplx *__restrict__ a, long n, float2 *__restrict__ b) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// y[r] = x[r] - s[r] t[r] + s[r] (B v)[r] with B complex64 (FP32 products), warp per row
+__global__ void k_B_combine32(const float2 *__restrict__ B, int n, int nB, const cplx *__restrict__ v,
+                              const cplx *__restrict__ x, const cplx *__restrict__ t, const cplx *__restrict__ s,
+                              cplx *__restrict__ y) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const float2 *b = B + (size_t)warp * nB;
+    float re = 0.f, im = 0.f;
+    for (int c = lane; c < nB; c += 32) {
+        const float2 m = b[c];
+        const cplx vv = __ldg(&v[c]);
+        const float wr = (float)vv.x, wi = (float)vv.y;
+        re = fmaf(m.x, wr, fmaf(-m.y, wi, re));
+        im = fmaf(m.x, wi, fmaf(m.y, wr, im));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) y[warp] = cadd(csub(x[warp], cmul(s[warp], t[warp])), cmul(s[warp], C(re, im)));
+}
+
 // g[r] = f[r] - (C x)[r] for r < nC, and f[r] for nC <= r < rows
 __global__ void k_f_minus_Cx(const cplx *__restrict__ Cm, int nC, int n, const cplx *__restrict__ x,
                              const cplx *__restrict__ f, int rows, cplx *__restrict__ g) {
@@ -251,6 +286,26 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
     int n = c->n(), nB = ly.nB(), nC = ly.nC();
     cplx *tx = c->v3;
     GS_TRY(gs_translate_impl(c, a, x, tx, precision));
+    if (precision == GS_C64) {
+        if (!a.B32) {   // complex64 copy of B_phys, once per geometry and angle
+            const long nb = (long)n * nB;
+            GS_CUDA(c, cudaMalloc((void **)&a.B32, sizeof(float2) * nb));
+            GS_COUNT_LAUNCH(c);
+            k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
+        }
+        // C x stays FP64: it feeds A^+, whose clipped Sigma^+ (up to 1/eps = 1e10 in the near-null
+        // directions) would amplify FP32 rounding of C x into the whole correction
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+        GS_COUNT_LAUNCH(c);
+        k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, tx, c->s, y);
+        GS_CHECK_LAUNCH(c);
+        return GS_OK;
+    }
     GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
     GS_COUNT_LAUNCH(c);

@@ -214,6 +214,19 @@ def test_translate_c64_matches_oracle(small):
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
+def test_operator_c64_matches_oracle(small):
+    """complex64 inner operator: complex64 translation and a complex64 copy of B_phys with FP32
+    products (C, U^*, V Sigma in FP64): single-precision accuracy, 1e-5 relative in norm."""
+    from paper_1412_7466_gb300 import GS_C64
+    cfg, prob, gs = small
+    rng = np.random.default_rng(6)
+    n = prob.M * prob.nc
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.tile(0.3 ** np.abs(np.arange(-prob.disks["p"], prob.disks["p"] + 1)), prob.M)
+    got = _np(gs.apply(x, precision=GS_C64))
+    ref = prob.apply(x)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
 def test_mixed_solve_small_bragg(small):
     """Mixed form (complex64 inner GMRES + FP64 refinement) reaches the same 1e-9 Bragg target."""
     from paper_1412_7466_gb300 import GS_C64
