@@ -104,6 +104,8 @@ void free_geometry(gs_ctx *c) {
     c->tc_zeroed_rp = c->tc_zeroed_k = c->tc_zeroed_R = -1;
     c->part_elems = 0;
     dfree(c->Vk);
+    dfree(c->kv1);
+    dfree(c->kv2);
     dfree(c->Hh);
     dfree(c->cs);
     dfree(c->sn);
@@ -168,6 +170,8 @@ int gs_ensure_krylov(gs_ctx *c, int restart) {
     const long n = c->n();
     c->kdim = want;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
+    GS_TRY(dalloc(c, &c->kv1, n));
+    GS_TRY(dalloc(c, &c->kv2, n));
     GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));
     GS_TRY(dalloc(c, &c->cs, c->kdim + 1));
     GS_TRY(dalloc(c, &c->sn, c->kdim + 1));
@@ -469,6 +473,10 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(gs_build_images_c64(c, c->xy, c->M, c->img32, c->stream));
     c->kdim = 200;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
+    GS_TRY(dalloc(c, &c->kv1, n));
+    GS_TRY(dalloc(c, &c->kv2, n));
+    GS_TRY(dalloc(c, &c->kv1, n));
+    GS_TRY(dalloc(c, &c->kv2, n));
     GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));
     GS_TRY(dalloc(c, &c->cs, c->kdim + 1));
     GS_TRY(dalloc(c, &c->sn, c->kdim + 1));

@@ -102,7 +102,8 @@ struct gs_ctx {
     size_t part_elems = 0;
     // GMRES workspace
     int kdim = 0;
-    cplx *Vk = nullptr;                                  // (kdim+1) x n
+    cplx *Vk = nullptr;                                  // (kdim+1) x n (complex64 basis: reinterpreted)
+    cplx *kv1 = nullptr, *kv2 = nullptr;                 // n each: complex64-basis GMRES work vectors
     cplx *Hh = nullptr;                                  // (kdim+1) x kdim column-major
     cplx *cs = nullptr, *sn = nullptr, *gg = nullptr, *yy = nullptr;
     double *dscal = nullptr;                             // device scalars

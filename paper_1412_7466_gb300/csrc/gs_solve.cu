@@ -362,6 +362,67 @@ __global__ void k_axpy_inplace(cplx *x, const cplx *y, long n) {
     if (e < n) x[e] = cadd(x[e], y[e]);
 }
 
+// ---- complex64 Krylov basis (inner GMRES of the mixed solve) ---------------------------------------
+// The CGS2 products with j basis vectors cost 16 j n flops per iteration; in FP64 they are bound by
+// the FP64 pipe (0.5 flop per byte).  The inner solves of the mixed form, solved to >= 1e-6 and
+// checked against their true residual, keep the basis in complex64 and do these products in FP32
+// (block sums in FP64); the operator still takes and returns FP64 vectors.
+
+// h[i] (+)= V_i^* w for i < cnt, V complex64, w complex128 (FP32 products), block per basis vector
+__global__ void k_dots32(const float2 *__restrict__ Vb, long n, const cplx *__restrict__ w, int cnt,
+                         cplx *__restrict__ h, int accumulate) {
+    const int i = blockIdx.x;
+    if (i >= cnt) return;
+    __shared__ double sh[32];
+    const float2 *v = Vb + (size_t)i * n;
+    float re = 0.f, im = 0.f;
+    for (long e = threadIdx.x; e < n; e += blockDim.x) {
+        const float2 a = v[e];
+        const cplx b = w[e];
+        const float br = (float)b.x, bi = (float)b.y;
+        re = fmaf(a.x, br, fmaf(a.y, bi, re));   // conj(a) b
+        im = fmaf(a.x, bi, fmaf(-a.y, br, im));
+    }
+    const double R = block_sum((double)re, sh), I = block_sum((double)im, sh);
+    if (threadIdx.x == 0) {
+        const cplx r = C(R, I);
+        h[i] = accumulate ? cadd(h[i], r) : r;
+    }
+}
+
+// w (+/-)= sum_{i < cnt} coef[i] V_i (sign -1: subtract), products in FP32; cnt <= GS_KMAX + 1
+__global__ void k_combo32(cplx *__restrict__ w, const float2 *__restrict__ Vb, long n, const cplx *__restrict__ coef,
+                          int cnt, float sign) {
+    __shared__ float2 cf[513];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = make_float2((float)coef[i].x, (float)coef[i].y);
+    __syncthreads();
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float sr = 0.f, si = 0.f;
+    for (int i = 0; i < cnt; ++i) {
+        const float2 v = Vb[(size_t)i * n + e], c = cf[i];
+        sr = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr));
+        si = fmaf(c.x, v.y, fmaf(c.y, v.x, si));
+    }
+    w[e] = cadd(w[e], C((double)(sign * sr), (double)(sign * si)));
+}
+
+// dst = src / norm[0] in complex64; records norm into Hsub (complex) if given
+__global__ void k_store32(const cplx *__restrict__ src, long n, const double *norm, float2 *__restrict__ dst,
+                          cplx *Hsub) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const double nv = norm[0];
+    if (e == 0 && Hsub) *Hsub = C(nv, 0.0);
+    if (e >= n) return;
+    const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+    dst[e] = make_float2((float)(src[e].x * inv), (float)(src[e].y * inv));
+}
+
+__global__ void k_load64(const float2 *__restrict__ v, long n, cplx *__restrict__ out) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = C((double)v[e].x, (double)v[e].y);
+}
+
 // Restarted GMRES (Saad-Schultz) with classical Gram-Schmidt applied twice and Givens rotations on
 // the device; the host reads one residual estimate per iteration.  Solves L_prec x = b from the
 // start x (zero when x_zero) until ||b - L_prec x|| <= tol * bnorm; the true residual is checked
@@ -453,6 +514,94 @@ int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx 
     return GS_OK;
 }
 
+// The same restarted GMRES with a complex64 basis (the inner solves of the mixed form): the basis
+// lives in Vk reinterpreted as complex64, the current vector and the operator output in kv1, kv2.
+int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx *x, double tol, int maxit,
+                 int restart, int *iters, double *relres) {
+    const long n = c->n();
+    cudaStream_t st = c->stream;
+    const int kd = std::min(restart, c->kdim);
+    const int ld = c->kdim + 1;
+    const int eb = (int)((n + 255) / 256);
+    float2 *V = (float2 *)c->Vk;
+    cplx *r = c->v2, *vj = c->kv1, *w = c->kv2;
+    double *ds = c->dscal;
+    int it = 0;
+    bool first = true;
+    double est = 1.0;
+    GS_CUDA(c, cudaMemsetAsync(x, 0, sizeof(cplx) * n, st));
+    while (it < maxit) {
+        if (first) {
+            GS_CUDA(c, cudaMemcpyAsync(r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            GS_TRY(gs_apply_impl(c, a, x, r, GS_C64));
+            GS_COUNT_LAUNCH(c);
+            k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+        }
+        first = false;
+        GS_COUNT_LAUNCH(c);
+        k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
+        GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(c, cudaStreamSynchronize(st));
+        est = c->hscal[1] / bnorm;
+        if (est <= tol) break;
+        GS_COUNT_LAUNCH(c);
+        k_store32<<<eb, 256, 0, st>>>(r, n, ds + 1, V, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_set_g0<<<(ld + 255) / 256, 256, 0, st>>>(c->gg, ld, ds + 1);
+        GS_CUDA(c, cudaMemsetAsync(c->Hh, 0, sizeof(cplx) * (size_t)ld * c->kdim, st));
+        int j = 0, kk = 0;
+        for (; j < kd && it < maxit; ++j) {
+            GS_COUNT_LAUNCH(c);
+            k_load64<<<eb, 256, 0, st>>>(V + (size_t)j * n, n, vj);
+            GS_TRY(gs_apply_impl(c, a, vj, w, GS_C64));
+            ++it;
+            cplx *h = c->Hh + (size_t)j * ld;
+            GS_COUNT_LAUNCH(c);
+            k_dots32<<<j + 1, 256, 0, st>>>(V, n, w, j + 1, h, 0);
+            GS_COUNT_LAUNCH(c);
+            k_combo32<<<eb, 256, 0, st>>>(w, V, n, h, j + 1, -1.f);
+            GS_COUNT_LAUNCH(c);
+            k_dots32<<<j + 1, 256, 0, st>>>(V, n, w, j + 1, c->yy, 0);
+            GS_COUNT_LAUNCH(c);
+            k_combo32<<<eb, 256, 0, st>>>(w, V, n, c->yy, j + 1, -1.f);
+            GS_COUNT_LAUNCH(c);
+            k_add_vec<<<1, 256, 0, st>>>(h, c->yy, j + 1);
+            GS_COUNT_LAUNCH(c);
+            k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
+            GS_COUNT_LAUNCH(c);
+            k_store32<<<eb, 256, 0, st>>>(w, n, ds + 3, V + (size_t)(j + 1) * n, h + j + 1);
+            GS_COUNT_LAUNCH(c);
+            k_givens<<<1, 128, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
+            GS_CHECK_LAUNCH(c);
+            GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            est = c->hscal[2] / bnorm;
+            kk = j + 1;
+            if (est <= tol) break;
+        }
+        GS_COUNT_LAUNCH(c);
+        k_backsolve<<<1, 256, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
+        GS_COUNT_LAUNCH(c);
+        k_combo32<<<eb, 256, 0, st>>>(x, V, n, c->yy, kk, 1.f);
+        GS_CHECK_LAUNCH(c);
+        if (est <= tol) {
+            GS_TRY(gs_apply_impl(c, a, x, r, GS_C64));
+            GS_COUNT_LAUNCH(c);
+            k_sub<<<eb, 256, 0, st>>>(b, r, n, r);
+            GS_COUNT_LAUNCH(c);
+            k_norm<<<1, 1024, 0, st>>>(r, n, ds + 1);
+            GS_CUDA(c, cudaMemcpyAsync(c->hscal + 1, ds + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            est = c->hscal[1] / bnorm;
+            if (est <= 10.0 * tol) break;
+        }
+    }
+    *iters = it;
+    *relres = est;
+    return GS_OK;
+}
+
 }  // namespace
 
 // FP64: GMRES on L.  GS_C64: iterative refinement with FP64 residuals and inner GMRES on the
@@ -517,7 +666,7 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
         int its = 0;
         double rr = 1.0;
         const double itol = std::max(floor_tol, 0.5 * o.tol / rel);
-        GS_TRY(gmres_core(c, a, r, rnorm, dx, true, itol, o.maxit - total, o.restart, GS_C64, &its, &rr));
+        GS_TRY(gmres_core32(c, a, r, rnorm, dx, itol, o.maxit - total, o.restart, &its, &rr));
         total += its;
         GS_COUNT_LAUNCH(c);
         k_axpy_inplace<<<eb, 256, 0, st>>>(x, dx, n);
