@@ -268,30 +268,90 @@ __global__ void k_batch_Bcombine(const cplx *__restrict__ Ball, long Ntot, int n
     }
 }
 
+// complex64 copy of B_g (FP32 products) for the mixed form's inner operator: B acts after A^+, so its
+// rounding is not amplified; C_g x stays FP64 (it feeds A^+, whose clipped Sigma^+ would)
+__global__ void k_batch_Bcombine32(const float2 *__restrict__ Ball, long Ntot, int nB, const int *__restrict__ gid,
+                                   int nc, const int *__restrict__ active, const cplx *__restrict__ vv, int ldv,
+                                   const cplx *__restrict__ x, const cplx *__restrict__ t, const cplx *__restrict__ s,
+                                   cplx *__restrict__ y) {
+    long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= Ntot) return;
+    const int g = gid[warp / nc];
+    if (active && !active[g]) return;
+    const float2 *b = Ball + (size_t)warp * nB;
+    const cplx *v = vv + (size_t)g * ldv;
+    float re = 0.f, im = 0.f;
+    for (int c = lane; c < nB; c += 32) {
+        const float2 m = b[c];
+        const cplx w = __ldg(&v[c]);
+        const float wr = (float)w.x, wi = (float)w.y;
+        re = fmaf(m.x, wr, fmaf(-m.y, wi, re));
+        im = fmaf(m.x, wi, fmaf(m.y, wr, im));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) y[warp] = cadd(csub(x[warp], cmul(s[warp], t[warp])), cmul(s[warp], C(re, im)));
+}
+
+__global__ void k_to_c64_b(const cplx *__restrict__ a, long n, float2 *__restrict__ b) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
 // ---- segmented GMRES kernels (step index j read from device memory) --------------------------------
+// Templated on the basis type: complex128 (FP64 solves) or complex64 (the inner solves of the mixed
+// form: FP32 products, FP64 block sums -- the FP64 products are bound by GB300's FP64 pipe).
+
+__device__ __forceinline__ cplx bget(const cplx *V, size_t i) { return V[i]; }
+__device__ __forceinline__ cplx bget(const float2 *V, size_t i) { const float2 v = V[i]; return C(v.x, v.y); }
+__device__ __forceinline__ void bput(cplx *V, size_t i, cplx v) { V[i] = v; }
+__device__ __forceinline__ void bput(float2 *V, size_t i, cplx v) { V[i] = make_float2((float)v.x, (float)v.y); }
+
+// re/im of sum_e conj(V[e]) w[e] over a thread's elements (FP64 basis: FP64; complex64: FP32)
+template <typename TB>
+__device__ __forceinline__ void seg_dot_part(const TB *v, const cplx *ww, size_t n, double &re, double &im) {
+    if constexpr (std::is_same<TB, cplx>::value) {
+        for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const cplx a = v[e], b = ww[e];
+            re += a.x * b.x + a.y * b.y;
+            im += a.x * b.y - a.y * b.x;
+        }
+    } else {
+        float fr = 0.f, fi = 0.f;
+        for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const float2 a = v[e];
+            const cplx b = ww[e];
+            const float br = (float)b.x, bi = (float)b.y;
+            fr = fmaf(a.x, br, fmaf(a.y, bi, fr));
+            fi = fmaf(a.x, bi, fmaf(-a.y, br, fi));
+        }
+        re = fr;
+        im = fi;
+    }
+}
 
 // X = V_j
-__global__ void k_seg_fetch(const cplx *__restrict__ Vb, long Ntot, const int *jdev, cplx *__restrict__ X) {
+template <typename TB>
+__global__ void k_seg_fetch(const TB *__restrict__ Vb, long Ntot, const int *jdev, cplx *__restrict__ X) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < Ntot) X[e] = Vb[(size_t)(*jdev) * Ntot + e];
+    if (e < Ntot) X[e] = bget(Vb, (size_t)(*jdev) * Ntot + e);
 }
 
 // h[g][i] (+)= V_i[g]^* w[g], i <= j, blocks (i, g); written into column j of H_g (ld = kdim+1)
-__global__ void k_seg_dots(const cplx *__restrict__ Vb, long Ntot, const cplx *__restrict__ w, const Geo *__restrict__ geo,
+template <typename TB>
+__global__ void k_seg_dots(const TB *__restrict__ Vb, long Ntot, const cplx *__restrict__ w, const Geo *__restrict__ geo,
                            int nc, const int *jdev, const int *__restrict__ active, cplx *__restrict__ H, int ld,
                            int kdim, int second) {
     const int i = blockIdx.x, g = blockIdx.y, j = *jdev;
     if (i > j || (active && !active[g])) return;
     __shared__ double sh[32];
     const size_t off = (size_t)geo[g].noff, n = (size_t)geo[g].M * nc;
-    const cplx *v = Vb + (size_t)i * Ntot + off;
-    const cplx *ww = w + off;
     double re = 0, im = 0;
-    for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
-        cplx a = v[e], b = ww[e];
-        re += a.x * b.x + a.y * b.y;
-        im += a.x * b.y - a.y * b.x;
-    }
+    seg_dot_part(Vb + (size_t)i * Ntot + off, w + off, n, re, im);
     re = block_sum(re, sh);
     im = block_sum(im, sh);
     if (threadIdx.x == 0) {
@@ -303,27 +363,23 @@ __global__ void k_seg_dots(const cplx *__restrict__ Vb, long Ntot, const cplx *_
 // per-geometry copy of the CGS coefficients of the current pass: hp[g][i] = value just written
 // (the second pass accumulates into H and subtracts only its own contribution, so the pass-2
 // coefficients are staged separately)
-__global__ void k_seg_dots2(const cplx *__restrict__ Vb, long Ntot, const cplx *__restrict__ w, const Geo *__restrict__ geo,
+template <typename TB>
+__global__ void k_seg_dots2(const TB *__restrict__ Vb, long Ntot, const cplx *__restrict__ w, const Geo *__restrict__ geo,
                             int nc, const int *jdev, const int *__restrict__ active, cplx *__restrict__ hp, int ldh) {
     const int i = blockIdx.x, g = blockIdx.y, j = *jdev;
     if (i > j || (active && !active[g])) return;
     __shared__ double sh[32];
     const size_t off = (size_t)geo[g].noff, n = (size_t)geo[g].M * nc;
-    const cplx *v = Vb + (size_t)i * Ntot + off;
-    const cplx *ww = w + off;
     double re = 0, im = 0;
-    for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
-        cplx a = v[e], b = ww[e];
-        re += a.x * b.x + a.y * b.y;
-        im += a.x * b.y - a.y * b.x;
-    }
+    seg_dot_part(Vb + (size_t)i * Ntot + off, w + off, n, re, im);
     re = block_sum(re, sh);
     im = block_sum(im, sh);
     if (threadIdx.x == 0) hp[(size_t)g * ldh + i] = C(re, im);
 }
 
 // w[e] -= sum_{i <= j} coef_g[i] V_i[e], coef_g = column j of H_g (pass 1) or hp[g] (pass 2)
-__global__ void k_seg_sub(cplx *__restrict__ w, const cplx *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
+template <typename TB>
+__global__ void k_seg_sub(cplx *__restrict__ w, const TB *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
                           int nc, const int *jdev, const int *__restrict__ active, const cplx *__restrict__ H, int ld,
                           int kdim, const cplx *__restrict__ hp, int ldh) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,9 +387,21 @@ __global__ void k_seg_sub(cplx *__restrict__ w, const cplx *__restrict__ Vb, lon
     const int g = gid[e / nc], j = *jdev;
     if (active && !active[g]) return;
     const cplx *coef = hp ? hp + (size_t)g * ldh : H + ((size_t)g * kdim + j) * ld;
-    cplx s = w[e];
-    for (int i = 0; i <= j; ++i) s = csub(s, cmul(coef[i], Vb[(size_t)i * Ntot + e]));
-    w[e] = s;
+    if constexpr (std::is_same<TB, cplx>::value) {
+        cplx s = w[e];
+        for (int i = 0; i <= j; ++i) s = csub(s, cmul(coef[i], Vb[(size_t)i * Ntot + e]));
+        w[e] = s;
+    } else {
+        float sr = 0.f, si = 0.f;
+        for (int i = 0; i <= j; ++i) {
+            const float2 v = Vb[(size_t)i * Ntot + e];
+            const cplx cf = coef[i];
+            const float cr = (float)cf.x, ci = (float)cf.y;
+            sr = fmaf(cr, v.x, fmaf(-ci, v.y, sr));
+            si = fmaf(cr, v.y, fmaf(ci, v.x, si));
+        }
+        w[e] = csub(w[e], C((double)sr, (double)si));
+    }
 }
 
 // H_g[:, j] += hp[g]
@@ -366,14 +434,15 @@ __global__ void k_seg_norm(const cplx *__restrict__ w, const Geo *__restrict__ g
 }
 
 // V_{j+1}[e] = w[e] / nrm[g]
-__global__ void k_seg_scale(const cplx *__restrict__ w, cplx *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
+template <typename TB>
+__global__ void k_seg_scale(const cplx *__restrict__ w, TB *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
                             int nc, const int *jdev, const int *__restrict__ active, const double *__restrict__ nrm) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Ntot) return;
     const int g = gid[e / nc], j = *jdev;
     if (active && !active[g]) return;
     const double nv = nrm[g];
-    Vb[(size_t)(j + 1) * Ntot + e] = nv > 0.0 ? cscale(w[e], 1.0 / nv) : C(0, 0);
+    bput(Vb, (size_t)(j + 1) * Ntot + e, nv > 0.0 ? cscale(w[e], 1.0 / nv) : C(0, 0));
 }
 
 // Givens step of column j of H_g for every active geometry (block per geometry); res[g] = |g_g[j+1]|
@@ -445,24 +514,26 @@ __global__ void k_seg_backsolve(const cplx *H, int ld, int kdim, const int *kk, 
 }
 
 // x[e] += sum_{i < kk[g]} yy[g][i] V_i[e]
-__global__ void k_seg_update(cplx *__restrict__ x, const cplx *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
+template <typename TB>
+__global__ void k_seg_update(cplx *__restrict__ x, const TB *__restrict__ Vb, long Ntot, const int *__restrict__ gid,
                              int nc, const int *__restrict__ kk, const cplx *__restrict__ yy, int ld) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Ntot) return;
     const int g = gid[e / nc];
     cplx s = x[e];
-    for (int i = 0; i < kk[g]; ++i) s = cadd(s, cmul(yy[(size_t)g * ld + i], Vb[(size_t)i * Ntot + e]));
+    for (int i = 0; i < kk[g]; ++i) s = cadd(s, cmul(yy[(size_t)g * ld + i], bget(Vb, (size_t)i * Ntot + e)));
     x[e] = s;
 }
 
 // V_0 = r / nrm[g]; gg[g] = (nrm[g], 0, ...)
-__global__ void k_seg_start(const cplx *__restrict__ r, cplx *__restrict__ V0, long Ntot, const int *__restrict__ gid,
+template <typename TB>
+__global__ void k_seg_start(const cplx *__restrict__ r, TB *__restrict__ V0, long Ntot, const int *__restrict__ gid,
                             int nc, const double *__restrict__ nrm, const int *__restrict__ active) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Ntot) return;
     const int g = gid[e / nc];
     const double nv = nrm[g];
-    V0[e] = (active[g] && nv > 0.0) ? cscale(r[e], 1.0 / nv) : C(0, 0);
+    bput(V0, (size_t)e, (active[g] && nv > 0.0) ? cscale(r[e], 1.0 / nv) : C(0, 0));
 }
 
 __global__ void k_seg_g0(cplx *gg, int ld, const double *nrm, int G) {
@@ -526,6 +597,7 @@ struct gs_batch {
     cudaStream_t bst = nullptr;    // the batch's own (capturable) stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<cplx *> B, Cm, beta;   // per angle
+    std::vector<float2 *> B32;         // per angle: complex64 copy of B (mixed inner operator)
     size_t call_elems = 0;
     // translation work list
     Item *items = nullptr;
@@ -568,6 +640,7 @@ void batch_free(gs_batch *b) {
     dfree_b(b->geo);
     dfree_b(b->coff);
     for (auto &p : b->B) dfree_b(p);
+    for (auto &p : b->B32) dfree_b(p);
     for (auto &p : b->Cm) dfree_b(p);
     for (auto &p : b->beta) dfree_b(p);
     dfree_b(b->items);
@@ -698,8 +771,13 @@ int batch_apply(gs_ctx *c, gs_batch *b, int angle, const cplx *x, cplx *y, int p
     GS_COUNT_LAUNCH(c);
     k_batch_V<<<wblk((long)b->G * nB), 256, 0, st>>>(a.Vr, nB, cols, b->w, a.dscale, b->G, active, b->xv);
     GS_COUNT_LAUNCH(c);
-    k_batch_Bcombine<<<wblk(b->Ntot), 256, 0, st>>>(b->B[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv, nB, x, b->T,
-                                                     b->s, y);
+    if (precision == GS_C64) {
+        k_batch_Bcombine32<<<wblk(b->Ntot), 256, 0, st>>>(b->B32[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv, nB,
+                                                           x, b->T, b->s, y);
+    } else {
+        k_batch_Bcombine<<<wblk(b->Ntot), 256, 0, st>>>(b->B[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv, nB, x,
+                                                         b->T, b->s, y);
+    }
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -731,34 +809,41 @@ int seg_norms(gs_ctx *c, gs_batch *b, const cplx *v, const int *active, std::vec
 }
 
 // one Arnoldi step for every active geometry, j read from b->jdev; captured into a graph
-int arnoldi_step(gs_ctx *c, gs_batch *b, int angle, int precision) {
+template <typename TB>
+int arnoldi_step_t(gs_ctx *c, gs_batch *b, int angle, int precision) {
     cudaStream_t st = c->stream;
     const long N = b->Ntot;
     const int ld = b->kdim + 1, eb = nblk(N);
+    TB *V = (TB *)b->Vk;
     GS_COUNT_LAUNCH(c);
-    k_seg_fetch<<<eb, 256, 0, st>>>(b->Vk, N, b->jdev, b->X);
+    k_seg_fetch<TB><<<eb, 256, 0, st>>>(V, N, b->jdev, b->X);
     GS_TRY(batch_apply(c, b, angle, b->X, b->Y, precision, b->active));
     dim3 gd(b->kdim, b->G);
     GS_COUNT_LAUNCH(c);
-    k_seg_dots<<<gd, 256, 0, st>>>(b->Vk, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->H, ld, b->kdim, 0);
+    k_seg_dots<TB><<<gd, 256, 0, st>>>(V, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->H, ld, b->kdim, 0);
     GS_COUNT_LAUNCH(c);
-    k_seg_sub<<<eb, 256, 0, st>>>(b->Y, b->Vk, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, nullptr, 0);
+    k_seg_sub<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, nullptr, 0);
     GS_COUNT_LAUNCH(c);
-    k_seg_dots2<<<gd, 256, 0, st>>>(b->Vk, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->hp, ld);
+    k_seg_dots2<TB><<<gd, 256, 0, st>>>(V, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->hp, ld);
     GS_COUNT_LAUNCH(c);
-    k_seg_sub<<<eb, 256, 0, st>>>(b->Y, b->Vk, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, b->hp, ld);
+    k_seg_sub<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, b->hp, ld);
     GS_COUNT_LAUNCH(c);
     k_seg_addh<<<b->G, 256, 0, st>>>(b->H, ld, b->kdim, b->hp, ld, b->jdev, b->active, b->G);
     GS_COUNT_LAUNCH(c);
     k_seg_norm<<<b->G, 256, 0, st>>>(b->Y, b->geo, b->nc, b->active, b->nrm, b->H, ld, b->kdim, b->jdev);
     GS_COUNT_LAUNCH(c);
-    k_seg_scale<<<eb, 256, 0, st>>>(b->Y, b->Vk, N, b->gid, b->nc, b->jdev, b->active, b->nrm);
+    k_seg_scale<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->nrm);
     GS_COUNT_LAUNCH(c);
     k_seg_givens<<<b->G, 128, 0, st>>>(b->H, ld, b->kdim, b->jdev, b->active, b->cs, b->sn, b->gg, b->res, b->G);
     GS_COUNT_LAUNCH(c);
     k_inc<<<1, 32, 0, st>>>(b->jdev);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
+}
+
+int arnoldi_step(gs_ctx *c, gs_batch *b, int angle, int precision) {
+    return precision == GS_C64 ? arnoldi_step_t<float2>(c, b, angle, precision)
+                               : arnoldi_step_t<cplx>(c, b, angle, precision);
 }
 
 int step_graph(gs_ctx *c, gs_batch *b, int angle, int precision) {
@@ -822,7 +907,10 @@ int batch_gmres(gs_ctx *c, gs_batch *b, int angle, const cplx *rhs, cplx *x, boo
         GS_CUDA(c, cudaMemcpyAsync(b->active, act.data(), sizeof(int) * G, cudaMemcpyHostToDevice, st));
         GS_CUDA(c, cudaMemcpyAsync(b->nrm, nr.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
         GS_COUNT_LAUNCH(c);
-        k_seg_start<<<eb, 256, 0, st>>>(b->r, b->Vk, N, b->gid, b->nc, b->nrm, b->active);
+        if (precision == GS_C64)
+            k_seg_start<float2><<<eb, 256, 0, st>>>(b->r, (float2 *)b->Vk, N, b->gid, b->nc, b->nrm, b->active);
+        else
+            k_seg_start<cplx><<<eb, 256, 0, st>>>(b->r, b->Vk, N, b->gid, b->nc, b->nrm, b->active);
         GS_COUNT_LAUNCH(c);
         k_seg_g0<<<nblk((long)G * ld), 256, 0, st>>>(b->gg, ld, b->nrm, G);
         GS_CUDA(c, cudaMemsetAsync(b->H, 0, sizeof(cplx) * (size_t)G * b->kdim * ld, st));
@@ -863,7 +951,10 @@ int batch_gmres(gs_ctx *c, gs_batch *b, int angle, const cplx *rhs, cplx *x, boo
         GS_COUNT_LAUNCH(c);
         k_seg_backsolve<<<G, 256, 0, st>>>(b->H, ld, b->kdim, b->kk, b->gg, b->yy, G);
         GS_COUNT_LAUNCH(c);
-        k_seg_update<<<eb, 256, 0, st>>>(x, b->Vk, N, b->gid, b->nc, b->kk, b->yy, ld);
+        if (precision == GS_C64)
+            k_seg_update<float2><<<eb, 256, 0, st>>>(x, (const float2 *)b->Vk, N, b->gid, b->nc, b->kk, b->yy, ld);
+        else
+            k_seg_update<cplx><<<eb, 256, 0, st>>>(x, b->Vk, N, b->gid, b->nc, b->kk, b->yy, ld);
         GS_CHECK_LAUNCH(c);
     }
     return GS_OK;
@@ -1045,9 +1136,11 @@ int gs_factor_batch(gs_ctx *c) {
     GS_CUDA(c, cudaMemcpy(b->coff, coff.data(), sizeof(size_t) * G, cudaMemcpyHostToDevice));
     b->coffh = coff;
     for (auto &p : b->B) dfree_b(p);
+    for (auto &p : b->B32) dfree_b(p);
     for (auto &p : b->Cm) dfree_b(p);
     for (auto &p : b->beta) dfree_b(p);
     b->B.assign(nA, nullptr);
+    b->B32.assign(nA, nullptr);
     b->Cm.assign(nA, nullptr);
     b->beta.assign(nA, nullptr);
     b->iters.assign(nA, std::vector<int>(G, 0));
@@ -1062,6 +1155,11 @@ int gs_factor_batch(gs_ctx *c) {
                                      b->B[q] + (size_t)b->noff[g] * ly.nB()));
             GS_TRY(gs_assemble_C_geo(c, c->ang[q], b->M[g], b->xy + 2 * (size_t)b->moff[g], b->Cm[q] + coff[g]));
         }
+        const long nb = (long)N * ly.nB();
+        GS_TRY(dalloc_b(c, &b->B32[q], nb));
+        GS_COUNT_LAUNCH(c);
+        k_to_c64_b<<<nblk(nb), 256, 0, c->stream>>>(b->B[q], nb, b->B32[q]);
+        GS_CHECK_LAUNCH(c);
     }
     // workspace
     b->kdim = 0;
