@@ -50,11 +50,34 @@ __device__ __forceinline__ void hankel01(double x, cplx &h0, cplx &h1) {
     h1 = C(j1(x), y1(x));
 }
 
-// J_n(x) for any integer n (J_{-n} = (-1)^n J_n).
-__device__ __forceinline__ double besselj_int(int n, double x) {
-    if (n >= 0) return jn(n, x);
-    double v = jn(-n, x);
-    return ((-n) & 1) ? -v : v;
+// J_n(x) for any integer n and x >= 0 (J_{-n} = (-1)^n J_n) by Miller's backward recurrence
+// J_{k-1} = (2k/x) J_k - J_{k+1}, started at an order well above max(|n|, x) and normalised with
+// J_0 + 2 sum_k J_{2k} = 1 (Miller 1952; Abramowitz & Stegun 9.12): stable for every order /
+// argument ratio, including orders far above the argument, where the library's jn returned NaN
+// (orders ~44 at x ~ 8 in the L2L expansion of an inclusion that crosses a period wall).
+__device__ inline double besselj_int(int n, double x) {
+    const int an = n < 0 ? -n : n;
+    if (x == 0.0) return an == 0 ? 1.0 : 0.0;
+    const double big = fmax((double)an, x);
+    const int m = 2 * (((int)big + 16 + (int)sqrt(40.0 * big)) / 2);
+    double jp = 0.0, jc = 1e-200, norm = 0.0, val = 0.0;
+    for (int k = m; k >= 0; --k) {
+        if (k == an) val = jc;
+        norm += (k == 0) ? jc : ((k & 1) ? 0.0 : 2.0 * jc);
+        if (k > 0) {
+            const double jm = (2.0 * k / x) * jc - jp;
+            jp = jc;
+            jc = jm;
+        }
+        if (fabs(jc) > 1e200) {   // rescale the recurrence and what it has accumulated
+            jc *= 1e-200;
+            jp *= 1e-200;
+            norm *= 1e-200;
+            val *= 1e-200;
+        }
+    }
+    const double r = val / norm;
+    return (n < 0 && (an & 1)) ? -r : r;
 }
 // Y_n(x) for any integer n (Y_{-n} = (-1)^n Y_n).
 __device__ __forceinline__ double bessely_int(int n, double x) {

@@ -283,3 +283,44 @@ def test_translate_with_and_without_pair_table(budget):
     got = _np(gs.translate(beta))
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
     gs.close()
+
+
+def test_disks_across_the_walls_match_oracle():
+    """Disks that straddle the period walls (Remark "cancel": the wall rows see only far copies),
+    Bragg amplitudes against the oracle's dense solution."""
+    g = W.grating("small")
+    rng = np.random.default_rng(12)
+    xy = np.array([[-0.49, 0.1], [0.495, -0.2], [0.0, 0.0], [-0.2, 0.25], [0.3, -0.05]])
+    dk = {"xy": xy, "radius": np.full(5, 0.03), "kp": np.full(5, 20.0), "p": 8}
+    th = -math.pi / 5
+    prob = S.setup(g, th, dk)
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, _ = prob.recover(beta)
+    gs = _setup_gpu(g, th, dk)
+    gs.solve(tol=1e-12, maxit=500)
+    got = gs.bragg()
+    a = np.concatenate([got["c"], got["d"]])
+    b = np.concatenate([ref["c"], ref["d"]])
+    assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b)
+    assert got["flux_err"] < 1e-10
+    gs.close()
+
+
+def test_degenerate_inputs_are_refused():
+    from paper_1412_7466_gb300 import GS_ERR_ARG, GsError
+    g = W.grating("tiny")
+    gs = _solver()
+    gs.set_layers(g)
+    gs.set_incidence([-0.8])
+    empty = {"xy": np.zeros((0, 2)), "radius": np.zeros(0), "kp": np.zeros(0), "p": 4}
+    with pytest.raises(GsError) as e:
+        gs.set_inclusions(empty)
+    assert e.value.status == GS_ERR_ARG
+    bad_p = {"xy": np.array([[0.0, 0.0]]), "radius": np.array([0.02]), "kp": np.array([10.0]), "p": 9}
+    with pytest.raises(GsError) as e:
+        gs.set_inclusions(bad_p)
+    assert e.value.status == GS_ERR_ARG
+    nan_xy = {"xy": np.array([[np.nan, 0.0]]), "radius": np.array([0.02]), "kp": np.array([10.0]), "p": 4}
+    with pytest.raises(GsError):
+        gs.set_inclusions(nan_xy)
+    gs.close()
