@@ -143,7 +143,9 @@ int gs_pinv_apply(gs_ctx *ctx, int angle, const gs_c128 *g_dev, gs_c128 *x_dev);
 
 /* ---- hot path (device vectors of length n, layout beta[i*(2p+1) + (m+p)]) ------------------- */
 /* alpha = T beta: all-pairs Graf translation including the +-d images, self term (i, l=0) left
- * out (Sec. 4.2 Eq. trans, Sec. 5 Eq. repre3_mod).  precision GS_FP64 or GS_C64. */
+ * out (Sec. 4.2 Eq. trans, Sec. 5 Eq. repre3_mod).  precision GS_FP64 or GS_C64.  GS_C64 (also in
+ * gs_apply and the mixed gs_solve) returns GS_ERR_ARG when the geometry's largest Hankel value,
+ * |H_2p(k2 R_min)| with R_min the smallest centre distance, would exceed 1e36 (FP32 range). */
 int gs_translate(gs_ctx *ctx, int angle, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision);
 /* y = L x = x - S T x + S B_phys A^+ C x (the preconditioned Schur operator, Sec. 5). */
 int gs_apply(gs_ctx *ctx, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision);

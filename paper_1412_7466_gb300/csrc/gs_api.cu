@@ -436,10 +436,35 @@ int gs_set_inclusions(gs_ctx *c, const gs_inclusions *I) {
                 }
             }
     }
+    // smallest centre distance (minimum image; a disk's own images are d away): for each disk,
+    // rings of cells outward until the ring is farther than the best distance found
+    double dmin = d;
+    for (int i = 0; i < I->M; ++i) {
+        const int gx = cx_of(I->xy[2 * i]), gy = cy_of(I->xy[2 * i + 1]);
+        for (int ring = 0; ring <= std::max(ncx, ncy); ++ring) {
+            if ((ring - 1) * cw > dmin) break;
+            for (int oy = -ring; oy <= ring; ++oy) {
+                const int yy = gy + oy;
+                if (yy < 0 || yy >= ncy) continue;
+                for (int ox = -ring; ox <= ring; ++ox) {
+                    if (std::max(std::abs(ox), std::abs(oy)) != ring) continue;   // the ring only
+                    const int xx = ((gx + ox) % ncx + ncx) % ncx;
+                    for (int j : grid[(size_t)yy * ncx + xx]) {
+                        if (j == i) continue;
+                        double dx = std::fabs(I->xy[2 * i] - I->xy[2 * j]);
+                        dx = std::min(dx, d - dx);
+                        const double dy = I->xy[2 * i + 1] - I->xy[2 * j + 1];
+                        dmin = std::min(dmin, std::sqrt(dx * dx + dy * dy));
+                    }
+                }
+            }
+        }
+    }
     free_geometry(c);
     c->M = I->M;
     c->p = I->p;
     c->nc = 2 * I->p + 1;
+    c->min_center_dist = dmin;
     GS_TRY(dalloc(c, &c->xy, 2 * (size_t)c->M));
     GS_TRY(dalloc(c, &c->radius, c->M));
     GS_TRY(dalloc(c, &c->kp, c->M));

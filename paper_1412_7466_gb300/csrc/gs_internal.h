@@ -119,6 +119,7 @@ struct gs_ctx {
 
     gs_batch *batch = nullptr;
     gs_mlp *mlp = nullptr;
+    double min_center_dist = 0.0;   // smallest inclusion centre distance (minimum image), set_inclusions
 
     int n() const { return M * nc; }
 };
@@ -164,6 +165,9 @@ int gs_ensure_grating(gs_ctx *c);
 int gs_factor_angle(gs_ctx *c, AngleData &a);
 // translation (gs_translate.cu)
 int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision);
+// GS_OK when the complex64 translation's Hankel values stay inside the FP32 range for this geometry
+// (|H_2p(k2 R_min)| <= 1e36), else GS_ERR_ARG with a message
+int gs_c64_range(gs_ctx *c);
 size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
 // (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st

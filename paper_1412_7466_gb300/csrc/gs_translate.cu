@@ -13,6 +13,7 @@
 // unrolled for the compile-time order P).  Warp-shuffle reductions combine the lanes.  The source
 // images are split into `nsplit` chunks across blockIdx.y to fill the 152 SMs; a second kernel
 // sums the chunk partials in a fixed order (deterministic).
+#include <cmath>
 #include <mutex>
 
 #include "gs_internal.h"
@@ -424,7 +425,23 @@ int gs_build_pair_table(gs_ctx *c) {
     }
 }
 
+// The complex64 translation keeps the Hankel values in their natural scale: the largest is
+// |H_2p(k2 R_min)| ~ (2p-1)!/pi (2/(k2 R_min))^{2p} for k2 R_min below the order; above ~1e36 (the
+// FP32 range ends at 3.4e38) it would overflow, so such geometries are refused for GS_C64.
+int gs_c64_range(gs_ctx *c) {
+    const int q = 2 * c->p;
+    const double z = c->L.k2 * c->min_center_dist;
+    double l10 = 0.0;
+    if (z > 0.0 && z < q) l10 = (std::lgamma((double)q) - std::log(GS_PI)) / std::log(10.0) + q * std::log10(2.0 / z);
+    if (!(z > 0.0) || l10 > 36.0)
+        return gs_fail(c, GS_ERR_ARG, "complex64 translation: |H_" + std::to_string(q) + "(k2 R_min = " +
+                                          std::to_string(z) + ")| ~ 1e" + std::to_string((int)l10) +
+                                          " exceeds the FP32 range; use GS_FP64 (or a smaller p)");
+    return GS_OK;
+}
+
 int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision) {
+    if (precision == GS_C64) GS_TRY(gs_c64_range(c));
     switch (c->p) {
         case 1: return launch_translate<1>(c, a, beta, out, precision);
         case 2: return launch_translate<2>(c, a, beta, out, precision);

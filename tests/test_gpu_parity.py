@@ -324,3 +324,83 @@ def test_degenerate_inputs_are_refused():
     with pytest.raises(GsError):
         gs.set_inclusions(nan_xy)
     gs.close()
+
+
+@pytest.mark.parametrize("prec_name,tol,gap", [("fp64", 1e-12, 0.01), ("c64", 1e-5, 0.2)])
+@pytest.mark.parametrize("p", [1, 16])
+def test_translate_extreme_orders(p, prec_name, tol, gap):
+    """The smallest and the largest supported multipole order, both translation precisions (the
+    complex64 case on well-separated disks: see the next test)."""
+    from paper_1412_7466_gb300 import GS_C64, GS_FP64
+    g = W.grating("tiny")
+    M = 8
+    dk = W.disks(M, 0.02, gap, 2.0, g["k"][0], seed=300 + p, p=p)
+    gs = _setup_gpu(g, -1.0, dk)
+    rng = np.random.default_rng(p)
+    n = M * (2 * p + 1)
+    w = np.tile(0.5 ** np.abs(np.arange(-p, p + 1)), M)
+    beta = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * w
+    alpha = np.exp(1j * g["k"][0] * math.cos(-1.0) * g["d"])
+    ref = I.translation_matrix(dk["xy"], g["k"][1], p, g["d"], alpha) @ beta
+    got = _np(gs.translate(beta, precision=GS_FP64 if prec_name == "fp64" else GS_C64))
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+    gs.close()
+
+
+def test_c64_translation_refused_outside_fp32_range():
+    """p = 16 with disks 0.05 apart at k2 = 8: |H_32(0.4)| ~ 1e56 would overflow FP32, so the
+    complex64 translation is refused (GS_ERR_ARG); the FP64 one still runs."""
+    from paper_1412_7466_gb300 import GS_C64, GS_ERR_ARG, GsError
+    g = W.grating("tiny")
+    dk = W.disks(8, 0.02, 0.01, 2.0, g["k"][0], seed=5, p=16)
+    gs = _setup_gpu(g, -1.0, dk)
+    beta = np.ones(8 * 33, dtype=complex)
+    with pytest.raises(GsError) as e:
+        gs.translate(beta, precision=GS_C64)
+    assert e.value.status == GS_ERR_ARG
+    assert np.all(np.isfinite(_np(gs.translate(beta))))
+    gs.close()
+
+
+def test_several_angles_in_one_context():
+    """gs_set_incidence with three angles: each angle's factorisation, coupling and solve, against
+    the oracle at that angle."""
+    cfg = W.config("small")
+    g, dk = cfg["grating"], cfg["disks"]
+    thetas = [-math.pi / 5, -1.2, W.wood_angle(g["k"][0], g["d"])]
+    from paper_1412_7466_gb300 import GratingSolver
+    gs = GratingSolver(0)
+    gs.set_layers(g)
+    gs.set_incidence(thetas)
+    gs.set_inclusions(dk)
+    gs.factor()
+    for q, th in enumerate(thetas):
+        prob = S.setup(g, th, dk)
+        beta, _, _ = S.solve_dense(prob)
+        _, ref, _ = prob.recover(beta)
+        gs.solve(angle=q, tol=1e-12, maxit=500)
+        got = gs.bragg(angle=q)
+        a = np.concatenate([got["c"], got["d"]])
+        b = np.concatenate([ref["c"], ref["d"]])
+        assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b), q
+    gs.close()
+
+
+def test_flat_interfaces():
+    """Flat interfaces (no Fourier terms) with inclusions, against the oracle."""
+    g = dict(W.grating("small"))
+    g["gamma1"] = {"h0": 0.5, "cos": [], "sin": []}
+    g["gamma2"] = {"h0": -0.5, "cos": [], "sin": []}
+    dk = W.disks(6, 0.04, 0.02, 2.0, g["k"][0], seed=8, p=8)
+    th = -math.pi / 5
+    prob = S.setup(g, th, dk)
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, _ = prob.recover(beta)
+    gs = _setup_gpu(g, th, dk)
+    gs.solve(tol=1e-12, maxit=500)
+    got = gs.bragg()
+    a = np.concatenate([got["c"], got["d"]])
+    b = np.concatenate([ref["c"], ref["d"]])
+    assert np.linalg.norm(a - b) <= BRAGG_TOL * np.linalg.norm(b)
+    assert got["flux_err"] < 1e-10
+    gs.close()
