@@ -83,3 +83,34 @@ def test_autotuned_tiles_are_candidates(batch):
     cfg, geos, gs, single = batch
     chunk, bps = gs.batch_tuning()
     assert chunk in (512, 1024, 2048) and bps in (2, 4, 8)
+
+
+def test_batched_two_angles_match_single():
+    """One batch factored at two angles: each angle's batched mixed solve matches the
+    single-geometry solve at that angle."""
+    from paper_1412_7466_gb300 import GS_C64, GratingSolver
+    cfg = W.config("small")
+    g = cfg["grating"]
+    thetas = [-1.3, -0.7]
+    geos = [W.disks(M, 0.02, 0.01, 2.0, g["k"][0], seed=500 + M, p=6) for M in (19, 5)]
+    gb = GratingSolver(0)
+    gb.set_layers(g)
+    gb.set_incidence(thetas)
+    gb.set_inclusions_batch(geos)
+    gb.factor_batch()
+    for q, th in enumerate(thetas):
+        gb.solve_batch(angle=q, tol=1e-12, precision=GS_C64)
+        for k, dk in enumerate(geos):
+            got = gb.bragg_batch(k, angle=q)
+            s1 = GratingSolver(0)
+            s1.set_layers(g)
+            s1.set_incidence([th])
+            s1.set_inclusions(dk)
+            s1.factor()
+            s1.solve(tol=1e-12, maxit=500)
+            ref = s1.bragg()
+            s1.close()
+            a = np.r_[got["c"], got["d"]]
+            b = np.r_[ref["c"], ref["d"]]
+            assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), (q, k)
+    gb.close()

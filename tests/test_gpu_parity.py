@@ -363,11 +363,11 @@ def test_c64_translation_refused_outside_fp32_range():
 
 
 def test_several_angles_in_one_context():
-    """gs_set_incidence with three angles: each angle's factorisation, coupling and solve, against
-    the oracle at that angle."""
+    """gs_set_incidence with four angles (one at a Wood anomaly, one at normal incidence, alpha = 1):
+    each angle's factorisation, coupling and solve, against the oracle at that angle."""
     cfg = W.config("small")
     g, dk = cfg["grating"], cfg["disks"]
-    thetas = [-math.pi / 5, -1.2, W.wood_angle(g["k"][0], g["d"])]
+    thetas = [-math.pi / 5, -1.2, W.wood_angle(g["k"][0], g["d"]), -math.pi / 2]   # ..., normal incidence
     from paper_1412_7466_gb300 import GratingSolver
     gs = GratingSolver(0)
     gs.set_layers(g)
