@@ -136,6 +136,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
+    ap.add_argument("--warm-train", type=int, default=24, help="warm start: training sweep points")
+    ap.add_argument("--warm-eval", type=int, default=6, help="warm start: held-out sweep points")
     ap.add_argument("--no-big", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-field", action="store_true")
@@ -635,7 +637,7 @@ def main():
     wres = None
     if not args.no_warm:
         from paper_1412_7466_gb300.warmstart import SweepTrainer
-        n_tr, n_ev = 24, 6
+        n_tr, n_ev = args.warm_train, args.warm_eval
         pts = W.sweep_points(n_tr + n_ev, seed=5)
         geo = cfg0["disks"]
         gw = GratingSolver(local)
@@ -695,8 +697,8 @@ def main():
                 "train_loss_first_last": [hist[0], hist[-1]],
                 "collect_s": t1 - t0, "train_s": t2 - t1,
                 "sweep": "headline geometry (M=1000, r=0.008, p=12), k=(1,1.5,2) k_top, kp=2 k_top, "
-                         "(phi, k_top) iid in [-pi/3, pi/3] x [35, 45] (seed 5); first 24 points train "
-                         "(complex64 + FP64 refinement to 1e-9), next 6 evaluate (FP64 GMRES to 1e-11)",
+                         f"(phi, k_top) iid in [-pi/3, pi/3] x [35, 45] (seed 5); first {n_tr} points train "
+                         f"(complex64 + FP64 refinement to 1e-9), next {n_ev} evaluate (FP64 GMRES to 1e-11)",
                 "step": "warm_start (features, network, start, FP64 residual check) + solve + Bragg; "
                         "the grating factorisation per sweep point is outside the timed region"}
 
