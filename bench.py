@@ -335,6 +335,24 @@ def main():
     couple_ms = e[1].elapsed_time(e[2])
     grating_ms = e[0].elapsed_time(e[1]) - couple_ms
 
+    if args.kernel_only and os.environ.get("GS_BENCH_PRECISION") == "batch":
+        # batched complex64 translation: the bench's eight uneven-M geometries at the Wood angle
+        bgeos = [gg for gg in W.batched_geometries(n_geom=64, seed=4) if gg["xy"].shape[0] <= 1200][:8]
+        gb = GratingSolver(local)
+        gb.set_layers(g)
+        gb.set_incidence([W.wood_angle(g["k"][0], g["d"])])
+        gb.set_inclusions_batch(bgeos)
+        gb.factor_batch()
+        xb = torch.randn(sum(gb.batch_sizes), dtype=torch.complex128, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            gb.apply_batch(xb, precision=GS_C64)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": True, "batched_applies": args.warmup + args.steps,
+                          "geometries_M": [int(x["xy"].shape[0]) for x in bgeos]}))
+        gb.close()
+        gs.close()
+        return
+
     if args.kernel_only and os.environ.get("GS_BENCH_PRECISION") == "tc":
         # tensor-core multi-right-hand-side translation, R = 256 angles
         R = 256

@@ -79,8 +79,15 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
     __shared__ float4 sg[TILE];
     __shared__ int sid[TILE];
     __shared__ int cur;
+    __shared__ float2 sphf[3];   // complex64 image phases alpha^l, l = -1, 0, 1 (once per launch)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const cplx ainv = cconj(alpha);
+    const float kf = (float)k;
+    if (threadIdx.x == 0) {
+        sphf[0] = make_float2((float)alpha.x, (float)-alpha.y);
+        sphf[1] = make_float2(1.f, 0.f);
+        sphf[2] = make_float2((float)alpha.x, (float)alpha.y);
+    }
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
@@ -120,11 +127,10 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
                 if (s < w.s1) {
                     const int l = (s >= G.M) + (s >= 2 * G.M) - 1;   // source image s = (l+1) M + j
                     const int j = s - (l + 1) * G.M;
-                    cplx ph = (l == 0) ? C(1.0, 0.0) : (l == 1 ? alpha : ainv);
                     if constexpr (C64) {
-                        float2 b = beta32[(size_t)G.noff + (size_t)j * NC + n];
-                        v = gs_cmulf(gs_cf((float)ph.x, (float)ph.y), b);
+                        v = gs_cmulf(sphf[l + 1], beta32[(size_t)G.noff + (size_t)j * NC + n]);
                     } else {
+                        const cplx ph = (l == 0) ? C(1.0, 0.0) : (l == 1 ? alpha : ainv);
                         v = cmul(ph, beta[(size_t)G.noff + (size_t)j * NC + n]);
                     }
                 }
@@ -157,7 +163,7 @@ k_batch_translate(const Item *__restrict__ items, int n_items, int *counter, con
             for (int n = 0; n < NC; ++n) b[n] = sb[n][lane];
             if constexpr (C64) {
                 const float4 gs = sg[lane];
-                gs_pair_c64x2<P>((gi.x - gs.x) + (gi.y - gs.y), (gi.z - gs.z) + (gi.w - gs.w), (float)k, b, acc, Qa);
+                gs_pair_c64x2<P>((gi.x - gs.x) + (gi.y - gs.y), (gi.z - gs.z) + (gi.w - gs.w), kf, b, acc, Qa);
             } else {
                 gs_pair_f64<P>(xi - sx[lane], yi - sy[lane], k, b, acc);
             }
