@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
     if (a >= n || b >= n) return;
     int pc = a < b ? a : b, qc = a < b ? b : a;
     cplx *wp = W + (size_t)pc * m, *wq = W + (size_t)qc * m;
-    __shared__ double sh[32];
+    __shared__ double4 sh4[32];
     __shared__ double rot[4];
     double al = 0, be = 0, gr = 0, gi = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -73,10 +73,30 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
         gr += x.x * y.x + x.y * y.y;   // conj(x) y
         gi += x.x * y.y - x.y * y.x;
     }
-    al = block_sum(al, sh);
-    be = block_sum(be, sh);
-    gr = block_sum(gr, sh);
-    gi = block_sum(gi, sh);
+    // the four sums in one block reduction
+    al = warp_sum(al);
+    be = warp_sum(be);
+    gr = warp_sum(gr);
+    gi = warp_sum(gi);
+    {
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+        if (l == 0) sh4[w] = make_double4(al, be, gr, gi);
+        __syncthreads();
+        if (w == 0) {
+            double4 t = (l < nw) ? sh4[l] : make_double4(0.0, 0.0, 0.0, 0.0);
+            t.x = warp_sum(t.x);
+            t.y = warp_sum(t.y);
+            t.z = warp_sum(t.z);
+            t.w = warp_sum(t.w);
+            if (l == 0) sh4[0] = t;
+        }
+        __syncthreads();
+        const double4 r = sh4[0];
+        al = r.x;
+        be = r.y;
+        gr = r.z;
+        gi = r.w;
+    }
     if (threadIdx.x == 0) {
         double g = hypot(gr, gi);
         if (g == 0.0 || g <= tol * sqrt(al * be)) {
@@ -120,19 +140,29 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ float block_sum_f(float v, float *sh) {
-    v = warp_sum_f(v);
+// the four sums of a Jacobi pair in one block reduction (one barrier pass instead of four)
+__device__ __forceinline__ void block_sum4_f(float &a, float &b, float &c, float &d, float4 *sh) {
+    a = warp_sum_f(a);
+    b = warp_sum_f(b);
+    c = warp_sum_f(c);
+    d = warp_sum_f(d);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) sh[w] = make_float4(a, b, c, d);
     __syncthreads();
-    if (l == 0) sh[w] = v;
+    if (w == 0) {
+        float4 t = (l < nw) ? sh[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        t.x = warp_sum_f(t.x);
+        t.y = warp_sum_f(t.y);
+        t.z = warp_sum_f(t.z);
+        t.w = warp_sum_f(t.w);
+        if (l == 0) sh[0] = t;
+    }
     __syncthreads();
-    float t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.f;
-    if (w == 0) t = warp_sum_f(t);
-    if (threadIdx.x == 0) sh[0] = t;
-    __syncthreads();
-    const float r = sh[0];
-    __syncthreads();
-    return r;
+    const float4 r = sh[0];
+    a = r.x;
+    b = r.y;
+    c = r.z;
+    d = r.w;
 }
 
 // FP32 round on the copy W32 with the rotations accumulated in V (FP32), one block per pair: the
@@ -146,7 +176,7 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
     if (a >= n || b >= n) return;
     int pc = a < b ? a : b, qc = a < b ? b : a;
     float2 *wp = W32 + (size_t)pc * m, *wq = W32 + (size_t)qc * m;
-    __shared__ float sh[32];
+    __shared__ float4 sh4[32];
     __shared__ double rot[4];
     float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -156,10 +186,7 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
         gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));   // conj(x) y
         gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
     }
-    al = block_sum_f(al, sh);
-    be = block_sum_f(be, sh);
-    gr = block_sum_f(gr, sh);
-    gi = block_sum_f(gi, sh);
+    block_sum4_f(al, be, gr, gi, sh4);
     if (threadIdx.x == 0) {
         const double g = hypot((double)gr, (double)gi);
         if (g == 0.0 || g <= (double)tol * sqrt((double)al * (double)be)) {
