@@ -145,7 +145,10 @@ def parse():
                     help="disk analogues of the paper's Example 1 (homogeneous vs layered, M = 100/500/1000) "
                          "and Example 3 (k2 = 1, 10, 20, 30): GMRES iterations, time, flux; one JSON line")
     ap.add_argument("--kernel-only", action="store_true",
-                    help="factor once, then run `steps` FP64 translation launches only (for ncu captures)")
+                    help="factor once, then run warmup + steps calls of one kernel family only, for ncu "
+                         "captures: GS_BENCH_PRECISION = fp64 (translation, default), c64 (complex64 "
+                         "translation), c64op (the mixed solve's inner operator), batch, tc; GS_BENCH_M "
+                         "sets a smaller M")
     return ap.parse_args()
 
 
@@ -363,6 +366,17 @@ def main():
             gs.translate_multi(alphas, betas)
         torch.cuda.synchronize()
         print(json.dumps({"kernel_only": True, "translate_multi_launches": args.warmup + args.steps, "R": R}))
+        gs.close()
+        return
+
+    if args.kernel_only and os.environ.get("GS_BENCH_PRECISION") == "c64op":
+        # the mixed solve's inner operator (complex64 translation, double-float C x, complex64 B)
+        x = torch.randn(M * nc, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(args.warmup + args.steps):
+            gs.apply(x, precision=GS_C64, out=y)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": True, "c64_operator_applies": args.warmup + args.steps}))
         gs.close()
         return
 

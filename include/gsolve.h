@@ -147,7 +147,11 @@ int gs_pinv_apply(gs_ctx *ctx, int angle, const gs_c128 *g_dev, gs_c128 *x_dev);
  * gs_apply and the mixed gs_solve) returns GS_ERR_ARG when the geometry's largest Hankel value,
  * |H_2p(k2 R_min)| with R_min the smallest centre distance, would exceed 1e36 (FP32 range). */
 int gs_translate(gs_ctx *ctx, int angle, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision);
-/* y = L x = x - S T x + S B_phys A^+ C x (the preconditioned Schur operator, Sec. 5). */
+/* y = L x = x - S T x + S B_phys A^+ C x (the preconditioned Schur operator, Sec. 5).  GS_FP64:
+ * FP64 throughout.  GS_C64 (the inner operator of the mixed solve): complex64 translation and
+ * complex64 B_phys; C x in double-float arithmetic (C and x as complex64 (hi, lo) pairs, 48-bit
+ * significands; C is copied to that form on first use, or kept FP64 if an entry exceeds 1e30);
+ * A^+ in FP64. */
 int gs_apply(gs_ctx *ctx, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision);
 /* b = S B_phys A^+ f (right-hand side of the preconditioned Schur system, Sec. 5). */
 int gs_rhs(gs_ctx *ctx, int angle, gs_c128 *b_dev);

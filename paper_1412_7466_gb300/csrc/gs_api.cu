@@ -64,6 +64,8 @@ void free_angle_geometry(AngleData &a) {
     dfree(a.B);
     dfree(a.Cm);
     dfree(a.B32);
+    dfree(a.C2);
+    a.C2_off = false;
     dfree(a.beta);
     a.iters = 0;
     a.outer = 0;
@@ -94,6 +96,8 @@ void free_geometry(gs_ctx *c) {
     dfree(c->part);
     dfree(c->b32);
     dfree(c->img32);
+    dfree(c->xdf);
+    dfree(c->iflag);
     dfree(c->htab);
     if (c->tcA) cudaFree(c->tcA);
     c->tcA = nullptr;
@@ -495,11 +499,11 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     GS_TRY(dalloc(c, &c->b32, n));
     GS_TRY(dalloc(c, &c->img32, 3 * (size_t)c->M));
+    GS_TRY(dalloc(c, &c->xdf, n));
+    GS_TRY(dalloc(c, &c->iflag, 1));
     GS_TRY(gs_build_images_c64(c, c->xy, c->M, c->img32, c->stream));
     c->kdim = 200;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
-    GS_TRY(dalloc(c, &c->kv1, n));
-    GS_TRY(dalloc(c, &c->kv2, n));
     GS_TRY(dalloc(c, &c->kv1, n));
     GS_TRY(dalloc(c, &c->kv2, n));
     GS_TRY(dalloc(c, &c->Hh, (size_t)(c->kdim + 1) * c->kdim));

@@ -308,6 +308,44 @@ __global__ void k_to_c64_b(const cplx *__restrict__ a, long n, float2 *__restric
     if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
 }
 
+// complex128 -> double-float (hi, lo) complex64 pairs; flag set if some |entry| exceeds lim or is
+// not finite
+__global__ void k_b_split_df(const cplx *__restrict__ a, long n, float4 *__restrict__ b, double lim,
+                             int *__restrict__ flag) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const cplx v = a[e];
+    b[e] = df_split(v.x, v.y);
+    if (flag && !(fabs(v.x) <= lim && fabs(v.y) <= lim)) *flag = 1;
+}
+
+// gC[g][r] = (C_g x_g)[r] for the mixed inner operator, in double-float arithmetic (C_g and x_g as
+// (hi, lo) complex64 pairs, 48-bit significands: C x feeds A^+, whose clipped Sigma^+ amplifies
+// rounding in its near-null directions); one block of BATCH_DF_THREADS per (geometry, row)
+constexpr int BATCH_DF_THREADS = 128;
+__global__ void __launch_bounds__(BATCH_DF_THREADS)
+    k_batch_C_df(const float4 *__restrict__ C2all, const size_t *__restrict__ coff, const Geo *__restrict__ geo,
+                 int nC, int nc, const int *__restrict__ active, const float4 *__restrict__ x2,
+                 cplx *__restrict__ gC) {
+    const int g = blockIdx.x / nC, r = blockIdx.x % nC;
+    if (active && !active[g]) return;
+    const long n = (long)geo[g].M * nc;
+    const float4 *a = C2all + coff[g] + (size_t)r * n;
+    const float4 *xv = x2 + geo[g].noff;
+    dfc s = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (long c = threadIdx.x; c < n; c += BATCH_DF_THREADS) dfc_mac(s, __ldcs(&a[c]), __ldg(&xv[c]));
+    dfc_warp_sum(s);
+    __shared__ dfc part[BATCH_DF_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dfc t = part[0];
+        for (int k = 1; k < BATCH_DF_THREADS / 32; ++k) dfc_add(t, part[k]);
+        gC[(size_t)g * nC + r] = C((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
+    }
+}
+
 // ---- segmented GMRES kernels (step index j read from device memory) --------------------------------
 // Templated on the basis type: complex128 (FP64 solves) or complex64 (the inner solves of the mixed
 // form: FP32 products, FP64 block sums -- the FP64 products are bound by GB300's FP64 pipe).
@@ -604,6 +642,8 @@ struct gs_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<cplx *> B, Cm, beta;   // per angle
     std::vector<float2 *> B32;         // per angle: complex64 copy of B (mixed inner operator)
+    std::vector<float4 *> C2;          // per angle: double-float copy of C (mixed inner operator;
+                                       // null when an entry exceeds GS_DF_LIMIT: FP64 C kept)
     size_t call_elems = 0;
     // translation work list
     Item *items = nullptr;
@@ -617,6 +657,8 @@ struct gs_batch {
     cplx *X = nullptr, *Y = nullptr, *T = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *xr = nullptr;
     float2 *b32 = nullptr;
     float4 *img32 = nullptr;       // (hi, lo) float image coordinates, 3 M_g per geometry at 3 moff_g
+    float4 *xdf = nullptr;         // Ntot: double-float split of the operator input
+    int *dflag = nullptr;          // range flag of the double-float split of C
     cplx *gC = nullptr, *w = nullptr, *xv = nullptr;   // G nC, G cols, G cols
     int *active = nullptr;
     // GMRES
@@ -647,6 +689,7 @@ void batch_free(gs_batch *b) {
     dfree_b(b->coff);
     for (auto &p : b->B) dfree_b(p);
     for (auto &p : b->B32) dfree_b(p);
+    for (auto &p : b->C2) dfree_b(p);
     for (auto &p : b->Cm) dfree_b(p);
     for (auto &p : b->beta) dfree_b(p);
     dfree_b(b->items);
@@ -664,6 +707,8 @@ void batch_free(gs_batch *b) {
     dfree_b(b->xr);
     dfree_b(b->b32);
     dfree_b(b->img32);
+    dfree_b(b->xdf);
+    dfree_b(b->dflag);
     dfree_b(b->gC);
     dfree_b(b->w);
     dfree_b(b->xv);
@@ -771,7 +816,15 @@ int batch_apply(gs_ctx *c, gs_batch *b, int angle, const cplx *x, cplx *y, int p
     cudaStream_t st = c->stream;
     GS_TRY(batch_translate(c, b, a, x, b->T, precision, active));
     GS_COUNT_LAUNCH(c);
-    k_batch_C<<<wblk((long)b->G * nC), 256, 0, st>>>(b->Cm[angle], b->coff, b->geo, b->G, nC, b->nc, active, x, b->gC);
+    if (precision == GS_C64 && b->C2[angle]) {
+        k_b_split_df<<<nblk(b->Ntot), 256, 0, st>>>(x, b->Ntot, b->xdf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_batch_C_df<<<b->G * nC, BATCH_DF_THREADS, 0, st>>>(b->C2[angle], b->coff, b->geo, nC, b->nc, active, b->xdf,
+                                                             b->gC);
+    } else {
+        k_batch_C<<<wblk((long)b->G * nC), 256, 0, st>>>(b->Cm[angle], b->coff, b->geo, b->G, nC, b->nc, active, x,
+                                                         b->gC);
+    }
     GS_COUNT_LAUNCH(c);
     k_batch_UH<<<wblk((long)b->G * cols), 256, 0, st>>>(a.W, ly.rows, nC, cols, b->gC, nC, a.coef, b->G, active, b->w);
     GS_COUNT_LAUNCH(c);
@@ -1143,10 +1196,12 @@ int gs_factor_batch(gs_ctx *c) {
     b->coffh = coff;
     for (auto &p : b->B) dfree_b(p);
     for (auto &p : b->B32) dfree_b(p);
+    for (auto &p : b->C2) dfree_b(p);
     for (auto &p : b->Cm) dfree_b(p);
     for (auto &p : b->beta) dfree_b(p);
     b->B.assign(nA, nullptr);
     b->B32.assign(nA, nullptr);
+    b->C2.assign(nA, nullptr);
     b->Cm.assign(nA, nullptr);
     b->beta.assign(nA, nullptr);
     b->iters.assign(nA, std::vector<int>(G, 0));
@@ -1166,6 +1221,17 @@ int gs_factor_batch(gs_ctx *c) {
         GS_COUNT_LAUNCH(c);
         k_to_c64_b<<<nblk(nb), 256, 0, c->stream>>>(b->B[q], nb, b->B32[q]);
         GS_CHECK_LAUNCH(c);
+        // double-float copy of C (the mixed inner operator's C x), unless an entry is out of range
+        if (!b->dflag) GS_TRY(dalloc_b(c, &b->dflag, 1));
+        GS_CUDA(c, cudaMemsetAsync(b->dflag, 0, sizeof(int), c->stream));
+        GS_TRY(dalloc_b(c, &b->C2[q], o));
+        GS_COUNT_LAUNCH(c);
+        k_b_split_df<<<nblk((long)o), 256, 0, c->stream>>>(b->Cm[q], (long)o, b->C2[q], GS_DF_LIMIT, b->dflag);
+        GS_CHECK_LAUNCH(c);
+        int big = 0;
+        GS_CUDA(c, cudaMemcpyAsync(&big, b->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (big) dfree_b(b->C2[q]);
     }
     // workspace
     b->kdim = 0;
@@ -1179,6 +1245,7 @@ int gs_factor_batch(gs_ctx *c) {
     GS_TRY(dalloc_b(c, &b->xr, N));
     GS_TRY(dalloc_b(c, &b->b32, N));
     GS_TRY(dalloc_b(c, &b->img32, 3 * (size_t)b->Mtot));
+    GS_TRY(dalloc_b(c, &b->xdf, N));
     for (int g = 0; g < G; ++g)
         GS_TRY(gs_build_images_c64(c, b->xy + 2 * (size_t)b->moff[g], b->M[g], b->img32 + 3 * (size_t)b->moff[g],
                                    c->stream));

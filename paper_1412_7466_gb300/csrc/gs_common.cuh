@@ -119,6 +119,70 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
+// ---- double-float arithmetic: a value held as an unevaluated sum hi + lo of two floats (Dekker
+// 1971), sums by Knuth's TwoSum, products by the FMA form of Dekker's exact product.  A complex
+// double-float number is a float4 (hi.re, hi.im, lo.re, lo.im): 48-bit significands on the FP32
+// pipe, for products whose FP64 form would be bound by the FP64 pipe.
+
+// s + e = a + b exactly
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += a * b: exact product error and TwoSum error go to lo, then lo is folded back so
+// that |lo| stays below half an ulp of hi
+__device__ __forceinline__ void df_mac(float &hi, float &lo, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float s, e;
+    df_two_sum(hi, p, s, e);
+    lo += e + pe;
+    hi = s + lo;
+    lo -= hi - s;
+}
+struct dfc {
+    float rh, rl, ih, il;   // real (hi, lo), imaginary (hi, lo)
+};
+// s += c * x for complex double-float c, x; the lo * lo terms (2^-48 of the product) are dropped
+__device__ __forceinline__ void dfc_mac(dfc &s, float4 c, float4 x) {
+    s.rl = fmaf(c.x, x.z, fmaf(c.z, x.x, fmaf(-c.y, x.w, fmaf(-c.w, x.y, s.rl))));
+    s.il = fmaf(c.x, x.w, fmaf(c.z, x.y, fmaf(c.y, x.z, fmaf(c.w, x.x, s.il))));
+    df_mac(s.rh, s.rl, c.x, x.x);
+    df_mac(s.rh, s.rl, -c.y, x.y);
+    df_mac(s.ih, s.il, c.x, x.y);
+    df_mac(s.ih, s.il, c.y, x.x);
+}
+__device__ __forceinline__ void dfc_add(dfc &a, const dfc &b) {
+    float s, e;
+    df_two_sum(a.rh, b.rh, s, e);
+    a.rl += e + b.rl;
+    a.rh = s + a.rl;
+    a.rl -= a.rh - s;
+    df_two_sum(a.ih, b.ih, s, e);
+    a.il += e + b.il;
+    a.ih = s + a.il;
+    a.il -= a.ih - s;
+}
+// warp-wide double-float sum (all lanes get it)
+__device__ __forceinline__ void dfc_warp_sum(dfc &a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dfc b;
+        b.rh = __shfl_xor_sync(0xffffffffu, a.rh, o);
+        b.rl = __shfl_xor_sync(0xffffffffu, a.rl, o);
+        b.ih = __shfl_xor_sync(0xffffffffu, a.ih, o);
+        b.il = __shfl_xor_sync(0xffffffffu, a.il, o);
+        dfc_add(a, b);
+    }
+}
+// (hi, lo) complex64 split of a complex128 value: hi the nearest complex64, lo the nearest
+// complex64 to the (exact) remainder
+__device__ __forceinline__ float4 df_split(double re, double im) {
+    const float hr = (float)re, hi = (float)im;
+    return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+}
+
 // H0(z), H1(z) in single precision from the polynomial approximations of Abramowitz & Stegun
 // 9.4.1-9.4.6 (Allen 1956): for z <= 3 power series in (z/3)^2 with the logarithmic terms of Y0, Y1;
 // for z > 3 modulus and phase, H_n = z^{-1/2} f_n e^{i theta_n}, as polynomials in 3/z.  Absolute

@@ -20,6 +20,10 @@ struct Layout {
     int nC() const { return row_w1v; }    // rows of C: Gamma1, Gamma2, middle walls
 };
 
+// largest |entry| of C held in double-float form: products with the inner operator's input (|x| of
+// order 1) and their sums over up to ~1e6 columns stay inside the FP32 exponent range
+#define GS_DF_LIMIT 1e30
+
 struct AngleData {
     double theta = 0, kappa0 = 0;
     cplx alpha = {1, 0};
@@ -35,6 +39,8 @@ struct AngleData {
     cplx *B = nullptr;           // n x nB row-major (physical sign)
     cplx *Cm = nullptr;          // nC x n row-major
     mutable float2 *B32 = nullptr;   // complex64 copy of B for the mixed inner operator (on first use)
+    mutable float4 *C2 = nullptr;    // double-float (hi, lo) copy of C for the mixed inner operator
+    mutable bool C2_off = false;     // C has entries beyond GS_DF_LIMIT: the inner operator keeps FP64
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
     int sweeps32 = 0;            // FP32-guided sweeps before them
@@ -91,6 +97,8 @@ struct gs_ctx {
     cplx *part = nullptr;                                // translation partials
     float2 *b32 = nullptr;                               // n, complex64 copy of the source coefficients
     float4 *img32 = nullptr;                             // 3M, (hi, lo) float image coordinates
+    float4 *xdf = nullptr;                               // n, double-float split of the operator input
+    int *iflag = nullptr;                                // one int, device-side flag
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
     void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
     long tcA_rows = 0, tcA_cols = 0;

@@ -66,11 +66,50 @@ __global__ void k_B_combine(const cplx *__restrict__ B, int n, int nB, const cpl
 // (1.26 TFLOP/s / 6.7 TB/s = 0.19): the FP64 products with B_phys and C are bound by the FP64
 // pipe.  The inner operator of the mixed solve (whose translation is complex64 anyway) reads a
 // complex64 copy of B_phys instead: half the bytes, FP32 arithmetic, HBM-bound.  B_phys acts last
-// (after A^+), so its FP32 rounding is not amplified; C x stays FP64 (see gs_apply_impl).
+// (after A^+), so its FP32 rounding is not amplified.  C x feeds A^+, whose clipped Sigma^+ (up to
+// 1/eps = 1e10 in the near-null directions) would amplify FP32 rounding of C x into the whole
+// correction: the inner operator forms it in double-float arithmetic (C and x as complex64 (hi, lo)
+// pairs, 48-bit significands), as accurate as the FP64 sum at the FP32 pipe's rate, and as
+// bytes-bound as the FP64 form would be with an FP64 pipe 64 times faster.
 
 __global__ void k_to_c64_vec(const cplx *__restrict__ a, long n, float2 *__restrict__ b) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// complex128 -> (hi, lo) complex64 pairs; flag set if some |entry| exceeds lim (beyond it, sums of
+// products could leave the FP32 exponent range) or is not finite
+__global__ void k_split_df(const cplx *__restrict__ a, long n, float4 *__restrict__ b, double lim,
+                           int *__restrict__ flag) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const cplx v = a[e];
+    b[e] = df_split(v.x, v.y);
+    if (flag && !(fabs(v.x) <= lim && fabs(v.y) <= lim)) *flag = 1;
+}
+
+// y[r] = (C x)[r] in double-float arithmetic, C (nrows x ncols row-major) and x as (hi, lo)
+// complex64 pairs; one block of GEMV_DF_THREADS per row, the FP64 result hi + lo
+constexpr int GEMV_DF_THREADS = 128;
+__global__ void __launch_bounds__(GEMV_DF_THREADS) k_gemv_rows_df(const float4 *__restrict__ C2, int nrows, long ncols,
+                                                                 const float4 *__restrict__ x2,
+                                                                 cplx *__restrict__ y) {
+    const int r = blockIdx.x;
+    if (r >= nrows) return;
+    const float4 *a = C2 + (size_t)r * ncols;
+    dfc s = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (long c = threadIdx.x; c < ncols; c += GEMV_DF_THREADS) dfc_mac(s, __ldcs(&a[c]), __ldg(&x2[c]));
+    dfc_warp_sum(s);
+    __shared__ dfc part[GEMV_DF_THREADS / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dfc t = part[0];
+        for (int k = 1; k < GEMV_DF_THREADS / 32; ++k) dfc_add(t, part[k]);
+        y[r] = C((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
+    }
 }
 
 // y[r] = x[r] - s[r] t[r] + s[r] (B v)[r] with B complex64 (FP32 products), warp per row
@@ -293,10 +332,30 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
             GS_COUNT_LAUNCH(c);
             k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
         }
-        // C x stays FP64: it feeds A^+, whose clipped Sigma^+ (up to 1/eps = 1e10 in the near-null
-        // directions) would amplify FP32 rounding of C x into the whole correction
+        if (!a.C2 && !a.C2_off) {   // double-float copy of C, once per geometry and angle
+            const long nc2 = (long)nC * n;
+            GS_CUDA(c, cudaMalloc((void **)&a.C2, sizeof(float4) * nc2));
+            GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
+            GS_COUNT_LAUNCH(c);
+            k_split_df<<<(int)((nc2 + 255) / 256), 256, 0, c->stream>>>(a.Cm, nc2, a.C2, GS_DF_LIMIT, c->iflag);
+            GS_CHECK_LAUNCH(c);
+            int big = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&big, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            GS_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (big) {   // entries beyond the double-float range: keep the FP64 product
+                cudaFree(a.C2);
+                a.C2 = nullptr;
+                a.C2_off = true;
+            }
+        }
         GS_COUNT_LAUNCH(c);
-        k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+        if (a.C2) {
+            k_split_df<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(x, n, c->xdf, 0.0, nullptr);
+            GS_COUNT_LAUNCH(c);
+            k_gemv_rows_df<<<nC, GEMV_DF_THREADS, 0, c->stream>>>(a.C2, nC, n, c->xdf, c->g);
+        } else {
+            k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+        }
         GS_COUNT_LAUNCH(c);
         k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
         GS_COUNT_LAUNCH(c);

@@ -216,7 +216,8 @@ def test_translate_c64_matches_oracle(small):
 
 def test_operator_c64_matches_oracle(small):
     """complex64 inner operator: complex64 translation and a complex64 copy of B_phys with FP32
-    products (C, U^*, V Sigma in FP64): single-precision accuracy, 1e-5 relative in norm."""
+    products, C x in double-float arithmetic, U^* and V Sigma in FP64: single-precision accuracy,
+    1e-5 relative in norm."""
     from paper_1412_7466_gb300 import GS_C64
     cfg, prob, gs = small
     rng = np.random.default_rng(6)
@@ -224,6 +225,22 @@ def test_operator_c64_matches_oracle(small):
     x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.tile(0.3 ** np.abs(np.arange(-prob.disks["p"], prob.disks["p"] + 1)), prob.M)
     got = _np(gs.apply(x, precision=GS_C64))
     ref = prob.apply(x)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_operator_c64_lowrank_part(small):
+    """The low-rank correction S B_phys A^+ C x inside the complex64 operator, isolated as
+    L32 x - x + S T32 x: C x in double-float arithmetic feeds A^+ (whose clipped Sigma^+ amplifies
+    rounding in its near-null directions), so a plain FP32 C x would show here; only the complex64
+    copy of B_phys (applied after A^+) rounds at single precision.  1e-5 relative in norm."""
+    from paper_1412_7466_gb300 import GS_C64
+    cfg, prob, gs = small
+    rng = np.random.default_rng(16)
+    n = prob.M * prob.nc
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.tile(0.3 ** np.abs(np.arange(-prob.disks["p"], prob.disks["p"] + 1)), prob.M)
+    s = prob.s.ravel()
+    got = _np(gs.apply(x, precision=GS_C64)) - x + s * _np(gs.translate(x, precision=GS_C64))
+    ref = prob.lowrank(x)
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
