@@ -130,28 +130,37 @@ __device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e)
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-// (hi, lo) += a * b: exact product error and TwoSum error go to lo, then lo is folded back so
-// that |lo| stays below half an ulp of hi
-__device__ __forceinline__ void df_mac(float &hi, float &lo, float a, float b) {
+// (hi, lo) += a * b, lo not folded back: the exact product error and the TwoSum error go to lo
+__device__ __forceinline__ void df_mac_nr(float &hi, float &lo, float a, float b) {
     const float p = a * b;
     const float pe = fmaf(a, b, -p);
     float s, e;
     df_two_sum(hi, p, s, e);
+    hi = s;
     lo += e + pe;
-    hi = s + lo;
-    lo -= hi - s;
+}
+// fold lo back into hi so that |lo| is at most half an ulp of hi
+__device__ __forceinline__ void df_renorm(float &hi, float &lo) {
+    const float s = hi + lo;
+    lo -= s - hi;
+    hi = s;
 }
 struct dfc {
     float rh, rl, ih, il;   // real (hi, lo), imaginary (hi, lo)
 };
-// s += c * x for complex double-float c, x; the lo * lo terms (2^-48 of the product) are dropped
-__device__ __forceinline__ void dfc_mac(dfc &s, float4 c, float4 x) {
+// s += c * x for complex double-float c, x, without the final renormalisation; the lo * lo terms
+// (2^-48 of the product) are dropped
+__device__ __forceinline__ void dfc_mac_nr(dfc &s, float4 c, float4 x) {
     s.rl = fmaf(c.x, x.z, fmaf(c.z, x.x, fmaf(-c.y, x.w, fmaf(-c.w, x.y, s.rl))));
     s.il = fmaf(c.x, x.w, fmaf(c.z, x.y, fmaf(c.y, x.z, fmaf(c.w, x.x, s.il))));
-    df_mac(s.rh, s.rl, c.x, x.x);
-    df_mac(s.rh, s.rl, -c.y, x.y);
-    df_mac(s.ih, s.il, c.x, x.y);
-    df_mac(s.ih, s.il, c.y, x.x);
+    df_mac_nr(s.rh, s.rl, c.x, x.x);
+    df_mac_nr(s.rh, s.rl, -c.y, x.y);
+    df_mac_nr(s.ih, s.il, c.x, x.y);
+    df_mac_nr(s.ih, s.il, c.y, x.x);
+}
+__device__ __forceinline__ void dfc_renorm(dfc &s) {
+    df_renorm(s.rh, s.rl);
+    df_renorm(s.ih, s.il);
 }
 __device__ __forceinline__ void dfc_add(dfc &a, const dfc &b) {
     float s, e;
@@ -176,6 +185,50 @@ __device__ __forceinline__ void dfc_warp_sum(dfc &a) {
         dfc_add(a, b);
     }
 }
+// s += sum_c a[c] x[c] over c = t, t + T, t + 2T, ... < n (T threads, t this thread).  Batches of
+// U = 4 entries per thread, software-pipelined: the next batch's eight 16-byte loads (C streamed,
+// evict-first; x from L2) are issued before the current batch's arithmetic; one renormalisation
+// per batch (lo then holds at most ~8 half-ulps of hi before it is folded back).
+template <int T>
+__device__ __forceinline__ void dfc_row_dot(dfc &s, const float4 *__restrict__ a, const float4 *__restrict__ x, long n,
+                                            int t) {
+    constexpr int U = 4;
+    long c = t;
+    float4 an[U], xn[U];
+    bool have = c + (long)(U - 1) * T < n;
+    if (have) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            an[u] = __ldcs(&a[c + u * T]);
+            xn[u] = __ldg(&x[c + u * T]);
+        }
+    }
+    while (have) {
+        float4 ac[U], xc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ac[u] = an[u];
+            xc[u] = xn[u];
+        }
+        c += (long)U * T;
+        have = c + (long)(U - 1) * T < n;
+        if (have) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                an[u] = __ldcs(&a[c + u * T]);
+                xn[u] = __ldg(&x[c + u * T]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) dfc_mac_nr(s, ac[u], xc[u]);
+        dfc_renorm(s);
+    }
+    for (; c < n; c += T) {
+        dfc_mac_nr(s, __ldcs(&a[c]), __ldg(&x[c]));
+        dfc_renorm(s);
+    }
+}
+
 // (hi, lo) complex64 split of a complex128 value: hi the nearest complex64, lo the nearest
 // complex64 to the (exact) remainder
 __device__ __forceinline__ float4 df_split(double re, double im) {
