@@ -333,8 +333,7 @@ __global__ void __launch_bounds__(BATCH_DF_THREADS)
     const float4 *a = C2all + coff[g] + (size_t)r * n;
     const float4 *xv = x2 + geo[g].noff;
     dfc s = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (long c = threadIdx.x; c < n; c += BATCH_DF_THREADS) dfc_mac(s, __ldcs(&a[c]), __ldg(&xv[c]));
+    dfc_row_dot<BATCH_DF_THREADS>(s, a, xv, n, threadIdx.x);
     dfc_warp_sum(s);
     __shared__ dfc part[BATCH_DF_THREADS / 32];
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;

@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(GEMV_DF_THREADS) k_gemv_rows_df(const float4 *
     if (r >= nrows) return;
     const float4 *a = C2 + (size_t)r * ncols;
     dfc s = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (long c = threadIdx.x; c < ncols; c += GEMV_DF_THREADS) dfc_mac(s, __ldcs(&a[c]), __ldg(&x2[c]));
+    dfc_row_dot<GEMV_DF_THREADS>(s, a, x2, ncols, threadIdx.x);
     dfc_warp_sum(s);
     __shared__ dfc part[GEMV_DF_THREADS / 32];
     const int w = threadIdx.x >> 5;
