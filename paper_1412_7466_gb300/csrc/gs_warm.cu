@@ -57,7 +57,6 @@ __device__ __forceinline__ float dsilu_f(float z) {
     const float g = 1.0f / (1.0f + expf(-z));
     return g * (1.0f + z * (1.0f - g));
 }
-__device__ __forceinline__ float ld(const float *p) { return *p; }
 __device__ __forceinline__ float ld(const bf16 *p) { return __bfloat162float(*p); }
 
 // x0 = bf16((X - mu) / sd)
