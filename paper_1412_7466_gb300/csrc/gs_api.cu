@@ -66,6 +66,7 @@ void free_angle_geometry(AngleData &a) {
     dfree(a.B32);
     dfree(a.C2);
     a.C2_off = false;
+    a.C2_ready = false;
     dfree(a.beta);
     a.iters = 0;
     a.outer = 0;

@@ -1221,16 +1221,21 @@ int gs_factor_batch(gs_ctx *c) {
         k_to_c64_b<<<nblk(nb), 256, 0, c->stream>>>(b->B[q], nb, b->B32[q]);
         GS_CHECK_LAUNCH(c);
         // double-float copy of C (the mixed inner operator's C x), unless an entry is out of range
+        // (no room for the copy, or an entry out of range: the FP64 product stays for this angle)
         if (!b->dflag) GS_TRY(dalloc_b(c, &b->dflag, 1));
-        GS_CUDA(c, cudaMemsetAsync(b->dflag, 0, sizeof(int), c->stream));
-        GS_TRY(dalloc_b(c, &b->C2[q], o));
-        GS_COUNT_LAUNCH(c);
-        k_b_split_df<<<nblk((long)o), 256, 0, c->stream>>>(b->Cm[q], (long)o, b->C2[q], GS_DF_LIMIT, b->dflag);
-        GS_CHECK_LAUNCH(c);
-        int big = 0;
-        GS_CUDA(c, cudaMemcpyAsync(&big, b->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        GS_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (big) dfree_b(b->C2[q]);
+        if (cudaMalloc((void **)&b->C2[q], sizeof(float4) * o) != cudaSuccess) {
+            cudaGetLastError();
+            b->C2[q] = nullptr;
+        } else {
+            GS_CUDA(c, cudaMemsetAsync(b->dflag, 0, sizeof(int), c->stream));
+            GS_COUNT_LAUNCH(c);
+            k_b_split_df<<<nblk((long)o), 256, 0, c->stream>>>(b->Cm[q], (long)o, b->C2[q], GS_DF_LIMIT, b->dflag);
+            GS_CHECK_LAUNCH(c);
+            int big = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&big, b->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            GS_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (big) dfree_b(b->C2[q]);
+        }
     }
     // workspace
     b->kdim = 0;

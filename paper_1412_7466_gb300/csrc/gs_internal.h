@@ -40,7 +40,9 @@ struct AngleData {
     cplx *Cm = nullptr;          // nC x n row-major
     mutable float2 *B32 = nullptr;   // complex64 copy of B for the mixed inner operator (on first use)
     mutable float4 *C2 = nullptr;    // double-float (hi, lo) copy of C for the mixed inner operator
-    mutable bool C2_off = false;     // C has entries beyond GS_DF_LIMIT: the inner operator keeps FP64
+    mutable bool C2_off = false;     // C has entries beyond GS_DF_LIMIT (or no memory for the copy):
+                                     // the inner operator keeps the FP64 product
+    mutable bool C2_ready = false;   // C2 holds the split of the current C
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
     int sweeps32 = 0;            // FP32-guided sweeps before them

@@ -333,7 +333,14 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
         }
         if (!a.C2 && !a.C2_off) {   // double-float copy of C, once per geometry and angle
             const long nc2 = (long)nC * n;
-            GS_CUDA(c, cudaMalloc((void **)&a.C2, sizeof(float4) * nc2));
+            if (cudaMalloc((void **)&a.C2, sizeof(float4) * nc2) != cudaSuccess) {
+                cudaGetLastError();   // no room for the copy: the FP64 product stays
+                a.C2 = nullptr;
+                a.C2_off = true;
+            }
+        }
+        if (a.C2 && !a.C2_ready) {
+            const long nc2 = (long)nC * n;
             GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
             GS_COUNT_LAUNCH(c);
             k_split_df<<<(int)((nc2 + 255) / 256), 256, 0, c->stream>>>(a.Cm, nc2, a.C2, GS_DF_LIMIT, c->iflag);
@@ -345,6 +352,8 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
                 cudaFree(a.C2);
                 a.C2 = nullptr;
                 a.C2_off = true;
+            } else {
+                a.C2_ready = true;
             }
         }
         GS_COUNT_LAUNCH(c);
