@@ -29,6 +29,36 @@ __global__ void k_gemv_rows(const cplx *__restrict__ A, int nrows, int ncols, lo
     if (lane == 0) y[warp] = scale ? cscale(s, scale[warp]) : s;
 }
 
+// y[r] = sum_c A[r, c] x[c] for few long rows (C: ~1300 rows of M (2p+1) columns), FP64: one block
+// of GEMV_BLK_THREADS per row, two independent accumulators per thread.  With a warp per row only
+// ~8 warps per SM would be in flight for C, about half of what the FP64 pipe needs.
+constexpr int GEMV_BLK_THREADS = 128;
+__global__ void __launch_bounds__(GEMV_BLK_THREADS) k_gemv_rows_blk(const cplx *__restrict__ A, int nrows, long ncols,
+                                                                   const cplx *__restrict__ x,
+                                                                   cplx *__restrict__ y) {
+    const int r = blockIdx.x;
+    if (r >= nrows) return;
+    const cplx *a = A + (size_t)r * ncols;
+    cplx s0 = C(0, 0), s1 = C(0, 0);
+    long c = threadIdx.x;
+    for (; c + GEMV_BLK_THREADS < ncols; c += 2 * GEMV_BLK_THREADS) {
+        cfma(s0, __ldcs(&a[c]), __ldg(&x[c]));
+        cfma(s1, __ldcs(&a[c + GEMV_BLK_THREADS]), __ldg(&x[c + GEMV_BLK_THREADS]));
+    }
+    if (c < ncols) cfma(s0, __ldcs(&a[c]), __ldg(&x[c]));
+    s0 = cadd(s0, s1);
+    s0.x = warp_sum(s0.x);
+    s0.y = warp_sum(s0.y);
+    __shared__ cplx part[GEMV_BLK_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cplx t = part[0];
+        for (int k = 1; k < GEMV_BLK_THREADS / 32; ++k) t = cadd(t, part[k]);
+        y[r] = t;
+    }
+}
+
 // y[j] = coef[j] * sum_{i < nr} conj(W[i, j]) g[i]   (W column-major, warp per column)
 __global__ void k_gemv_colsH(const cplx *__restrict__ W, int m, int nr, int ncols, const cplx *__restrict__ g,
                              const double *__restrict__ coef, cplx *__restrict__ y) {
@@ -362,7 +392,7 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
             GS_COUNT_LAUNCH(c);
             k_gemv_rows_df<<<nC, GEMV_DF_THREADS, 0, c->stream>>>(a.C2, nC, n, c->xdf, c->g);
         } else {
-            k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+            k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
         }
         GS_COUNT_LAUNCH(c);
         k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
@@ -374,7 +404,7 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
         return GS_OK;
     }
     GS_COUNT_LAUNCH(c);
-    k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+    k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
     GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
     GS_COUNT_LAUNCH(c);
@@ -390,7 +420,7 @@ int gs_layer_response_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *z
     const Layout &ly = c->lay;
     int n = c->n(), nB = ly.nB(), nC = ly.nC();
     GS_COUNT_LAUNCH(c);
-    k_gemv_rows<<<warps_blocks(nC), 256, 0, c->stream>>>(a.Cm, nC, n, n, x, nullptr, c->g);
+    k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
     GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
     GS_COUNT_LAUNCH(c);
