@@ -197,7 +197,7 @@ int gs_translate_noalloc(int M, int p, const double *xy_dev, double k2, double d
                          void *cuda_stream);
 
 /* ---- batched solves (many geometries on one grating) ----------------------------------------- */
-/* Batched form (north_star "Batching"): G geometries of uneven size, all with the same multipole
+/* Batched form: G geometries of uneven size, all with the same multipole
  * order, share the per-angle grating factorisation; their translations run as one persistent launch
  * (an atomic work queue over (geometry, 4 targets, chunk of source images) items, largest geometries
  * first, chunk length and blocks per SM picked by timing candidates on the first factorisation),

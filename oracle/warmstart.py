@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE (see the package docstring): never used by the product path.
 
-The paper has no learned component; the warm start is the task's addition to the method of Sec. 5
+The paper has no learned component; the warm start is an addition to the method of Sec. 5
 (the iterative solve of the preconditioned Schur system for the outgoing coefficients beta).  What
 it computes, stated here in plain FP64 so that the kernels can be checked against it:
 

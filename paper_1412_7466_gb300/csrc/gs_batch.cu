@@ -1,6 +1,5 @@
-// Batched solves: many inclusion geometries of uneven size on one factored grating (the benchmark spec
-// "Batching"), solved in lockstep by GMRES (FP64) or by the mixed refinement (complex64 inner
-// solves, FP64 residuals).
+// Batched solves: many inclusion geometries of uneven size on one factored grating, solved in
+// lockstep by GMRES (FP64) or by the mixed refinement (complex64 inner solves, FP64 residuals).
 //
 //  * Translation: one persistent launch for the whole batch.  The (geometry, group of 4 targets,
 //    chunk of source images) work items are taken from an atomic counter by a fixed grid of

@@ -702,7 +702,7 @@ extern "C" int gs_warm_start(gs_ctx *c, int angle, gs_c128 *beta0_dev, double *r
     GS_TRY(forward(c, q->X, c->M));
     GS_COUNT_LAUNCH(c);
     k_ws_guess<<<nblk(n), 256, 0, st>>>(q->out, q->w, c->s, q->norm + 2 * NIN, c->M, c->nc, beta0);
-    // the judge: ||b - L beta_0|| against ||b|| (the zero start), in FP64
+    // acceptance test of the start: ||b - L beta_0|| against ||b|| (the zero start), in FP64
     GS_TRY(gs_rhs_impl(c, a, q->t1));
     GS_TRY(gs_apply_impl(c, a, beta0, q->t2, GS_FP64));
     GS_COUNT_LAUNCH(c);
