@@ -70,7 +70,8 @@ def scaled_grating(base: str, k_top: float) -> dict:
 
 
 def wood_angle(k1: float, d: float = 1.0, n: int = 1) -> float:
-    """Incidence angle (paper convention, sin < 0) at which kappa_{-n} = -k1 (a Wood anomaly, Sec. 2)."""
+    """Incidence angle (paper convention, sin < 0) at which kappa_n = kappa + 2 pi n / d = k1, so that
+    k_{1,n} = 0 (a Wood anomaly, Sec. 2)."""
     return -math.acos(1.0 - 2.0 * math.pi * n / (k1 * d))
 
 
