@@ -178,20 +178,25 @@ int gs_bragg(gs_ctx *ctx, int angle, int *n_top, int *orders_top, gs_c128 *c,
  * of gs_translate (alpha = T beta over all pairs and the +-d images) without a context.  Inputs and
  * outputs are the caller's device buffers on the current device: xy_dev holds the M centres
  * (x, y interleaved, FP64), beta_dev and alpha_dev hold M (2p+1) complex128 values each (layout
- * of gs_translate), k2 is the middle-layer wavenumber, d the period, alpha_re + i alpha_im the
- * Bloch phase exp(i k1 cos(theta) d); precision GS_FP64 or GS_C64; work is queued on cuda_stream
- * (NULL = legacy default stream) and is asynchronous.
+ * of gs_translate; alpha_dev must not overlap the inputs), k2 is the middle-layer wavenumber, d
+ * the period, alpha_re + i alpha_im the Bloch phase exp(i k1 cos(theta) d); precision GS_FP64 or
+ * GS_C64; work is queued on cuda_stream (NULL = legacy default stream).  GS_FP64 is asynchronous.
+ * GS_C64 first finds the smallest image distance R_min on the device and reads it back (one wait
+ * for cuda_stream), then refuses with GS_ERR_ARG, as gs_translate does, a geometry whose largest
+ * Hankel value |H_2p(k2 R_min)| would exceed 1e36 (FP32 range); the translation itself is then
+ * queued asynchronously.
  * Nothing is allocated: the chunk partials live in a fixed device array of 2^19 complex128 values
  * (8 MiB) compiled into the library, which every GPU that loads the library holds until exit.
  * Sizes: M (2p+1) must not exceed 2^19 (524288) for GS_FP64; for GS_C64, whose complex64 copy of
- * beta and float image coordinates share the array, M (2p+1) + ceil(M (2p+1) / 2) + 3M must not
- * exceed 2^19 (M <= 12945 at p = 12); else GS_ERR_ARG is returned before any device work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
- * precision; GS_ERR_CUDA if the launch fails.  The first call on a device looks up the array's
+ * beta, float image coordinates and R_min share the array, M (2p+1) + ceil(M (2p+1) / 2) + 3M + 1
+ * must not exceed 2^19 (M <= 12945 at p = 12); else GS_ERR_ARG is returned before any device
+ * work; GS_ERR_ARG also for M < 1, null or aliased pointers, k2 <= 0, d <= 0, an unsupported p or
+ * precision; GS_ERR_CUDA if a launch fails.  The first call on a device looks up the array's
  * device address (once per device, with that device current); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's partials: every
- * partial a call reads is written by that same call, so nothing needs clearing, but calls whose
- * work overlaps on the GPU (other streams, other host threads) race on the array and must be
- * serialised by the caller. */
+ * stream capture.  All calls share the one array and it keeps the last call's contents: every
+ * value a call reads there is written by that same call (R_min's slot is reset first), so nothing
+ * needs clearing, but calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on the array and must be serialised by the caller. */
 int gs_translate_noalloc(int M, int p, const double *xy_dev, double k2, double d, double alpha_re,
                          double alpha_im, const gs_c128 *beta_dev, gs_c128 *alpha_dev, int precision,
                          void *cuda_stream);
@@ -302,6 +307,16 @@ int gs_mlp_train_step(gs_ctx *ctx, const float *X_dev, const float *Y_dev, long 
 /* Features of the current geometry at `angle` into X_dev[M][64] (needs gs_factor and a network of
  * the context's order). */
 int gs_ws_features(gs_ctx *ctx, int angle, float *X_dev);
+/* Fixes the network's normalisations from the current geometry and its last solution at `angle`
+ * (run once, after the first solved sweep point), in place of the mu, sd and scale loaded by
+ * gs_mlp_set_params (the trained weights are kept): mu and sd of each feature over the M inclusions
+ * (mean and population standard deviation), except theta and k1, which take the sweep's uniform
+ * ranges [theta_lo, theta_hi] and [k_lo, k_hi] (mean (lo + hi)/2, sd (hi - lo)/sqrt(12)); a constant
+ * feature gets sd = 1.  scale[n] = rms over the inclusions of t_n (as in gs_ws_targets), or 0 where
+ * the order's share of beta, rms(s_n t_n), is at most `share` times the largest order's (such orders
+ * are left to the empty grating's field).  GS_ERR_ARG for lo >= hi, non-finite ranges or share < 0. */
+int gs_ws_normalise(gs_ctx *ctx, int angle, double theta_lo, double theta_hi, double k_lo, double k_hi,
+                    double share);
 /* Training targets from the last solution at `angle`: Y_dev[M][2(2p+1)] = t / scale split as
  * [Re, Im], t = T beta - B_phys A^+ C beta (the incoming field from the other inclusions, their
  * images and the layers' response; equal to beta/s - w at a converged beta). */

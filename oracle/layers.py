@@ -116,26 +116,6 @@ def kernels(tpos, tnrm, spos, snrm, k):
     return {"S": S, "D": D, "N": N, "T": T}
 
 
-def log_coefficients(tpos, tnrm, spos, snrm, k):
-    """Coefficient of log r in each kernel (obtained by replacing H_n by (2i/pi) J_n, since
-    Y_n(z) = (2/pi) J_n(z) log(z/2) + terms without a logarithm)."""
-    Rx = tpos[:, None, 0] - spos[None, :, 0]
-    Ry = tpos[:, None, 1] - spos[None, :, 1]
-    r = np.hypot(Rx, Ry)
-    kr = k * r
-    J0 = jv(0, kr)
-    J1 = jv(1, kr)
-    Rnx = Rx * tnrm[:, None, 0] + Ry * tnrm[:, None, 1]
-    Rny = Rx * snrm[None, :, 0] + Ry * snrm[None, :, 1]
-    nn = tnrm[:, None, 0] * snrm[None, :, 0] + tnrm[:, None, 1] * snrm[None, :, 1]
-    c = -1.0 / (2.0 * math.pi)
-    S = c * J0
-    D = c * k * J1 * Rny / r
-    N = -c * k * J1 * Rnx / r
-    T = c * k * (k * J0 * Rnx * Rny / r**2 - 2.0 * J1 * Rnx * Rny / r**3 + J1 * nn / r)
-    return {"S": S, "D": D, "N": N, "T": T}
-
-
 def diag_limits(ka, kb):
     """Limits at coincidence of the kernel differences (ka - kb), per unit arc length.
 

@@ -92,6 +92,30 @@ def features(xy: np.ndarray, theta: float, k1: float, w0: np.ndarray, d: float =
     return F
 
 
+def standardisation(X0: np.ndarray, theta_range, k_range):
+    """(mu, sd) of the 64 features: mean and population standard deviation over one geometry's
+    inclusions, except theta (column 10) and k1 (column 11), which take the sweep's ranges read as
+    uniform distributions (mean (lo + hi)/2, sd (hi - lo)/sqrt(12)); a constant column gets sd = 1."""
+    X0 = np.asarray(X0, dtype=np.float64)
+    mu, sd = X0.mean(0), X0.std(0)
+    for col, (lo, hi) in ((10, theta_range), (11, k_range)):
+        mu[col] = 0.5 * (lo + hi)
+        sd[col] = (hi - lo) / math.sqrt(12.0)
+    sd[~(sd > 1e-12)] = 1.0
+    return mu, sd
+
+
+def order_scale(ms_t: np.ndarray, ms_st: np.ndarray, share: float = 1e-4) -> np.ndarray:
+    """Per-order output scale from (mean |t_n|^2, mean |s_n t_n|^2) of one solved point: rms(t_n)
+    where the order's share of beta, rms(s_n t_n), exceeds `share` times the largest order's, else 0
+    (the order is left to the empty grating's field)."""
+    rt = np.sqrt(np.asarray(ms_t, dtype=np.float64))
+    rst = np.sqrt(np.asarray(ms_st, dtype=np.float64))
+    top = rst.max() if np.isfinite(rst.max()) else 0.0
+    keep = (rst > share * top) & (rt > 0) & np.isfinite(rt)
+    return np.where(keep, rt, 0.0)
+
+
 def incoming_empty(prob) -> np.ndarray:
     """w = B_phys A^+ f: the empty grating's incoming coefficients about every centre, (M, 2p+1)."""
     return (prob.B @ prob.pinv.apply(prob.eg.f)).reshape(prob.M, prob.nc)

@@ -106,6 +106,8 @@ _SIGS = {
     "gs_ws_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "gs_ws_targets": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "gs_ws_moments": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "gs_ws_normalise": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double]),
     "gs_warm_start": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _dp, _ip]),
 }
 
@@ -136,10 +138,31 @@ def load_library(path: str = LIB_PATH):
 
 def translate_noalloc(xy, beta, out, p, k2, d, alpha, precision=GS_FP64, stream=None):
     """alpha = T beta through the allocation-free entry point (no context; for callers that
-    cannot allocate device memory).  xy: (M, 2) float64, beta/out: M (2p+1) complex128, all CUDA
-    tensors on the current device.  Returns the status code."""
+    cannot allocate device memory).  xy: (M, 2) float64, beta and out: M (2p+1) complex128, all
+    contiguous CUDA tensors on the current device, out not overlapping beta or xy (the library
+    trusts these sizes, so they are checked here).  Returns the status code."""
     import torch
     lib = load_library()
+    if not (isinstance(xy, torch.Tensor) and xy.dtype == torch.float64 and xy.dim() == 2 and xy.shape[1] == 2):
+        raise ValueError("xy must be a (M, 2) float64 tensor")
+    n = int(xy.shape[0]) * (2 * int(p) + 1)
+    for name, t in (("beta", beta), ("out", out)):
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.complex128 and t.numel() == n):
+            raise ValueError(f"{name} must be a complex128 tensor of M (2p+1) = {n} values")
+    dev = torch.cuda.current_device()
+    for name, t in (("xy", xy), ("beta", beta), ("out", out)):
+        if not t.is_cuda or t.device.index != dev or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous tensor on the current CUDA device ({dev})")
+
+    def span(t):
+        a = t.data_ptr()
+        return a, a + t.numel() * t.element_size()
+
+    o0, o1 = span(out)
+    for t in (beta, xy):
+        a0, a1 = span(t)
+        if t.numel() and out.numel() and a0 < o1 and o0 < a1:
+            raise ValueError("out overlaps an input")
     st = stream if stream is not None else torch.cuda.current_stream()
     a = complex(alpha)
     return lib.gs_translate_noalloc(int(xy.shape[0]), int(p), _vp(xy.data_ptr()), float(k2), float(d), a.real,
@@ -460,6 +483,12 @@ class GratingSolver:
         self._check(self.lib.gs_ws_moments(self.ctx, angle, ms.ctypes.data_as(_dp)), "gs_ws_moments")
         nc = 2 * self._mlp_p + 1
         return ms[:nc], ms[nc:]
+
+    def ws_normalise(self, theta_range, k_range, share=1e-4, angle=0):
+        """Fixes the network's feature standardisation and per-order output scale from the current
+        geometry and its last solution at `angle` (gs_ws_normalise)."""
+        self._check(self.lib.gs_ws_normalise(self.ctx, angle, float(theta_range[0]), float(theta_range[1]),
+                                             float(k_range[0]), float(k_range[1]), float(share)), "gs_ws_normalise")
 
     def warm_start(self, angle=0):
         """(beta_0 device tensor, its relative residual, used); beta_0 is zero when not used."""

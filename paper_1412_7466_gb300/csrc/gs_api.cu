@@ -258,6 +258,11 @@ int gs_create(gs_ctx **out, int device, void *cuda_stream) {
     gs_ctx *c = new gs_ctx();
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1) {
+        cudaGetLastError();
+        delete c;
+        return GS_ERR_CUDA;
+    }
     if (cudaMalloc((void **)&c->dscal, sizeof(double) * 16) != cudaSuccess ||
         cudaMallocHost((void **)&c->hscal, sizeof(double) * 16) != cudaSuccess ||
         cudaMalloc((void **)&c->dcount, sizeof(unsigned long long)) != cudaSuccess) {

@@ -3,7 +3,7 @@
 //
 //  * Translation: one persistent launch for the whole batch.  The (geometry, group of 4 targets,
 //    chunk of source images) work items are taken from an atomic counter by a fixed grid of
-//    152 x blocks-per-SM blocks, largest geometries first; each item writes its partial sums to its
+//    SMs x blocks-per-SM blocks, largest geometries first; each item writes its partial sums to its
 //    own slot, and a second kernel adds each target's slots in a fixed order (deterministic).
 //    The chunk length and the blocks per SM are picked by timing candidates on first use (autotuner).
 //  * Low rank: the grating factorisation (U, V Sigma, D, coef) is shared by all geometries, so the
@@ -767,8 +767,7 @@ template <int P>
 int launch_batch_translate(gs_ctx *c, gs_batch *b, const AngleData &a, const cplx *x, cplx *out, int precision,
                            const int *active) {
     cudaStream_t st = c->stream;
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int sms = c->sms;
     if (precision == GS_C64) {
         GS_COUNT_LAUNCH(c);
         k_b_to_c64<<<nblk(b->Ntot), 256, 0, st>>>(x, b->Ntot, b->b32);

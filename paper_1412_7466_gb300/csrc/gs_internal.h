@@ -56,6 +56,7 @@ struct gs_mlp;     // network of the learned warm start (gs_warm.cu)
 
 struct gs_ctx {
     int device = 0;
+    int sms = 1;                  // streaming multiprocessors of the device (queried at gs_create)
     cudaStream_t stream = nullptr;
     std::string err;
 

@@ -11,9 +11,10 @@
 // forms H_q u^q and (-1)^q H_q conj(u)^q with u = e^{i Th}, and applies the (2p+1)x(2p+1)
 // Toeplitz block to the staged coefficients with the 2p+1 accumulators held in registers (fully
 // unrolled for the compile-time order P).  Warp-shuffle reductions combine the lanes.  The source
-// images are split into `nsplit` chunks across blockIdx.y to fill the 152 SMs; a second kernel
+// images are split into `nsplit` chunks across blockIdx.y to fill the SMs; a second kernel
 // sums the chunk partials in a fixed order (deterministic).
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "gs_internal.h"
@@ -131,7 +132,6 @@ k_translate_f64(const double *__restrict__ xy, int M, const cplx *__restrict__ b
 typedef cplxf_t cplxf;
 __device__ __forceinline__ cplxf CF(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ cplxf cmulf(cplxf a, cplxf b) { return gs_cmulf(a, b); }
-__device__ __forceinline__ void cfmaf(cplxf &acc, cplxf a, cplxf b) { gs_cfmaf(acc, a, b); }
 
 // beta (complex128) -> complex64 once per call
 __global__ void k_beta_to_c64(const cplx *__restrict__ b, long n, cplxf *__restrict__ b32) {
@@ -354,7 +354,7 @@ int launch_translate(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out,
     const int M = c->M;
     const int gx = (M + WARPS - 1) / WARPS;
     // enough blocks for several waves over the SMs
-    int nsplit = (int)((152L * 8 + gx - 1) / gx);
+    int nsplit = (int)((c->sms * 8L + gx - 1) / gx);
     if (nsplit < 1) nsplit = 1;
     if (nsplit > 64) nsplit = 64;
     if ((long)nsplit * 32 > 3L * M) nsplit = (int)((3L * M + 31) / 32);
@@ -477,25 +477,72 @@ constexpr int GS_NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mutex;
 cplx *g_noalloc_scratch[GS_NOALLOC_MAX_DEVICES] = {};   // device address of the array, per device
 
+// Smallest distance between a target centre and any source image (all pairs, images l = -1, 0, 1,
+// the target's own l = 0 copy left out), as the bit pattern of a non-negative double (ordered like
+// the value) folded into *slot by atomicMin.  One thread per target.
+__global__ void k_noalloc_min_dist(const double *xy, int M, double d, unsigned long long *slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double m2 = 1e300;
+    if (i < M) {
+        const double xi = xy[2 * i], yi = xy[2 * i + 1];
+        for (int j = 0; j < M; ++j) {
+            const double dy = yi - xy[2 * j + 1];
+            const double dx0 = xi - xy[2 * j];
+#pragma unroll
+            for (int l = -1; l <= 1; ++l) {
+                if (l == 0 && j == i) continue;
+                const double dx = dx0 - l * d;
+                m2 = fmin(m2, dx * dx + dy * dy);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m2 = fmin(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    if ((threadIdx.x & 31) == 0 && i - (int)(threadIdx.x & 31) < M)
+        atomicMin(slot, (unsigned long long)__double_as_longlong(sqrt(m2)));
+}
+
+// The complex64 form's range check without a context: the smallest image distance R_min is found
+// on the device (into the array's last slot), read back (one stream synchronisation) and tested as
+// in gs_c64_range: |H_2p(k2 R_min)| ~ (2p-1)!/pi (2/(k2 R_min))^{2p} must stay below 1e36.
+int noalloc_c64_range(int M, int p, const double *xy, double k, double d, cudaStream_t st,
+                      unsigned long long *slot) {
+    if (cudaMemsetAsync(slot, 0x7f, sizeof(unsigned long long), st) != cudaSuccess) return GS_ERR_CUDA;
+    k_noalloc_min_dist<<<(M + 127) / 128, 128, 0, st>>>(xy, M, d, slot);
+    unsigned long long bits = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    double rmin;
+    std::memcpy(&rmin, &bits, sizeof(rmin));
+    const int q = 2 * p;
+    const double z = k * rmin;
+    double l10 = 0.0;
+    if (z > 0.0 && z < q) l10 = (std::lgamma((double)q) - std::log(GS_PI)) / std::log(10.0) + q * std::log10(2.0 / z);
+    return (!(z > 0.0) || l10 > 36.0) ? GS_ERR_ARG : GS_OK;
+}
+
 template <int P>
 int noalloc_launch(int M, const double *xy, const cplx *beta, double k, double d, cplx alpha, int precision,
-                   cplx *out, cudaStream_t st, cplx *scratch) {
+                   cplx *out, cudaStream_t st, cplx *scratch, int sms) {
     constexpr int WARPS = 4;
     constexpr int NC = 2 * P + 1;
     const int gx = (M + WARPS - 1) / WARPS;
-    int nsplit = (int)((152L * 8 + gx - 1) / gx);
+    int nsplit = (int)((sms * 8L + gx - 1) / gx);
     if (nsplit > 64) nsplit = 64;
     if ((long)nsplit * 32 > 3L * M) nsplit = (int)((3L * M + 31) / 32);
     if (nsplit < 1) nsplit = 1;
     const long len = (long)M * NC;
-    // complex64 form: the converted coefficients take ceil(len/2) complex128 slots at the end of the
-    // array and the (hi, lo) float image coordinates 3M slots before them
-    const long room = (precision == GS_C64) ? GS_NOALLOC_CAPACITY - (len + 1) / 2 - 3L * M : GS_NOALLOC_CAPACITY;
+    // complex64 form, from the end of the array: one slot for the range check's distance, the
+    // converted coefficients (ceil(len/2) complex128 slots) and the (hi, lo) float image
+    // coordinates (3M slots); the partials take what is left
+    const long room = (precision == GS_C64) ? GS_NOALLOC_CAPACITY - 1 - (len + 1) / 2 - 3L * M : GS_NOALLOC_CAPACITY;
     if (room < len) return GS_ERR_ARG;   // exceeds the fixed scratch
     if ((long)nsplit * len > room) nsplit = (int)(room / len);
     if (nsplit < 1) return GS_ERR_ARG;
     dim3 grid(gx, nsplit);
     if (precision == GS_C64) {
+        GS_TRY(noalloc_c64_range(M, P, xy, k, d, st, (unsigned long long *)(scratch + GS_NOALLOC_CAPACITY - 1)));
         float4 *img = (float4 *)(scratch + room);
         cplxf *b32 = (cplxf *)(scratch + room + 3L * M);
         k_images_c64<<<(int)((3L * M + 255) / 256), 256, 0, st>>>(xy, M, d, img);
@@ -541,21 +588,26 @@ extern "C" int gs_translate_noalloc(int M, int p, const double *xy_dev, double k
         }
         scratch = g_noalloc_scratch[dev];
     }
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     const cplx alpha = C(alpha_re, alpha_im);
     const cplx *beta = (const cplx *)beta_dev;
     cplx *out = (cplx *)alpha_dev;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     switch (p) {
-        case 1: return noalloc_launch<1>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 2: return noalloc_launch<2>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 3: return noalloc_launch<3>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 4: return noalloc_launch<4>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 5: return noalloc_launch<5>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 6: return noalloc_launch<6>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 7: return noalloc_launch<7>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 8: return noalloc_launch<8>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 10: return noalloc_launch<10>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        case 12: return noalloc_launch<12>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
-        default: return noalloc_launch<16>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch);
+        case 1: return noalloc_launch<1>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 2: return noalloc_launch<2>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 3: return noalloc_launch<3>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 4: return noalloc_launch<4>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 5: return noalloc_launch<5>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 6: return noalloc_launch<6>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 7: return noalloc_launch<7>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 8: return noalloc_launch<8>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 10: return noalloc_launch<10>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        case 12: return noalloc_launch<12>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
+        default: return noalloc_launch<16>(M, xy_dev, beta, k2, d, alpha, precision, out, st, scratch, sms);
     }
 }

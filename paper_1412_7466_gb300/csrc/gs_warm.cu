@@ -340,6 +340,52 @@ __global__ void k_ws_guess(const float *__restrict__ out, const cplx *__restrict
     beta0[e] = cmul(s[e], a);
 }
 
+// Feature standardisation from one geometry (one block per feature column): mu = the column's mean
+// over the M inclusions and sd = its population standard deviation (two passes, FP64 sums), except
+// theta (column 10) and k1 (column 11), which take the sweep's uniform ranges: mean (lo + hi)/2 and
+// sd (hi - lo)/sqrt(12); a constant column (sd <= 1e-12) gets sd = 1.
+__global__ void k_ws_colstats(const float *__restrict__ X, int M, double th_lo, double th_hi, double k_lo,
+                              double k_hi, float *__restrict__ norm) {
+    __shared__ double sh[32];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) s += X[(size_t)i * NIN + k];
+    const double mu = block_sum(s, sh) / M;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double e = X[(size_t)i * NIN + k] - mu;
+        v += e * e;
+    }
+    double sd = sqrt(block_sum(v, sh) / M);
+    if (threadIdx.x != 0) return;
+    double m = mu;
+    if (k == 10) { m = 0.5 * (th_lo + th_hi); sd = (th_hi - th_lo) / sqrt(12.0); }
+    if (k == 11) { m = 0.5 * (k_lo + k_hi); sd = (k_hi - k_lo) / sqrt(12.0); }
+    if (!(sd > 1e-12)) sd = 1.0;
+    norm[k] = (float)m;
+    norm[NIN + k] = (float)sd;
+}
+
+// Per-order output scale from the target moments ms[n] = mean |t_n|^2, ms[nc + n] = mean |s_n t_n|^2
+// (one block of >= nc threads).  The start's error is s (.) (t_hat - t), so an order matters in
+// proportion to its share of beta, rms(s_n t_n); orders whose share is at most `share` times the
+// largest are not predicted (scale 0: the empty grating's field alone), because any error of the
+// network there is multiplied by the translation's large high-order entries; the others take
+// rms(t_n), which gives their normalised targets unit size.
+__global__ void k_ws_order_scale(const double *__restrict__ ms, int nc, double share, float *__restrict__ scale) {
+    __shared__ double top;
+    const int n = threadIdx.x;
+    if (n == 0) {
+        double t = 0.0;
+        for (int q = 0; q < nc; ++q) t = fmax(t, sqrt(ms[nc + q]));
+        top = isfinite(t) ? t : 0.0;
+    }
+    __syncthreads();
+    if (n >= nc) return;
+    const double rt = sqrt(ms[n]), rst = sqrt(ms[nc + n]);
+    scale[n] = (rst > share * top && rt > 0.0 && isfinite(rt)) ? (float)rt : 0.f;
+}
+
 // out[0] = ||b - y||^2, out[1] = ||b||^2
 __global__ void k_res_norms(const cplx *__restrict__ b, const cplx *__restrict__ y, long n, double *__restrict__ out) {
     __shared__ double sh[32];
@@ -500,7 +546,7 @@ int loss_grad(gs_ctx *c, const float *X, const float *Y, long rows, double *loss
     cudaStream_t st = c->stream;
     GS_TRY(forward(c, X, rows));
     const long n = rows * q->no;
-    const int lb = 152;
+    const int lb = c->sms;   // partial sums of the loss, one per block
     GS_COUNT_LAUNCH(c);
     k_loss_grad<<<lb, 256, 0, st>>>(q->out, Y, n, q->g3, q->lpart);
     const int gr = (int)((rows + BM - 1) / BM);
@@ -573,8 +619,8 @@ extern "C" int gs_mlp_set_params(gs_ctx *c, int p, const float *params, long n) 
         GS_TRY(walloc(c, &q->grad, o.n));
         GS_TRY(walloc(c, &q->norm, 2 * NIN + nc));
         GS_TRY(walloc(c, &q->wb, o.bn));
-        GS_TRY(walloc(c, &q->lpart, 152));
-        GS_CUDA(c, cudaMallocHost((void **)&q->lhost, sizeof(double) * 152));
+        GS_TRY(walloc(c, &q->lpart, c->sms));
+        GS_CUDA(c, cudaMallocHost((void **)&q->lhost, sizeof(double) * c->sms));
     }
     gs_mlp *q = c->mlp;
     GS_CUDA(c, cudaMemcpyAsync(q->master, params, sizeof(float) * o.n, cudaMemcpyHostToDevice, c->stream));
@@ -669,6 +715,31 @@ extern "C" int gs_ws_moments(gs_ctx *c, int angle, double *ms_host) {
     GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaMemcpyAsync(ms_host, q->w, sizeof(double) * 2 * c->nc, cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+extern "C" int gs_ws_normalise(gs_ctx *c, int angle, double theta_lo, double theta_hi, double k_lo, double k_hi,
+                               double share) {
+    GS_TRY(guard(c));
+    GS_TRY(angle_ready(c, angle));
+    if (!(theta_hi > theta_lo) || !(k_hi > k_lo) || !(share >= 0.0) || !std::isfinite(theta_lo + theta_hi + k_lo + k_hi))
+        return gs_fail(c, GS_ERR_ARG, "sweep ranges must be finite with lo < hi, share >= 0");
+    const AngleData &a = c->ang[angle];
+    gs_mlp *q = c->mlp;
+    cudaStream_t st = c->stream;
+    GS_TRY(gs_incoming_impl(c, a, q->w));
+    GS_COUNT_LAUNCH(c);
+    k_ws_features<<<nblk(c->M), 256, 0, st>>>(c->xy, c->M, a.theta, c->L.k1, c->L.d, q->w, c->nc, c->p, q->X);
+    GS_COUNT_LAUNCH(c);
+    k_ws_colstats<<<NIN, 256, 0, st>>>(q->X, c->M, theta_lo, theta_hi, k_lo, k_hi, q->norm);
+    GS_TRY(gs_translate_impl(c, a, a.beta, q->t1, GS_FP64));
+    GS_TRY(gs_layer_response_impl(c, a, a.beta, q->t2));
+    GS_COUNT_LAUNCH(c);
+    k_ws_moments<<<c->nc, 256, 0, st>>>(q->t1, q->t2, c->s, c->M, c->nc, (double *)q->w);
+    GS_COUNT_LAUNCH(c);
+    k_ws_order_scale<<<1, 64, 0, st>>>((const double *)q->w, c->nc, share, q->norm + 2 * NIN);
+    GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaStreamSynchronize(st));
     return GS_OK;
 }
 

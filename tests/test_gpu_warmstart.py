@@ -145,6 +145,33 @@ def test_targets_and_moments_match_oracle(small):
         np.testing.assert_allclose(got, ref, rtol=1e-6)
 
 
+def test_normalisations_match_oracle(small):
+    """gs_ws_normalise: feature mean and population sd over the geometry (theta and k1 from the
+    sweep ranges) and the per-order scale from the target moments with the 1e-4 share cut, against
+    the oracle's standardisation and order_scale of the oracle's features and moments; the trained
+    weights are left as they were."""
+    from paper_1412_7466_gb300 import GratingSolver
+    cfg, prob, beta, gs, prm = small
+    p = cfg["disks"]["p"]
+    g2 = _solver_for(cfg, prm, p)
+    g2.solve(tol=cfg["tol"], maxit=500)
+    th_r, k_r = (-math.pi / 2 - 1.0, -math.pi / 2 + 1.0), (9.0, 11.0)
+    g2.ws_normalise(th_r, k_r, share=1e-4)
+    got = g2.mlp_get_params().astype(np.float64)
+    g2.close()
+    w_, mu, sd, scale = WS.unpack(got, p)
+    nw = WS.n_weights(p)
+    np.testing.assert_array_equal(got[:nw], prm[:nw].astype(np.float32))
+    w = WS.incoming_empty(prob)
+    Xo = WS.features(prob.disks["xy"], cfg["theta"], prob.eg.k[0], w[:, p], prob.eg.d)
+    muo, sdo = WS.standardisation(Xo, th_r, k_r)
+    np.testing.assert_allclose(mu, muo, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(sd, sdo, rtol=1e-5, atol=1e-6)
+    so = WS.order_scale(*WS.moments(prob, beta), share=1e-4)
+    assert np.array_equal(scale > 0, so > 0)
+    np.testing.assert_allclose(scale, so, rtol=1e-6, atol=0)
+
+
 def _solver_for(cfg, params, p):
     from paper_1412_7466_gb300 import GratingSolver
     g2 = GratingSolver(0)

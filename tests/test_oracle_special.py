@@ -319,3 +319,68 @@ def test_c_direct_sum_matches_dense_translation():
     r1 = T @ b
     r2 = m2l.apply(dk["xy"], 60.0, 12, 1.0, al, b)
     assert np.linalg.norm(r1 - r2) <= 1e-13 * np.linalg.norm(r1)
+
+
+def test_translation_rows_by_direct_field_modes():
+    """translation_apply_rows (the reference of the sampled-row GPU checks) against the field it
+    stands for: around target i, the directly summed outgoing waves of every other particle and of
+    every +-d image (phases alpha^l, i's own l = 0 wave left out) have Fourier modes
+    alpha_m J_m(k r) on a circle of radius r about c_i (Graf, Sec. 4.2 Eq. trans).  The modes come
+    from an FFT of the directly evaluated field, not from any translation formula."""
+    k, p, d = 60.0, 12, 1.0
+    alpha = np.exp(-0.83j)
+    dk = W.disks(40, 0.01, 0.005, 2.0, 40.0, seed=8, p=p)
+    xy = dk["xy"]
+    M, nc = xy.shape[0], 2 * p + 1
+    rng = np.random.default_rng(4)
+    w = np.tile(0.5 ** np.abs(np.arange(-p, p + 1)), M)
+    beta = (rng.standard_normal(M * nc) + 1j * rng.standard_normal(M * nc)) * w
+    B = beta.reshape(M, nc)
+    rows = [0, 17, 39]
+    got = I.translation_apply_rows(xy, k, p, d, alpha, beta, rows)
+    n = np.arange(-p, p + 1)
+    npts = 256
+    t = 2 * np.pi * np.arange(npts) / npts
+    for row, i in zip(got, rows):
+        srcs = [(j, l) for l in (-1, 0, 1) for j in range(M) if not (l == 0 and j == i)]
+        dist = min(np.hypot(*(xy[i] - xy[j] - [l * d, 0.0])) for j, l in srcs)
+        r = 0.6 * dist
+        x = xy[i][None, :] + r * np.stack([np.cos(t), np.sin(t)], axis=1)
+        u = np.zeros(npts, dtype=complex)
+        for j, l in srcs:
+            v = x - (xy[j] + [l * d, 0.0])
+            rho, ph = np.hypot(v[:, 0], v[:, 1]), np.arctan2(v[:, 1], v[:, 0])
+            u += alpha ** l * (hankel1(n[None, :], k * rho[:, None]) * np.exp(1j * n[None, :] * ph[:, None])) @ B[j]
+        modes = np.fft.fft(u) / npts            # mode m at index m mod npts
+        c = modes[n % npts]
+        expect = row * jv(n, k * r)
+        scale = np.max(np.abs(u))
+        assert np.max(np.abs(c - expect)) <= 1e-11 * scale, i
+        # the check is not vacuous: the highest orders carry a visible share of the field
+        assert np.abs(expect[[0, -1]]).max() > 1e-6 * scale
+
+
+def test_translation_rows_match_dense_matrix_and_c_direct_sum():
+    """translation_apply_rows equals the rows of the dense matrix and of the C direct sum
+    (three independent evaluations of Eq. trans), for first, middle and last targets: on a dense
+    40-disk geometry, and entry by entry on a sparse one whose +-d images carry a large share of
+    every entry (so a wrong image phase or self-image mask cannot hide under near-pair terms)."""
+    from oracle import m2l
+    k, p, d = 60.0, 12, 1.0
+    nc = 2 * p + 1
+    al = np.exp(0.41j)
+    for M, gap, wdec in ((40, 0.005, 1.0), (6, 0.25, 0.3)):
+        dk = W.disks(M, 0.01, gap, 2.0, 40.0, seed=5, p=p)
+        rng = np.random.default_rng(6)
+        w = np.tile(wdec ** np.abs(np.arange(-p, p + 1)), M)
+        b = (rng.standard_normal(M * nc) + 1j * rng.standard_normal(M * nc)) * w
+        rows = [0, 1, M // 2, M - 2, M - 1]
+        got = I.translation_apply_rows(dk["xy"], k, p, d, al, b, rows)
+        dense = (I.translation_matrix(dk["xy"], k, p, d, al) @ b).reshape(M, nc)[rows]
+        csum = m2l.apply(dk["xy"], k, p, d, al, b).reshape(M, nc)[rows]
+        if M > 10:
+            assert np.linalg.norm(got - dense) <= 1e-13 * np.linalg.norm(dense)
+            assert np.linalg.norm(got - csum) <= 1e-13 * np.linalg.norm(dense)
+        else:
+            np.testing.assert_allclose(got, dense, rtol=1e-12, atol=0)
+            np.testing.assert_allclose(got, csum, rtol=1e-12, atol=0)

@@ -1,11 +1,13 @@
-"""Host-side helpers of the warm-start driver (paper_1412_7466_gb300/warmstart.py), on the CPU:
-the feature standardisation, the per-order output scale and the parameter packing that the
-library's gs_mlp_set_params reads.  No GPU, no kernels."""
+"""On the CPU: the oracle's warm-start normalisations (oracle/warmstart.py: the feature
+standardisation and the per-order output scale, against hand-worked values), which gs_ws_normalise
+is checked against on the GPU, and the driver's parameter packing that gs_mlp_set_params reads.
+No GPU, no kernels."""
 import math
 
 import numpy as np
 
-from paper_1412_7466_gb300.warmstart import N_IN, order_scale, pack, standardisation
+from oracle.warmstart import N_IN, order_scale, standardisation
+from paper_1412_7466_gb300.warmstart import pack
 
 
 def test_standardisation_sweep_columns_and_constants():
