@@ -226,6 +226,23 @@ int gs_bragg_batch(gs_ctx *ctx, int angle, int g, int *n_top, int *orders_top, g
 /* The autotuned source-image chunk length and blocks per SM of the batched translation. */
 int gs_batch_tuning(gs_ctx *ctx, int *chunk, int *blocks_per_sm);
 
+/* ---- many incidence angles of one geometry ---------------------------------------------------- */
+/* Solves the current geometry at every incidence angle of the context (R = the n_angles given to
+ * gs_set_incidence, 1 <= R <= 256) together, in the mixed form (opts->precision must be GS_C64; the
+ * other fields as for gs_solve): per angle, FP64 residuals b_r - L_r beta_r and refinement to the
+ * relative residual tol (Sec. 5, each angle its own quasi-periodic problem, Sec. 2 Eqs. quasi,
+ * rad1-rad2); the inner GMRES advances all open angles in lockstep.  Its translation applies the
+ * geometry's operator [T_-1 T_0 T_1] to all R angles' vectors at once on the tensor cores (bfloat16
+ * hi + lo parts of the operator and of the coefficients, three products accumulated in FP32,
+ * ~1e-5 relative; the two bfloat16 operators take 2 x 2n x 6n x 2 bytes, 30 GB at M = 1000,
+ * p = 12; GS_ERR_OOM if they do not fit); the low-rank part runs per angle (complex64 B_phys,
+ * double-float C x, FP64 A^+); each Arnoldi step of the R angles is one CUDA-graph replay.  Needs
+ * gs_factor (all angles).  Per-angle results are read with gs_get_beta, gs_stats,
+ * gs_stats_refinement and gs_bragg at that angle.  GS_ERR_NOT_CONVERGED if an angle misses tol
+ * within maxit inner iterations (its iterate stays readable); GS_ERR_TIMEOUT if a tensor-core wait
+ * gave up.  Synchronous. */
+int gs_solve_angles(gs_ctx *ctx, const gs_solve_opts *opts);
+
 /* ---- instrumentation (not part of the method) ------------------------------------------------ */
 /* Kernel launches issued by this context since gs_create (all calls). */
 int gs_launch_count(gs_ctx *ctx, unsigned long long *count);
@@ -259,6 +276,10 @@ int gs_field(gs_ctx *ctx, int angle, long npts, const double *xy_dev, gs_c128 *u
  * Relative accuracy ~3e-3 (bfloat16 operands) -- an inner operator, not a final one.  Needs
  * gs_factor; GS_ERR_TIMEOUT if a device wait gave up.  Synchronous. */
 int gs_translate_multi(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev, gs_c128 *out_dev);
+/* The operator of gs_solve_angles' inner solves: as gs_translate_multi, with the bfloat16 operator
+ * and coefficients each split into hi + lo parts (the three leading products accumulated in FP32,
+ * ~1e-5 relative; twice the operator memory of gs_translate_multi).  Synchronous. */
+int gs_translate_multi_hilo(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev, gs_c128 *out_dev);
 #define GS_TC_BF16 3             /* gs_profile_read tag of the tensor-core product in gs_translate_multi */
 
 /* ---- tensor-core product ---------------------------------------------------------------------

@@ -75,6 +75,7 @@ _SIGS = {
     "gs_apply": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "gs_rhs": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "gs_solve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gs_solve_opts), _vp]),
+    "gs_solve_angles": (ctypes.c_int, [_vp, ctypes.POINTER(gs_solve_opts)]),
     "gs_get_beta": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "gs_stats": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
     "gs_bragg": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _vp, _ip, _ip, _vp, _dp]),
@@ -96,6 +97,7 @@ _SIGS = {
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
     "gs_tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_long, ctypes.c_long, ctypes.c_long]),
     "gs_translate_multi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "gs_translate_multi_hilo": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "gs_field": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_long, _vp, _vp]),
     "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
     "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -327,6 +329,15 @@ class GratingSolver:
         ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
         return self._check(self.lib.gs_solve(self.ctx, angle, ctypes.byref(o), b0), "gs_solve", ok=ok)
 
+    def solve_angles(self, tol=1e-11, maxit=4000, restart=500, inner_tol=1e-6, max_sweeps=0,
+                     allow_unconverged=False):
+        """All incidence angles of the context in lockstep (mixed form, tensor-core translation);
+        per-angle results through stats/get_beta/bragg(angle)."""
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=GS_C64, inner_tol=inner_tol,
+                          max_sweeps=max_sweeps)
+        ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
+        return self._check(self.lib.gs_solve_angles(self.ctx, ctypes.byref(o)), "gs_solve_angles", ok=ok)
+
     def refinement_sweeps(self, angle=0):
         v = ctypes.c_int()
         self._check(self.lib.gs_stats_refinement(self.ctx, angle, ctypes.byref(v)), "gs_stats_refinement")
@@ -518,6 +529,18 @@ class GratingSolver:
         out = self.torch.empty_like(B)
         self._check(self.lib.gs_translate_multi(self.ctx, a.size, a.ctypes.data_as(_vp), _ptr(B), _ptr(out)),
                     "gs_translate_multi")
+        return out
+
+    def translate_multi_hilo(self, alphas, betas):
+        """As translate_multi with the operator and coefficients split into bfloat16 hi + lo parts
+        (~1e-5 relative): the inner operator of solve_angles."""
+        a = np.ascontiguousarray(np.asarray(alphas, dtype=np.complex128))
+        B = self._as_dev(betas)
+        if B.dim() != 2 or B.shape[0] != a.size:
+            raise ValueError("betas must be (R, n) with R = len(alphas)")
+        out = self.torch.empty_like(B)
+        self._check(self.lib.gs_translate_multi_hilo(self.ctx, a.size, a.ctypes.data_as(_vp), _ptr(B), _ptr(out)),
+                    "gs_translate_multi_hilo")
         return out
 
     def tc_gemm_bf16(self, A, B):

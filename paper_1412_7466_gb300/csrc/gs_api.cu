@@ -100,9 +100,16 @@ void free_geometry(gs_ctx *c) {
     dfree(c->xdf);
     dfree(c->iflag);
     dfree(c->htab);
+    gs_angles_destroy(c);
     if (c->tcA) cudaFree(c->tcA);
     c->tcA = nullptr;
+    if (c->tcA_lo) cudaFree(c->tcA_lo);
+    c->tcA_lo = nullptr;
     c->tcA_rows = c->tcA_cols = 0;
+    if (c->hl_scratch) cudaFree(c->hl_scratch);
+    c->hl_scratch = nullptr;
+    c->hl_scratch_bytes = 0;
+    c->hl_zeroed_R = -1;
     if (c->tc_scratch) cudaFree(c->tc_scratch);
     c->tc_scratch = nullptr;
     c->tc_scratch_bytes = 0;

@@ -52,6 +52,7 @@ struct AngleData {
 };
 
 struct gs_batch;   // batched solves over many geometries (gs_batch.cu)
+struct gs_angles;  // lockstep solves of one geometry at many angles (gs_angles.cu)
 struct gs_mlp;     // network of the learned warm start (gs_warm.cu)
 
 struct gs_ctx {
@@ -106,6 +107,10 @@ struct gs_ctx {
     void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
     long tcA_rows = 0, tcA_cols = 0;
     double tc_gamma = 1.0;                               // order rescaling of tcA (min(1, k2 r_min))
+    void *tcA_lo = nullptr;                              // bfloat16 remainder of the same operator (hi + lo split)
+    void *hl_scratch = nullptr;                          // scratch of the hi + lo multi-right-hand-side product
+    size_t hl_scratch_bytes = 0;
+    long hl_zeroed_R = -1;                               // R whose scratch padding is already zero
     void *tc_scratch = nullptr;                          // multi-right-hand-side scratch
     size_t tc_scratch_bytes = 0;
     long tc_zeroed_rp = -1, tc_zeroed_k = -1, tc_zeroed_R = -1;   // padding of the scratch already zero
@@ -129,6 +134,7 @@ struct gs_ctx {
     size_t prof_used = 0;               // events used since the last reset
 
     gs_batch *batch = nullptr;
+    gs_angles *angles = nullptr;
     gs_mlp *mlp = nullptr;
     double min_center_dist = 0.0;   // smallest inclusion centre distance (minimum image), set_inclusions
 
@@ -136,6 +142,7 @@ struct gs_ctx {
 };
 
 void gs_batch_destroy(gs_ctx *c);
+void gs_angles_destroy(gs_ctx *c);
 void gs_mlp_destroy(gs_ctx *c);
 
 #define GS_COUNT_LAUNCH(ctx) ((ctx)->nlaunch++)
@@ -183,12 +190,25 @@ size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
 // (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st
 int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st);
+// Tensor-core translation of R concatenated coefficient vectors (R angles of the current geometry,
+// image phases alpha_dev[r]) with the bfloat16 operator and the coefficients each split into hi + lo
+// parts (gs_tc.cu).  _prepare builds the two operators and the scratch for R (allocates: call it
+// before any stream capture); _translate only launches kernels (capturable) and sets *err_dev if a
+// device wait gave up.
+int gs_tc_hilo_prepare(gs_ctx *c, int R);
+int gs_tc_hilo_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
+                         cudaStream_t st);
 // tensor-core product C[M][N] = A[M][K] B[N][K]^T, bfloat16 in, FP32 out (gs_tc.cu)
 int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
                     cudaStream_t st);
 // low-rank, operator, GMRES, Bragg (gs_solve.cu)
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);
+// the mixed inner operator in two parts: copies of B_phys (complex64) and C (double-float) made once
+// per geometry and angle (allocates), then y = x - s t + s B_phys A^+ C x for a given t = T x
+// (launches only; uses the context's scratch vectors g, w, x, xdf)
+int gs_prepare_c64(gs_ctx *c, const AngleData &a);
+int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, cplx *y);
 int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b);
 // w = B_phys A^+ f: incoming coefficients of the empty grating's field about every centre
 int gs_incoming_impl(gs_ctx *c, const AngleData &a, cplx *w);

@@ -348,6 +348,71 @@ int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x) {
     return GS_OK;
 }
 
+// complex64 copy of B_phys and double-float copy of C for the mixed inner operator, once per
+// geometry and angle (allocates: not inside a stream capture)
+int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
+    const Layout &ly = c->lay;
+    const int n = c->n(), nB = ly.nB(), nC = ly.nC();
+    if (!a.B32) {
+        const long nb = (long)n * nB;
+        GS_CUDA(c, cudaMalloc((void **)&a.B32, sizeof(float2) * nb));
+        GS_COUNT_LAUNCH(c);
+        k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
+    }
+    if (!a.C2 && !a.C2_off) {
+        const long nc2 = (long)nC * n;
+        if (cudaMalloc((void **)&a.C2, sizeof(float4) * nc2) != cudaSuccess) {
+            cudaGetLastError();   // no room for the copy: the FP64 product stays
+            a.C2 = nullptr;
+            a.C2_off = true;
+        }
+    }
+    if (a.C2 && !a.C2_ready) {
+        const long nc2 = (long)nC * n;
+        GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
+        GS_COUNT_LAUNCH(c);
+        k_split_df<<<(int)((nc2 + 255) / 256), 256, 0, c->stream>>>(a.Cm, nc2, a.C2, GS_DF_LIMIT, c->iflag);
+        GS_CHECK_LAUNCH(c);
+        int big = 0;
+        GS_CUDA(c, cudaMemcpyAsync(&big, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (big) {   // entries beyond the double-float range: keep the FP64 product
+            cudaFree(a.C2);
+            a.C2 = nullptr;
+            a.C2_off = true;
+        } else {
+            a.C2_ready = true;
+        }
+    }
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// y = x - s .* t + s .* (B_phys A^+ C x) for the mixed inner operator, t = T x given: C x in
+// double-float arithmetic (or FP64 when the copy is off), A^+ in FP64, B_phys in complex64.  Only
+// launches kernels (after gs_prepare_c64).
+int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, cplx *y) {
+    const Layout &ly = c->lay;
+    const int n = c->n(), nB = ly.nB(), nC = ly.nC();
+    if (!a.B32 || (!a.C2 && !a.C2_off)) return gs_fail(c, GS_ERR_STATE, "gs_prepare_c64 has not run");
+    GS_COUNT_LAUNCH(c);
+    if (a.C2) {
+        k_split_df<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(x, n, c->xdf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows_df<<<nC, GEMV_DF_THREADS, 0, c->stream>>>(a.C2, nC, n, c->xdf, c->g);
+    } else {
+        k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
+    }
+    GS_COUNT_LAUNCH(c);
+    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+    GS_COUNT_LAUNCH(c);
+    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    GS_COUNT_LAUNCH(c);
+    k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, t, c->s, y);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
 // y = x - s .* T x + s .* (B_phys A^+ C x)
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision) {
     const Layout &ly = c->lay;
@@ -355,53 +420,8 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
     cplx *tx = c->v3;
     GS_TRY(gs_translate_impl(c, a, x, tx, precision));
     if (precision == GS_C64) {
-        if (!a.B32) {   // complex64 copy of B_phys, once per geometry and angle
-            const long nb = (long)n * nB;
-            GS_CUDA(c, cudaMalloc((void **)&a.B32, sizeof(float2) * nb));
-            GS_COUNT_LAUNCH(c);
-            k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
-        }
-        if (!a.C2 && !a.C2_off) {   // double-float copy of C, once per geometry and angle
-            const long nc2 = (long)nC * n;
-            if (cudaMalloc((void **)&a.C2, sizeof(float4) * nc2) != cudaSuccess) {
-                cudaGetLastError();   // no room for the copy: the FP64 product stays
-                a.C2 = nullptr;
-                a.C2_off = true;
-            }
-        }
-        if (a.C2 && !a.C2_ready) {
-            const long nc2 = (long)nC * n;
-            GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
-            GS_COUNT_LAUNCH(c);
-            k_split_df<<<(int)((nc2 + 255) / 256), 256, 0, c->stream>>>(a.Cm, nc2, a.C2, GS_DF_LIMIT, c->iflag);
-            GS_CHECK_LAUNCH(c);
-            int big = 0;
-            GS_CUDA(c, cudaMemcpyAsync(&big, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            GS_CUDA(c, cudaStreamSynchronize(c->stream));
-            if (big) {   // entries beyond the double-float range: keep the FP64 product
-                cudaFree(a.C2);
-                a.C2 = nullptr;
-                a.C2_off = true;
-            } else {
-                a.C2_ready = true;
-            }
-        }
-        GS_COUNT_LAUNCH(c);
-        if (a.C2) {
-            k_split_df<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(x, n, c->xdf, 0.0, nullptr);
-            GS_COUNT_LAUNCH(c);
-            k_gemv_rows_df<<<nC, GEMV_DF_THREADS, 0, c->stream>>>(a.C2, nC, n, c->xdf, c->g);
-        } else {
-            k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
-        }
-        GS_COUNT_LAUNCH(c);
-        k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
-        GS_COUNT_LAUNCH(c);
-        k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
-        GS_COUNT_LAUNCH(c);
-        k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, tx, c->s, y);
-        GS_CHECK_LAUNCH(c);
-        return GS_OK;
+        GS_TRY(gs_prepare_c64(c, a));
+        return gs_lowrank_c64(c, a, x, tx, y);
     }
     GS_COUNT_LAUNCH(c);
     k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);

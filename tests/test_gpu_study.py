@@ -26,3 +26,40 @@ def test_paper_experiment_analogues():
         assert abs(h - l) <= 0.5 * max(h, l), (M, h, l)
     its = [r["iters"] for r in out["example3"]]
     assert its[-1] > its[0], its
+
+
+@pytest.mark.parametrize("case", ["example1_homogeneous", "example1_layered", "example3_k2_20"])
+def test_study_configurations_against_oracle(case):
+    """Study configurations solved by the library against the oracle's dense LU solution: Example 1
+    with M = 100 disks (k_p = 30, p = 10) in the homogeneous k = (10, 10, 10) and layered
+    k = (10, 8, 10) backgrounds near the k1 = 10 Wood angle, and Example 3 at k2 = 20 with disks
+    crossing the walls; Bragg amplitudes to 1e-9 (norm-wise and element-wise)."""
+    import math
+
+    import workloads as W
+    from bragg import check as check_bragg
+    from oracle import solver as S
+    from paper_1412_7466_gb300 import GratingSolver
+    base = W.grating("small")
+    g = dict(base)
+    if case.startswith("example1"):
+        g["k"] = (10.0, 10.0, 10.0) if case.endswith("homogeneous") else (10.0, 8.0, 10.0)
+        theta = -math.acos(1.0 - 2.0 * math.pi / 10.0) + 0.1
+        dk = W.disks(100, 0.025, 0.0125, 3.0, 10.0, seed=100, p=10)
+    else:
+        g["k"] = (5.0, 20.0, 5.0)
+        theta = -math.pi / 5
+        dk = W.disks(100, 0.025, 0.0125, 1.6, 5.0, seed=3, p=10)
+    gs = GratingSolver(0)
+    gs.set_layers(g)
+    gs.set_incidence([theta])
+    gs.set_inclusions(dk)
+    gs.factor()
+    gs.solve(tol=1e-12, maxit=4000, restart=500)
+    got = gs.bragg()
+    gs.close()
+    prob = S.setup(g, theta, dk)
+    beta, _, _ = S.solve_dense(prob)
+    _, ref, _ = prob.recover(beta)
+    nw, ew = check_bragg(got, ref)
+    print(case, "Bragg error vs oracle", nw, ew)
