@@ -636,7 +636,7 @@ def main():
         gs.set_inclusions(cfg0["disks"])
         gs.factor()
         gs.solve(tol=tol, maxit=4000, restart=500)
-        xs, ys = np.meshgrid(np.linspace(-0.5, 0.5, 512), np.linspace(-0.44, 0.44, 256))
+        xs, ys = np.meshgrid(np.linspace(-0.5, 0.5, 512), np.linspace(-1.2, 1.2, 512))
         pts = torch.from_numpy(np.stack([xs.ravel(), ys.ravel()], axis=1)).to("cuda")
         gs.field(pts)
         a_, b_ = ev(), ev()
@@ -648,8 +648,11 @@ def main():
         fres = {"points": int(pts.shape[0]), "ms": fms, "unit": "points/s", "value": pts.shape[0] / (fms * 1e-3),
                 "nan_points": int(torch.isnan(uf.real).sum().item()),
                 "max_abs": float(torch.nan_to_num(uf.abs(), nan=0.0).max().item()),
-                "per_point": "2 interfaces x 3 copies x N = 256 nodes, a 181-term J-expansion, "
-                             "3000 inclusion images x (2p+1) orders (FP64)"}
+                "grid": "512 x 512 over one period, y in [-1.2, 1.2]: all three layers and the Rayleigh-Bloch "
+                        "regions beyond +-y0",
+                "per_point": "middle layer: 2 interfaces x 3 copies x N = 256 nodes, a 181-term J-expansion, "
+                             "3000 inclusion images x (2p+1) orders; top/bottom: 1 interface x 3 copies x 256 "
+                             "nodes and a 181-term J-expansion; beyond +-y0: 61 Rayleigh-Bloch orders (FP64)"}
 
     # the mixed-precision workload at its own size: M = 4000 disks of radius 0.004 on the same
     # grating and angle (100 000 unknowns); one warm-up geometry, one timed geometry
@@ -737,7 +740,7 @@ def main():
         gb.close()
 
     # many incidence angles of one geometry (the batched workload's angle list, every 256/R-th
-    # angle, with the k1 = 40 Wood angle): all R in lockstep (tensor-core hi + lo inner translation,
+    # angle, with the k1 = 40 Wood angle): all R in lockstep (three-part bf16 tensor-core inner translation,
     # per-angle low rank, FP64 refinement) against the same R angles solved one by one in the mixed
     # form on the same factored context
     angres = None
@@ -785,7 +788,7 @@ def main():
         diff = max(float(np.linalg.norm(np.r_[x["c"], x["d"]] - np.r_[y["c"], y["d"]]) /
                          np.linalg.norm(np.r_[y["c"], y["d"]])) for x, y in zip(brs_l, brs_s))
         ga.close()
-        angres = {"value": len(ths) / t_lock, "unit": "solves/s", "dtype": "bf16 hi+lo tensor-core translation + f64 refinement",
+        angres = {"value": len(ths) / t_lock, "unit": "solves/s", "dtype": "three-part bf16 tensor-core translation + f64 refinement",
                   "R": len(ths), "sequential_mixed_value": len(ths) / t_seq,
                   "thetas": ths, "wood_angle": th_w, "grating_factor_ms_all_angles": fac_ms,
                   "inner_iters": [x[0] for x in st_l], "refinement_sweeps": sw_l,

@@ -232,10 +232,10 @@ int gs_batch_tuning(gs_ctx *ctx, int *chunk, int *blocks_per_sm);
  * other fields as for gs_solve): per angle, FP64 residuals b_r - L_r beta_r and refinement to the
  * relative residual tol (Sec. 5, each angle its own quasi-periodic problem, Sec. 2 Eqs. quasi,
  * rad1-rad2); the inner GMRES advances all open angles in lockstep.  Its translation applies the
- * geometry's operator [T_-1 T_0 T_1] to all R angles' vectors at once on the tensor cores (bfloat16
- * hi + lo parts of the operator and of the coefficients, three products accumulated in FP32,
- * ~1e-5 relative; the two bfloat16 operators take 2 x 2n x 6n x 2 bytes, 30 GB at M = 1000,
- * p = 12; GS_ERR_OOM if they do not fit); the low-rank part runs per angle (complex64 B_phys,
+ * geometry's operator [T_-1 T_0 T_1] to all R angles' vectors at once on the tensor cores (three
+ * bfloat16 parts of the operator and of the coefficients, the six products of parts whose orders
+ * add up to at most 2 accumulated in FP32, single-precision accuracy; the three bfloat16 operator
+ * parts take 3 x 2n x 6n x 2 bytes, 45 GB at M = 1000, p = 12; GS_ERR_OOM if they do not fit); the low-rank part runs per angle (complex64 B_phys,
  * double-float C x, FP64 A^+); each Arnoldi step of the R angles is one CUDA-graph replay.  Needs
  * gs_factor (all angles).  Per-angle results are read with gs_get_beta, gs_stats,
  * gs_stats_refinement and gs_bragg at that angle.  GS_ERR_NOT_CONVERGED if an angle misses tol
@@ -258,13 +258,18 @@ int gs_profile_read(gs_ctx *ctx, int precision, int *launches, double *total_ms)
 #define GS_PROBE_F32X2 2
 int gs_probe_fma(gs_ctx *ctx, int precision, double *tflops);
 
-/* Total field in the layer holding the inclusions at npts points (the paper's field plots; Sec. 3
- * Eq. repre3 and Sec. 5 Eq. repre3_mod with the last solution at `angle`): interface potentials
- * (k2, +-d copies), the far-copy J-expansion and the inclusions' outgoing fields (+-d copies).
+/* Total field at npts points of one period, in all three layers (the paper's field plots; Sec. 3
+ * Eqs. repre1-repre3 and Sec. 5 Eq. repre3_mod with the last solution at `angle`): in the middle
+ * layer the interface potentials at k2 (+-d copies), the far-copy J-expansion and the inclusions'
+ * outgoing fields (+-d copies); in the top layer the incident wave, the potentials of Gamma1's
+ * densities at k1 and the J-expansion about the top layer's centre, and above Gamma_u (y >= y0) the
+ * incident wave plus the Rayleigh-Bloch expansion with the amplitudes c_n (Eq. rad1); in the bottom
+ * layer the potentials of Gamma2's densities at k3 and the J-expansion about the bottom layer's
+ * centre, and below Gamma_d (y <= -y0) the Rayleigh-Bloch expansion with d_n (Eq. rad2).
  * xy_dev holds (x, y) pairs, u_dev receives complex128 values (device arrays, caller-owned).
- * Points outside one period of the middle layer (|x| > d/2 or not strictly between the
- * interfaces) or inside an inclusion give NaN; accuracy is that of the trapezoid rule, i.e. a few
- * node spacings (d/N) away from the interfaces.  Needs gs_solve at this angle (GS_ERR_STATE). */
+ * Points outside one period (|x| > d/2), exactly on an interface, or inside an inclusion give NaN;
+ * accuracy is that of the trapezoid rule, i.e. a few node spacings (d/N) away from the interfaces.
+ * Needs gs_solve at this angle (GS_ERR_STATE). */
 int gs_field(gs_ctx *ctx, int angle, long npts, const double *xy_dev, gs_c128 *u_dev);
 
 /* alpha_r = T(theta_r) beta_r for R right-hand sides at once (R incidence angles of the current
@@ -276,10 +281,12 @@ int gs_field(gs_ctx *ctx, int angle, long npts, const double *xy_dev, gs_c128 *u
  * Relative accuracy ~3e-3 (bfloat16 operands) -- an inner operator, not a final one.  Needs
  * gs_factor; GS_ERR_TIMEOUT if a device wait gave up.  Synchronous. */
 int gs_translate_multi(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev, gs_c128 *out_dev);
-/* The operator of gs_solve_angles' inner solves: as gs_translate_multi, with the bfloat16 operator
- * and coefficients each split into hi + lo parts (the three leading products accumulated in FP32,
- * ~1e-5 relative; twice the operator memory of gs_translate_multi).  Synchronous. */
-int gs_translate_multi_hilo(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev, gs_c128 *out_dev);
+/* The operator of gs_solve_angles' inner solves: as gs_translate_multi, with the operator and the
+ * coefficients each split into three bfloat16 parts (~24 significant bits together; the six
+ * products of parts whose orders add up to at most 2 accumulated in FP32, single-precision accuracy;
+ * three times the operator memory of gs_translate_multi).  Synchronous. */
+int gs_translate_multi_split(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev,
+                             gs_c128 *out_dev);
 #define GS_TC_BF16 3             /* gs_profile_read tag of the tensor-core product in gs_translate_multi */
 
 /* ---- tensor-core product ---------------------------------------------------------------------

@@ -27,27 +27,31 @@ from scipy.special import h1vp, hankel1, jv, jvp
 from .layers import Curve, EmptyGrating
 
 
-def mie_coefficients(p: int, R: float, k2: float, kp: float) -> np.ndarray:
+def mie_coefficients(p: int, R: float, k2: float, kp, pol: str = "TM") -> np.ndarray:
     """s_n, n = -p..p, of a disk of radius R (inside kp, outside k2): incoming J_n(k2 r)e^{in th}
-    -> outgoing s_n H_n(k2 r) e^{in th}, from continuity of u and d_r u at r = R (Sec. 4.1)."""
+    -> outgoing s_n H_n(k2 r) e^{in th}, from continuity of u and of w d_r u at r = R (Sec. 4.1),
+    w = 1 for TM and w = 1/eps, proportional to 1/k^2, for TE (Sec. 2).  kp may be complex
+    (a lossy inclusion, Im kp > 0: complex permittivity, Sec. 7)."""
     n = np.arange(-p, p + 1)
     a, b = k2 * R, kp * R
-    num = kp * jvp(n, b) * jv(n, a) - k2 * jv(n, b) * jvp(n, a)
-    den = k2 * jv(n, b) * h1vp(n, a) - kp * jvp(n, b) * hankel1(n, a)
+    # weights of the radial derivative terms: k (TM) or k / k^2 = 1 / k (TE), from d_r J_n(k r) = k J_n'
+    wp, w2 = (kp, k2) if pol == "TM" else (1.0 / kp, 1.0 / k2)
+    num = wp * jvp(n, b) * jv(n, a) - w2 * jv(n, b) * jvp(n, a)
+    den = w2 * jv(n, b) * h1vp(n, a) - wp * jvp(n, b) * hankel1(n, a)
     return num / den
 
 
-def scattering_diagonal(disks: dict, k2: float) -> np.ndarray:
+def scattering_diagonal(disks: dict, k2: float, pol: str = "TM") -> np.ndarray:
     """(M, 2p+1) diagonal of the block-diagonal preconditioner S (Sec. 4.2, Remark on several
-    particle types: one diagonal per disk)."""
+    particle types: one diagonal per disk).  disks["kp"] may be complex (lossy inclusions)."""
     p = disks["p"]
     M = disks["xy"].shape[0]
     out = np.empty((M, 2 * p + 1), dtype=np.complex128)
     cache = {}
     for i in range(M):
-        key = (float(disks["radius"][i]), float(disks["kp"][i]))
+        key = (float(disks["radius"][i]), complex(disks["kp"][i]))
         if key not in cache:
-            cache[key] = mie_coefficients(p, key[0], k2, key[1])
+            cache[key] = mie_coefficients(p, key[0], k2, key[1], pol)
         out[i] = cache[key]
     return out
 

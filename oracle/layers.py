@@ -26,6 +26,15 @@ paper is silent or garbled:
   * Sigma^+ = min(1/sigma_j, 1/eps) taken literally (a clip, not a truncation), eps absolute.
   * Wood branch: k_{j,n} = +sqrt(k_j^2 - kappa_n^2), principal branch; |k_j^2-kappa_n^2| <
     1e-12 k_j^2 is set to 0.
+  * TE polarisation (Sec. 2 names it and Sec. 7 leaves it to future work; g["pol"] = "TE"): u is the
+    magnetic field and the flux condition on every interface carries the inverse permittivity,
+    [u] = 0, [(1/eps) d_n u] = 0, with eps_j proportional to k_j^2 (constant permeability, Sec. 2).
+    Relative to the middle layer, w_j = eps_j / eps_2 = (k_j / k_2)^2.  Each layer's potentials are
+    scaled by its w_j (u_j = w_j (D mu + S sigma) + J-expansions, Mueller's choice), which keeps the
+    system of the second kind: the value rows of an interface carry (w_a + w_b)/2 I + w_a D_a - w_b D_b
+    and w_a S_a - w_b S_b, the flux rows (1/w_j) d_n of each side, where the potentials' hypersingular
+    parts still cancel (T_a - T_b, N_a - N_b).  The J-expansion and Rayleigh-Bloch unknowns absorb
+    the scaling.  TM is w_j = 1.
 """
 from __future__ import annotations
 
@@ -73,16 +82,17 @@ class Curve:
     speed: np.ndarray    # |gamma'(x)|
     w: np.ndarray        # periodic trapezoid weights h*speed
     h: float
+    curv: np.ndarray = None   # signed curvature h'' / (1 + h'^2)^{3/2} (with respect to the upward normal)
 
 
 def discretise_curve(iface: dict, d: float, N: int) -> Curve:
     hstep = d / N
     x = -0.5 * d + (np.arange(N) + 0.5) * hstep
-    y, yp, _ = iface_eval(iface, d, x)
+    y, yp, ypp = iface_eval(iface, d, x)
     speed = np.sqrt(1.0 + yp * yp)
     nrm = np.stack([-yp / speed, 1.0 / speed], axis=1)
     pos = np.stack([x, y], axis=1)
-    return Curve(x=x, pos=pos, nrm=nrm, speed=speed, w=hstep * speed, h=hstep)
+    return Curve(x=x, pos=pos, nrm=nrm, speed=speed, w=hstep * speed, h=hstep, curv=ypp / speed**3)
 
 
 def gauss_legendre(n: int, lo: float, hi: float) -> np.ndarray:
@@ -116,20 +126,25 @@ def kernels(tpos, tnrm, spos, snrm, k):
     return {"S": S, "D": D, "N": N, "T": T}
 
 
-def diag_limits(ka, kb):
-    """Limits at coincidence of the kernel differences (ka - kb), per unit arc length.
+def diag_limits(ka, kb, wa=1.0, wb=1.0):
+    """Limits at coincidence of the kernel differences, per unit arc length: wa S_ka - wb S_kb and
+    wa D_ka - wb D_kb for S and D, plain differences (ka - kb) for N and T.
 
     Returns (K1, Krest) for each of S, D, N, T where K = K1 log r + Krest + o(1) as y -> x on a
     smooth curve.  Small-argument forms: H0(z) = 1 + (2i/pi)(log(z/2) + gamma) + ..., and
     H1(z) = -2i/(pi z) + z/2 + (iz/pi) log(z/2) - (iz/(2 pi))(1 - 2 gamma) + ...; the curvature
-    terms of D, N and the hypersingular part of T do not depend on k and cancel in differences.
+    terms of N and the hypersingular part of T do not depend on k and cancel in the differences.
+    D's limit is (wa - wb) kappa / (4 pi), kappa the curvature (the Laplace double layer's
+    (R.n_y)/(2 pi r^2) tends to kappa/(4 pi)): it is returned per unit curvature.
     """
     ka = complex(ka)
     kb = complex(kb)
     la = np.log(ka / 2.0)
     lb = np.log(kb / 2.0)
-    S = (0.0, -(la - lb) / (2.0 * math.pi))
-    D = (0.0, 0.0)
+    def s_rest(k_log):
+        return 0.25j - (k_log + EULER) / (2.0 * math.pi)
+    S = (-(wa - wb) / (2.0 * math.pi), wa * s_rest(la) - wb * s_rest(lb))
+    D = (0.0, (wa - wb) / (4.0 * math.pi))
     N = (0.0, 0.0)
     dk2 = ka * ka - kb * kb
     T = (-dk2 / (4.0 * math.pi),
@@ -162,9 +177,11 @@ def kress_weights(N: int) -> np.ndarray:
     return R
 
 
-def self_difference_operators(c: Curve, d: float, alpha: complex, ka, kb):
-    """Nystrom matrices of S^{ka}-S^{kb}, D..., N..., T... on one interface, summed over the near
-    copies l = -1, 0, 1 with Bloch phases alpha^l (Sec. 3, A11 and Eq. qGreen2 with P = 1).
+def self_difference_operators(c: Curve, d: float, alpha: complex, ka, kb, wa=1.0, wb=1.0):
+    """Nystrom matrices of wa S^{ka} - wb S^{kb}, wa D^{ka} - wb D^{kb}, N^{ka} - N^{kb},
+    T^{ka} - T^{kb} on one interface, summed over the near copies l = -1, 0, 1 with Bloch phases
+    alpha^l (Sec. 3, A11 and Eq. qGreen2 with P = 1; the weights are the TE permittivity ratios,
+    1 for TM).
 
     A_ij = h F_ij + (W_ij - h log(4 sin^2(pi (i-j)/N))) L_ij   (j != i)
     A_ii = h F_ii + W_ii L_ii + h speed_i [ (K1_ii/2) log(speed_i^2 d^2/(4 pi^2)) + Krest_ii ]
@@ -182,7 +199,8 @@ def self_difference_operators(c: Curve, d: float, alpha: complex, ka, kb):
             Kb = kernels(c.pos, c.nrm, spos, c.nrm, kb)
         ph = alpha ** l
         for key in "SDNT":
-            diff = Ka[key] - Kb[key]
+            wgt_a, wgt_b = (wa, wb) if key in "SD" else (1.0, 1.0)
+            diff = wgt_a * Ka[key] - wgt_b * Kb[key]
             if l == 0:
                 np.fill_diagonal(diff, 0.0)
             F[key] += ph * diff
@@ -203,13 +221,13 @@ def self_difference_operators(c: Curve, d: float, alpha: complex, ka, kb):
     K1 = {}
     for key in "SDNT":
         K1[key] = np.zeros((N, N), dtype=np.complex128)
-    for k, sgn in ((ka, 1.0), (kb, -1.0)):
+    for k, sgn, wsd in ((ka, 1.0, wa), (kb, -1.0, wb)):
         kr = k * r
         J0 = jv(0, kr)
         J1 = jv(1, kr)
         cc = -1.0 / (2.0 * math.pi)
-        K1["S"] += sgn * cc * J0
-        K1["D"] += sgn * cc * k * J1 * Rny / r
+        K1["S"] += sgn * wsd * cc * J0
+        K1["D"] += sgn * wsd * cc * k * J1 * Rny / r
         K1["N"] += sgn * (-cc) * k * J1 * Rnx / r
         K1["T"] += sgn * cc * k * (k * J0 * Rnx * Rny / r**2 - 2.0 * J1 * Rnx * Rny / r**3
                                    + J1 * nn / r)
@@ -220,14 +238,15 @@ def self_difference_operators(c: Curve, d: float, alpha: complex, ka, kb):
     with np.errstate(divide="ignore"):
         logt = np.log(4.0 * np.sin(math.pi * idx / N) ** 2)
     np.fill_diagonal(logt, 0.0)
-    lim = diag_limits(ka, kb)
+    lim = diag_limits(ka, kb, wa, wb)
     for key in "SDNT":
         L = psi * 0.5 * K1[key] * phase * c.speed[None, :]
         np.fill_diagonal(L, 0.5 * lim[key][0] * c.speed)
         A = h * F[key] * c.speed[None, :] + (W - h * logt) * L
+        rest = lim[key][1] * (c.curv if key == "D" else 1.0)
         diag = (h * np.diag(F[key]) * c.speed + W[0, 0] * 0.5 * lim[key][0] * c.speed
                 + h * c.speed * (0.5 * lim[key][0] * np.log(c.speed**2 * d * d / (4.0 * math.pi**2))
-                                 + lim[key][1]))
+                                 + rest))
         np.fill_diagonal(A, diag)
         out[key] = A
     return out
@@ -327,6 +346,18 @@ def _offsets(sizes: dict, order) -> dict:
     return out
 
 
+def layer_weights(g: dict):
+    """(w1, w3): the permittivities of the top and bottom layers relative to the middle layer,
+    (k_j / k_2)^2, for TE polarisation; (1, 1) for TM (g["pol"], TM when absent)."""
+    pol = g.get("pol", "TM")
+    if pol == "TM":
+        return 1.0, 1.0
+    if pol != "TE":
+        raise ValueError(f"unknown polarisation {pol!r}")
+    k1, k2, k3 = g["k"]
+    return (k1 / k2) ** 2, (k3 / k2) ** 2
+
+
 def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     """Assemble A and f for the grating g at incidence theta (Sec. 3, Eqs. bound1-bound3, matA)."""
     d = g["d"]
@@ -359,6 +390,7 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     eg = EmptyGrating(g=g, theta=theta, d=d, k=(k1, k2, k3), alpha=alpha, kappa=kap, k1n=k1n,
                       k3n=k3n, c1=c1, c2=c2, centers=(x1, x2, x3), wall_y=(wall1, wall2, wall3),
                       bound_x=bx)
+    w1, w3 = layer_weights(g)
     csz = dict(mu1=N, sigma1=N, mu2=N, sigma2=N, a2=2 * Q2 + 1, a1=2 * Q1 + 1, a3=2 * Q3 + 1,
                c=2 * K + 1, d=2 * K + 1)
     rsz = dict(g1v=N, g1n=N, g2v=N, g2n=N, w2v=nw2, w2n=nw2, w1v=nw1, w1n=nw1, w3v=nw3, w3n=nw3,
@@ -370,17 +402,20 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     A = np.zeros((nrow, ncol), dtype=np.complex128)
     C, R = eg.cols, eg.rows
 
-    def put(rv, rn, cm, cs, P):
-        """value rows get D (mu) and S (sigma); derivative rows get T (mu) and N (sigma)."""
-        A[R[rv], C[cm]] += P["D"]
-        A[R[rv], C[cs]] += P["S"]
-        A[R[rn], C[cm]] += P["T"]
-        A[R[rn], C[cs]] += P["N"]
+    def put(rv, rn, cm, cs, P, wgt=1.0):
+        """value rows get D (mu) and S (sigma); derivative rows get T (mu) and N (sigma); all scaled
+        by the layer's TE weight wgt."""
+        A[R[rv], C[cm]] += wgt * P["D"]
+        A[R[rv], C[cs]] += wgt * P["S"]
+        A[R[rn], C[cm]] += wgt * P["T"]
+        A[R[rn], C[cs]] += wgt * P["N"]
 
     # --- Gamma1 rows: u1 - u2 = -u_inc, d_n u1 - d_n u2 = -d_n u_inc (Eq. bound1) -------------
-    s1 = self_difference_operators(c1, d, alpha, k1, k2)
+    # u1 = w1 (D mu1 + S sigma1) + J(a1) + u_inc above, u2 = D mu1 + S sigma1 + ... below; the flux
+    # rows take (1/w1) d_n u1 - d_n u2
+    s1 = self_difference_operators(c1, d, alpha, k1, k2, w1, 1.0)
     I = np.eye(N)
-    A[R["g1v"], C["mu1"]] = I + s1["D"]
+    A[R["g1v"], C["mu1"]] = 0.5 * (w1 + 1.0) * I + s1["D"]
     A[R["g1v"], C["sigma1"]] = s1["S"]
     A[R["g1n"], C["mu1"]] = s1["T"]
     A[R["g1n"], C["sigma1"]] = -I + s1["N"]
@@ -391,11 +426,11 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     A[R["g1n"], C["a2"]] = -dn
     v, dn = jexp_columns(c1.pos, c1.nrm, x1, k1, Q1)
     A[R["g1v"], C["a1"]] = v
-    A[R["g1n"], C["a1"]] = dn
+    A[R["g1n"], C["a1"]] = dn / w1
 
     # --- Gamma2 rows: u2 - u3 = 0, d_n u2 - d_n u3 = 0 ------------------------------------------
-    s2 = self_difference_operators(c2, d, alpha, k2, k3)
-    A[R["g2v"], C["mu2"]] = I + s2["D"]
+    s2 = self_difference_operators(c2, d, alpha, k2, k3, 1.0, w3)
+    A[R["g2v"], C["mu2"]] = 0.5 * (1.0 + w3) * I + s2["D"]
     A[R["g2v"], C["sigma2"]] = s2["S"]
     A[R["g2n"], C["mu2"]] = s2["T"]
     A[R["g2n"], C["sigma2"]] = -I + s2["N"]
@@ -406,27 +441,27 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     A[R["g2n"], C["a2"]] = dn
     v, dn = jexp_columns(c2.pos, c2.nrm, x3, k3, Q3)
     A[R["g2v"], C["a3"]] = -v
-    A[R["g2n"], C["a3"]] = -dn
+    A[R["g2n"], C["a3"]] = -dn / w3
 
     # --- wall rows: alpha u(L) - u(R), alpha d_x u(L) - d_x u(R) (Eq. bound2, cancelled form) ----
     ex = np.array([1.0, 0.0])
 
-    def wall(rv, rn, ys, curves, kk, center, ca, Qc):
+    def wall(rv, rn, ys, curves, kk, center, ca, Qc, wgt):
         L = np.stack([np.full_like(ys, -0.5 * d), ys], axis=1)
         Rt = np.stack([np.full_like(ys, 0.5 * d), ys], axis=1)
         tn = np.tile(ex, (ys.size, 1))
         for cv, cm, cs in curves:
             P = near_potentials(L, tn, cv, d, alpha, kk, shifts=(1, -2),
                                 phases=(alpha ** 2, -alpha ** -1))
-            put(rv, rn, cm, cs, P)
+            put(rv, rn, cm, cs, P, wgt)
         vL, dL = jexp_columns(L, tn, center, kk, Qc)
         vR, dR = jexp_columns(Rt, tn, center, kk, Qc)
         A[R[rv], C[ca]] = alpha * vL - vR
         A[R[rn], C[ca]] = alpha * dL - dR
 
-    wall("w2v", "w2n", wall2, [(c1, "mu1", "sigma1"), (c2, "mu2", "sigma2")], k2, x2, "a2", Q2)
-    wall("w1v", "w1n", wall1, [(c1, "mu1", "sigma1")], k1, x1, "a1", Q1)
-    wall("w3v", "w3n", wall3, [(c2, "mu2", "sigma2")], k3, x3, "a3", Q3)
+    wall("w2v", "w2n", wall2, [(c1, "mu1", "sigma1"), (c2, "mu2", "sigma2")], k2, x2, "a2", Q2, 1.0)
+    wall("w1v", "w1n", wall1, [(c1, "mu1", "sigma1")], k1, x1, "a1", Q1, w1)
+    wall("w3v", "w3n", wall3, [(c2, "mu2", "sigma2")], k3, x3, "a3", Q3, w3)
 
     # --- Gamma_u / Gamma_d rows (Eq. bound3) ------------------------------------------------------
     ey = np.array([0.0, 1.0])
@@ -434,7 +469,7 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     U = np.stack([bx, np.full_like(bx, y0)], axis=1)
     Dd = np.stack([bx, np.full_like(bx, -y0)], axis=1)
     P = near_potentials(U, tn, c1, d, alpha, k1)
-    put("uv", "un", "mu1", "sigma1", P)
+    put("uv", "un", "mu1", "sigma1", P, w1)
     v, dn = jexp_columns(U, tn, x1, k1, Q1)
     A[R["uv"], C["a1"]] = v
     A[R["un"], C["a1"]] = dn
@@ -442,7 +477,7 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     A[R["uv"], C["c"]] = -E
     A[R["un"], C["c"]] = -1j * E * k1n[None, :]
     P = near_potentials(Dd, tn, c2, d, alpha, k3)
-    put("dv", "dn", "mu2", "sigma2", P)
+    put("dv", "dn", "mu2", "sigma2", P, w3)
     v, dn = jexp_columns(Dd, tn, x3, k3, Q3)
     A[R["dv"], C["a3"]] = v
     A[R["dn"], C["a3"]] = dn
@@ -455,7 +490,7 @@ def build_empty_grating(g: dict, theta: float) -> EmptyGrating:
     uinc = np.exp(1j * (c1.pos @ kv))
     dninc = 1j * (c1.nrm @ kv) * uinc
     f[R["g1v"]] = -uinc
-    f[R["g1n"]] = -dninc
+    f[R["g1n"]] = -dninc / w1
     eg.A = A
     eg.f = f
     return eg
@@ -523,9 +558,16 @@ def bragg(eg: EmptyGrating, avec: np.ndarray):
             "k1n": eg.k1n[pt].real, "k3n": eg.k3n[pb].real}
 
 
-def flux_error(eg: EmptyGrating, avec: np.ndarray) -> float:
-    """|sum k_{1,n}|c_n|^2 + sum k_{3,n}|d_n|^2 - k1|sin theta|| / (k1 |sin theta|)."""
+def flux_balance(eg: EmptyGrating, avec: np.ndarray):
+    """(outgoing, incident) vertical energy fluxes: sum k_{1,n}|c_n|^2 / w1 + sum k_{3,n}|d_n|^2 / w3
+    over the propagating orders and k1 |sin theta| / w1 (TE weights w_j; 1 for TM)."""
     b = bragg(eg, avec)
-    out = np.sum(b["k1n"] * np.abs(b["c"]) ** 2) + np.sum(b["k3n"] * np.abs(b["d"]) ** 2)
-    inc = eg.k[0] * abs(math.sin(eg.theta))
+    w1, w3 = layer_weights(eg.g)
+    out = np.sum(b["k1n"] * np.abs(b["c"]) ** 2) / w1 + np.sum(b["k3n"] * np.abs(b["d"]) ** 2) / w3
+    return float(out), eg.k[0] * abs(math.sin(eg.theta)) / w1
+
+
+def flux_error(eg: EmptyGrating, avec: np.ndarray) -> float:
+    """|outgoing - incident| / incident of flux_balance (Sec. 6; zero for lossless media)."""
+    out, inc = flux_balance(eg, avec)
     return float(abs(out - inc) / inc)

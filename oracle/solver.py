@@ -67,7 +67,7 @@ def setup(g: dict, theta: float, disks: dict, eps=None, lapack_driver="gesdd") -
     t1 = time.perf_counter()
     pinv = lay.factor(eg, eps=eps, lapack_driver=lapack_driver)
     t2 = time.perf_counter()
-    s = inc.scattering_diagonal(disks, eg.k[1])
+    s = inc.scattering_diagonal(disks, eg.k[1], g.get("pol", "TM"))
     B = inc.coupling_B(eg, disks)
     C = inc.coupling_C(eg, disks)
     t3 = time.perf_counter()

@@ -97,7 +97,7 @@ _SIGS = {
                                             ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp]),
     "gs_tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_long, ctypes.c_long, ctypes.c_long]),
     "gs_translate_multi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
-    "gs_translate_multi_hilo": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "gs_translate_multi_split": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "gs_field": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_long, _vp, _vp]),
     "gs_mlp_param_count": (ctypes.c_int, [ctypes.c_int]),
     "gs_mlp_set_params": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -531,16 +531,16 @@ class GratingSolver:
                     "gs_translate_multi")
         return out
 
-    def translate_multi_hilo(self, alphas, betas):
-        """As translate_multi with the operator and coefficients split into bfloat16 hi + lo parts
-        (~1e-5 relative): the inner operator of solve_angles."""
+    def translate_multi_split(self, alphas, betas):
+        """As translate_multi with the operator and the coefficients each split into three bfloat16
+        parts (single-precision accuracy): the inner operator of solve_angles."""
         a = np.ascontiguousarray(np.asarray(alphas, dtype=np.complex128))
         B = self._as_dev(betas)
         if B.dim() != 2 or B.shape[0] != a.size:
             raise ValueError("betas must be (R, n) with R = len(alphas)")
         out = self.torch.empty_like(B)
-        self._check(self.lib.gs_translate_multi_hilo(self.ctx, a.size, a.ctypes.data_as(_vp), _ptr(B), _ptr(out)),
-                    "gs_translate_multi_hilo")
+        self._check(self.lib.gs_translate_multi_split(self.ctx, a.size, a.ctypes.data_as(_vp), _ptr(B), _ptr(out)),
+                    "gs_translate_multi_split")
         return out
 
     def tc_gemm_bf16(self, A, B):

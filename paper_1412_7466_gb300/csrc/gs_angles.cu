@@ -3,9 +3,10 @@
 //
 //  * Translation: the R angles' coefficient vectors go through one tensor-core product per operator
 //    part (tcgen05, gs_tc.cu): the geometry's operator [T_-1 T_0 T_1] and the coefficients are each
-//    split into bfloat16 hi + lo parts and the three leading products (hi hi, hi lo, lo hi) are
-//    accumulated in FP32, ~1e-5 relative -- the accuracy of the complex64 translation -- for all R
-//    angles at the cost of streaming the operator twice.
+//    split into three bfloat16 parts (~24 significant bits together, the precision of FP32) and the
+//    six products of parts whose orders add up to at most 2 are accumulated in FP32 -- the accuracy
+//    of the complex64 translation -- for all R angles at the cost of streaming the operator three
+//    times.
 //  * Low rank: per angle, since the grating factorisation, B_phys and C depend on the angle: C x in
 //    double-float arithmetic, U^* and V Sigma in FP64, complex64 B_phys, fused combination
 //    (gs_lowrank_c64).
@@ -37,6 +38,7 @@ struct gs_angles {
     double *hbuf = nullptr;            // pinned host: R residuals + the error flag
     cudaGraphExec_t step = nullptr;
     unsigned long long step_kernels = 0;   // kernels in one replay of the step graph
+    const void *key[4] = {nullptr, nullptr, nullptr, nullptr};   // operator and scratch buffers the graph uses
 };
 
 namespace {
@@ -145,7 +147,7 @@ int angles_setup(gs_ctx *c, int restart) {
 
 // y_r = x_r - s T(a_r) x_r + s B_phys,r A_r^+ C_r x_r for every angle r (the mixed inner operator)
 int angles_apply_c64(gs_ctx *c, gs_angles *A, const cplx *x, cplx *y) {
-    GS_TRY(gs_tc_hilo_translate(c, A->R, A->alpha, x, A->T, A->err, c->stream));
+    GS_TRY(gs_tc_split_translate(c, A->R, A->alpha, x, A->T, A->err, c->stream));
     for (int r = 0; r < A->R; ++r)
         GS_TRY(gs_lowrank_c64(c, c->ang[r], x + (size_t)r * A->n, A->T + (size_t)r * A->n, y + (size_t)r * A->n));
     return GS_OK;
@@ -194,7 +196,13 @@ int angles_step(gs_ctx *c, gs_angles *A) {
 }
 
 int angles_step_graph(gs_ctx *c, gs_angles *A) {
-    if (A->step) return GS_OK;
+    const void *key[4] = {c->tcA, c->tcA_sp[0], c->tcA_sp[1], c->sp_scratch};
+    if (A->step && std::equal(key, key + 4, A->key)) return GS_OK;
+    if (A->step) {   // the tensor-core buffers were rebuilt since the capture
+        cudaGraphExecDestroy(A->step);
+        A->step = nullptr;
+    }
+    std::copy(key, key + 4, A->key);
     cudaGraph_t gph;
     const unsigned long long l0 = c->nlaunch;
     GS_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -337,7 +345,7 @@ extern "C" int gs_solve_angles(gs_ctx *c, const gs_solve_opts *o) {
     const long n = A->n, N = A->N;
     // everything that allocates, before the step graph is captured
     for (int r = 0; r < R; ++r) GS_TRY(gs_prepare_c64(c, c->ang[r]));
-    GS_TRY(gs_tc_hilo_prepare(c, R));
+    GS_TRY(gs_tc_split_prepare(c, R));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     OnAnglesStream on(c);
     cudaStream_t st = c->stream;

@@ -103,13 +103,15 @@ void free_geometry(gs_ctx *c) {
     gs_angles_destroy(c);
     if (c->tcA) cudaFree(c->tcA);
     c->tcA = nullptr;
-    if (c->tcA_lo) cudaFree(c->tcA_lo);
-    c->tcA_lo = nullptr;
+    for (int q = 0; q < 2; ++q) {
+        if (c->tcA_sp[q]) cudaFree(c->tcA_sp[q]);
+        c->tcA_sp[q] = nullptr;
+    }
     c->tcA_rows = c->tcA_cols = 0;
-    if (c->hl_scratch) cudaFree(c->hl_scratch);
-    c->hl_scratch = nullptr;
-    c->hl_scratch_bytes = 0;
-    c->hl_zeroed_R = -1;
+    if (c->sp_scratch) cudaFree(c->sp_scratch);
+    c->sp_scratch = nullptr;
+    c->sp_scratch_bytes = 0;
+    c->sp_zeroed_R = -1;
     if (c->tc_scratch) cudaFree(c->tc_scratch);
     c->tc_scratch = nullptr;
     c->tc_scratch_bytes = 0;

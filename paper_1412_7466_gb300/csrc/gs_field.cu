@@ -1,13 +1,18 @@
-// Total field in the layer that holds the inclusions, at given points (the paper's field plots,
-// Sec. 6 Figs.; representation of Sec. 3 Eq. repre3 and Sec. 5 Eq. repre3_mod):
-//   u(x) = sum over both interfaces and their +-d copies of alpha^l [S sigma + D mu](x)   (k2)
-//        + sum_q a2_q J_q(k2 |x - c_2|) e^{i q theta}                                   (far copies)
-//        + sum_j sum_l alpha^l sum_n beta^j_n H_n(k2 |x - c_j - l d|) e^{i n theta}       (inclusions)
-// with the layer unknowns a = A^+ (f - C beta) of the converged solution.  One thread per point,
-// FP64 throughout: interface sums by the plain trapezoid rule (accurate a few node spacings away
-// from the interfaces), J_q by Miller's backward recurrence accumulated on the fly (no per-order
-// storage), H_n by upward recurrence from H_0, H_1.  Points outside one period of the middle layer
-// (|x| > d/2, or not strictly between the interfaces) and points inside an inclusion give NaN.
+// Total field at given points of one period, in all three layers (the paper's field plots, Sec. 6
+// Figs.), from the layer unknowns a = A^+ (f - C beta) of the converged solution:
+//   middle (Sec. 3 Eq. repre3, Sec. 5 Eq. repre3_mod):
+//     u = sum over both interfaces and their +-d copies of alpha^l [S sigma + D mu](x)      (k2)
+//       + sum_q a2_q J_q(k2 |x - x2|) e^{i q theta}                                        (far copies)
+//       + sum_j sum_l alpha^l sum_n beta^j_n H_n(k2 |x - c_j - l d|) e^{i n theta}          (inclusions)
+//   top, below Gamma_u (Eq. repre1): u_inc + the potentials of Gamma1's densities at k1 (near
+//     copies) + sum_q a1_q J_q(k1 |x - x1|) e^{i q theta};  above (Eq. rad1):
+//     u_inc + sum_n c_n e^{i (kappa_n x + k_{1,n} (y - y0))}
+//   bottom, above Gamma_d (Eq. repre2): the potentials of Gamma2's densities at k3 +
+//     sum_q a3_q J_q(k3 |x - x3|) e^{i q theta};  below (Eq. rad2): sum_n d_n e^{i (kappa_n x - k_{3,n} (y + y0))}
+// One thread per point, FP64 throughout: interface sums by the plain trapezoid rule (accurate a few
+// node spacings away from the interfaces), J_q by Miller's backward recurrence accumulated on the
+// fly (no per-order storage), H_n by upward recurrence from H_0, H_1.  Points outside one period
+// (|x| > d/2), on an interface, or inside an inclusion give NaN.
 #include <cmath>
 
 #include "gs_internal.h"
@@ -19,10 +24,12 @@ struct FieldArgs {
     int N;
     const double *four;           // [h1_cos, h1_sin, h2_cos, h2_sin], nfa each
     int nf, nfa;
-    double h1_0, h2_0, d, k2, ycen;
+    double h1_0, h2_0, d, k1, k2, k3, y0, ycen, ycen1, ycen3, kx, ky;   // kx, ky: incident wave vector
     cplx alpha;
     const cplx *a;                // layer unknowns (cols)
-    int col_mu1, col_sig1, col_mu2, col_sig2, col_a2, Q2;
+    int col_mu1, col_sig1, col_mu2, col_sig2, col_a2, Q2, col_a1, Q1, col_a3, Q3, col_c, col_d, K;
+    const double *kappa;          // 2K+1 Bloch wavenumbers kappa_n
+    const cplx *k1n, *k3n;        // 2K+1 vertical wavenumbers of the top and bottom layers
     const double *xy, *radius;    // inclusions
     const cplx *beta;
     int M, p;
@@ -76,40 +83,84 @@ __device__ cplx jexp_sum(const cplx *a, int Q, double z, double th) {
     return cscale(acc, 1.0 / norm);
 }
 
+// sum over the +-d copies of alpha^l [S sigma + D mu](x, y) for interface q's densities at wavenumber k
+__device__ cplx layer_potentials(const FieldArgs &A, int q, double k, double x, double y) {
+    const double *cv = q == 0 ? A.c1 : A.c2;
+    const double *px = cv + A.N, *py = cv + 2 * A.N, *nx = cv + 3 * A.N, *ny = cv + 4 * A.N, *w = cv + 6 * A.N;
+    const cplx *mu = A.a + (q == 0 ? A.col_mu1 : A.col_mu2), *sg = A.a + (q == 0 ? A.col_sig1 : A.col_sig2);
+    const cplx ai = cconj(A.alpha);
+    cplx acc = C(0.0, 0.0);
+    for (int l = -1; l <= 1; ++l) {
+        const cplx ph = l == 0 ? C(1.0, 0.0) : (l == 1 ? A.alpha : ai);
+        cplx s = C(0.0, 0.0);
+        for (int j = 0; j < A.N; ++j) {
+            const double Rx = x - (px[j] + l * A.d), Ry = y - py[j];
+            const double r = hypot(Rx, Ry);
+            cplx H0, H1;
+            hankel01(k * r, H0, H1);
+            // S = (i/4) H0, D = (i k/4) H1 (R . n_y) / r
+            const cplx Sk = cmuli(cscale(H0, 0.25 * w[j]));
+            const cplx Dk = cmuli(cscale(H1, 0.25 * k * (Rx * nx[j] + Ry * ny[j]) / r * w[j]));
+            s = cadd(s, cadd(cmul(Sk, sg[j]), cmul(Dk, mu[j])));
+        }
+        acc = cadd(acc, cmul(ph, s));
+    }
+    return acc;
+}
+
+// sum_n amp_n e^{i (kappa_n x + kv_n dy)} over the 2K+1 Rayleigh-Bloch orders (kv complex: the
+// evanescent orders decay away from the layer)
+__device__ cplx rayleigh_bloch(const FieldArgs &A, const cplx *amp, const cplx *kv, double x, double dy) {
+    cplx acc = C(0.0, 0.0);
+    for (int n = 0; n < 2 * A.K + 1; ++n) {
+        const double ph = A.kappa[n] * x + kv[n].x * dy, damp = exp(-kv[n].y * dy);
+        double s, c;
+        sincos(ph, &s, &c);
+        acc = cadd(acc, cmul(amp[n], C(damp * c, damp * s)));
+    }
+    return acc;
+}
+
 __global__ void k_field(FieldArgs A, long npts, const double *__restrict__ pts, cplx *__restrict__ u) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts) return;
     const double x = pts[2 * t], y = pts[2 * t + 1];
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (!(fabs(x) <= 0.5 * A.d)) {
+        u[t] = C(nan, nan);
+        return;
+    }
     const double top = iface_h(A.h1_0, A.four, A.four + A.nfa, A.nf, A.d, x);
     const double bot = iface_h(A.h2_0, A.four + 2 * A.nfa, A.four + 3 * A.nfa, A.nf, A.d, x);
-    if (!(fabs(x) <= 0.5 * A.d) || !(y > bot && y < top)) {
+    double si, co;
+    sincos(A.kx * x + A.ky * y, &si, &co);
+    const cplx uinc = C(co, si);
+    if (y >= A.y0) {
+        u[t] = cadd(uinc, rayleigh_bloch(A, A.a + A.col_c, A.k1n, x, y - A.y0));
+        return;
+    }
+    if (y <= -A.y0) {
+        u[t] = rayleigh_bloch(A, A.a + A.col_d, A.k3n, x, -(y + A.y0));
+        return;
+    }
+    if (y > top) {
+        const double Ry = y - A.ycen1;
+        cplx acc = cadd(uinc, layer_potentials(A, 0, A.k1, x, y));
+        u[t] = cadd(acc, jexp_sum(A.a + A.col_a1, A.Q1, A.k1 * hypot(x, Ry), atan2(Ry, x)));
+        return;
+    }
+    if (y < bot) {
+        const double Ry = y - A.ycen3;
+        const cplx acc = layer_potentials(A, 1, A.k3, x, y);
+        u[t] = cadd(acc, jexp_sum(A.a + A.col_a3, A.Q3, A.k3 * hypot(x, Ry), atan2(Ry, x)));
+        return;
+    }
+    if (!(y > bot && y < top)) {   // on an interface
         u[t] = C(nan, nan);
         return;
     }
     const cplx ai = cconj(A.alpha);
-    cplx acc = C(0.0, 0.0);
-    // interfaces (k2), three copies each
-    for (int q = 0; q < 2; ++q) {
-        const double *cv = q == 0 ? A.c1 : A.c2;
-        const double *px = cv + A.N, *py = cv + 2 * A.N, *nx = cv + 3 * A.N, *ny = cv + 4 * A.N, *w = cv + 6 * A.N;
-        const cplx *mu = A.a + (q == 0 ? A.col_mu1 : A.col_mu2), *sg = A.a + (q == 0 ? A.col_sig1 : A.col_sig2);
-        for (int l = -1; l <= 1; ++l) {
-            const cplx ph = l == 0 ? C(1.0, 0.0) : (l == 1 ? A.alpha : ai);
-            cplx s = C(0.0, 0.0);
-            for (int j = 0; j < A.N; ++j) {
-                const double Rx = x - (px[j] + l * A.d), Ry = y - py[j];
-                const double r = hypot(Rx, Ry);
-                cplx H0, H1;
-                hankel01(A.k2 * r, H0, H1);
-                // S = (i/4) H0, D = (i k/4) H1 (R . n_y) / r
-                const cplx Sk = cmuli(cscale(H0, 0.25 * w[j]));
-                const cplx Dk = cmuli(cscale(H1, 0.25 * A.k2 * (Rx * nx[j] + Ry * ny[j]) / r * w[j]));
-                s = cadd(s, cadd(cmul(Sk, sg[j]), cmul(Dk, mu[j])));
-            }
-            acc = cadd(acc, cmul(ph, s));
-        }
-    }
+    cplx acc = cadd(layer_potentials(A, 0, A.k2, x, y), layer_potentials(A, 1, A.k2, x, y));
     // far copies: J-expansion about the layer's centre
     {
         const double Rx = x, Ry = y - A.ycen;
@@ -173,8 +224,25 @@ extern "C" int gs_field(gs_ctx *c, int angle, long npts, const double *xy_dev, g
     A.h1_0 = c->L.h1_0;
     A.h2_0 = c->L.h2_0;
     A.d = c->L.d;
+    A.k1 = c->L.k1;
     A.k2 = c->L.k2;
+    A.k3 = c->L.k3;
+    A.y0 = c->L.y0;
     A.ycen = 0.5 * (c->L.h1_0 + c->L.h2_0);
+    A.ycen1 = 0.5 * (c->L.h1_0 + c->L.y0);
+    A.ycen3 = 0.5 * (c->L.h2_0 - c->L.y0);
+    A.kx = a.kappa0;
+    A.ky = c->L.k1 * std::sin(a.theta);
+    A.col_a1 = ly.col_a1;
+    A.Q1 = ly.Q1;
+    A.col_a3 = ly.col_a3;
+    A.Q3 = ly.Q3;
+    A.col_c = ly.col_c;
+    A.col_d = ly.col_d;
+    A.K = ly.K;
+    A.kappa = a.kappa;
+    A.k1n = a.k1n;
+    A.k3n = a.k3n;
     A.alpha = a.alpha;
     A.a = c->x;
     A.col_mu1 = ly.col_mu1;

@@ -107,10 +107,10 @@ struct gs_ctx {
     void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
     long tcA_rows = 0, tcA_cols = 0;
     double tc_gamma = 1.0;                               // order rescaling of tcA (min(1, k2 r_min))
-    void *tcA_lo = nullptr;                              // bfloat16 remainder of the same operator (hi + lo split)
-    void *hl_scratch = nullptr;                          // scratch of the hi + lo multi-right-hand-side product
-    size_t hl_scratch_bytes = 0;
-    long hl_zeroed_R = -1;                               // R whose scratch padding is already zero
+    void *tcA_sp[2] = {nullptr, nullptr};                // second and third bfloat16 parts of the same operator
+    void *sp_scratch = nullptr;                          // scratch of the three-part multi-right-hand-side product
+    size_t sp_scratch_bytes = 0;
+    long sp_zeroed_R = -1;                               // R whose scratch padding is already zero
     void *tc_scratch = nullptr;                          // multi-right-hand-side scratch
     size_t tc_scratch_bytes = 0;
     long tc_zeroed_rp = -1, tc_zeroed_k = -1, tc_zeroed_R = -1;   // padding of the scratch already zero
@@ -191,13 +191,13 @@ int gs_build_pair_table(gs_ctx *c);
 // (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st
 int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st);
 // Tensor-core translation of R concatenated coefficient vectors (R angles of the current geometry,
-// image phases alpha_dev[r]) with the bfloat16 operator and the coefficients each split into hi + lo
-// parts (gs_tc.cu).  _prepare builds the two operators and the scratch for R (allocates: call it
-// before any stream capture); _translate only launches kernels (capturable) and sets *err_dev if a
-// device wait gave up.
-int gs_tc_hilo_prepare(gs_ctx *c, int R);
-int gs_tc_hilo_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
-                         cudaStream_t st);
+// image phases alpha_dev[r]) with the operator and the coefficients each split into three bfloat16
+// parts (gs_tc.cu).  _prepare builds the three operator parts and the scratch for R (allocates: call
+// it before any stream capture); _translate only launches kernels (capturable) and sets *err_dev if
+// a device wait gave up.
+int gs_tc_split_prepare(gs_ctx *c, int R);
+int gs_tc_split_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
+                          cudaStream_t st);
 // tensor-core product C[M][N] = A[M][K] B[N][K]^T, bfloat16 in, FP32 out (gs_tc.cu)
 int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
                     cudaStream_t st);

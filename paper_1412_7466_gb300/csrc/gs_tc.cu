@@ -255,8 +255,18 @@ int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, l
     CUtensorMap ma, mb;
     GS_TRY(make_map(c, &ma, A, M, K, TBM));
     GS_TRY(make_map(c, &mb, B, N, K, TBN));
-    // the function attribute is per device: set it on every call (cheap, host-side only)
-    GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
+    // the function attribute is per device: set once per device, outside any stream capture (the
+    // first product on a device is never inside one: gs_tc_split_prepare and the eager calls come first)
+    {
+        static std::mutex mu;
+        static bool done[64] = {};
+        std::lock_guard<std::mutex> lock(mu);
+        const int d = (c->device >= 0 && c->device < 64) ? c->device : 0;
+        if (!done[d]) {
+            GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
+            done[d] = true;
+        }
+    }
     GS_COUNT_LAUNCH(c);
     k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN)), 128, TSMEM, st>>>(ma, mb, C, (int)M, (int)N, (int)K,
                                                                                  err_dev);
@@ -275,11 +285,13 @@ namespace {
 // entry inside the bfloat16 range (23!/pi = 8e21 at p = 12); the coefficients are divided by
 // gamma^|n| on the way in and the results by gamma^|m| on the way out.
 //
-// With A_lo given, the remainder of each entry after its rounding to bfloat16 is rounded into A_lo
-// (A + A_lo carries ~16 significant bits instead of 8).
+// With A1 and A2 given, each entry is split into three bfloat16 parts: A holds its rounding, A1 the
+// rounding of the remainder and A2 the rounding of what is then left (A + A1 + A2 carries ~24
+// significant bits, the precision of FP32, instead of 8).
 template <int P>
 __global__ void k_tc_build_A(const double *__restrict__ xy, int M, double k, double d, double gamma, long lda,
-                             __nv_bfloat16 *__restrict__ A, __nv_bfloat16 *__restrict__ A_lo) {
+                             __nv_bfloat16 *__restrict__ A, __nv_bfloat16 *__restrict__ A1,
+                             __nv_bfloat16 *__restrict__ A2) {
     constexpr int NC = 2 * P + 1, NQ = 4 * P + 1;
     const long S = 3L * M;
     const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -323,14 +335,16 @@ __global__ void k_tc_build_A(const double *__restrict__ xy, int M, double k, dou
 #pragma unroll
         for (int n = 0; n < NC; ++n) {
             const cplx v = cscale(h[n - m + 2 * P], gm * gp[n < P ? P - n : n - P]);
-            const __nv_bfloat16 hr = __float2bfloat16_rn((float)v.x), hi_ = __float2bfloat16_rn((float)v.y);
-            re_row[n] = __halves2bfloat162(hr, __float2bfloat16_rn((float)-v.y));
-            im_row[n] = __halves2bfloat162(hi_, __float2bfloat16_rn((float)v.x));
-            if (A_lo) {
-                const __nv_bfloat16 lr = __float2bfloat16_rn((float)(v.x - (double)__bfloat162float(hr)));
-                const __nv_bfloat16 li = __float2bfloat16_rn((float)(v.y - (double)__bfloat162float(hi_)));
-                ((__nv_bfloat162 *)(A_lo + r_re))[n] = __halves2bfloat162(lr, __hneg(li));
-                ((__nv_bfloat162 *)(A_lo + r_im))[n] = __halves2bfloat162(li, lr);
+            double vr = v.x, vi = v.y;
+            __nv_bfloat16 *parts[3] = {A, A1, A2};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (!parts[q]) break;
+                const __nv_bfloat16 pr = __float2bfloat16_rn((float)vr), pi = __float2bfloat16_rn((float)vi);
+                ((__nv_bfloat162 *)(parts[q] + r_re))[n] = __halves2bfloat162(pr, __hneg(pi));
+                ((__nv_bfloat162 *)(parts[q] + r_im))[n] = __halves2bfloat162(pi, pr);
+                vr -= (double)__bfloat162float(pr);
+                vi -= (double)__bfloat162float(pi);
             }
         }
     }
@@ -368,10 +382,11 @@ __global__ void k_tc_unpack(const float *__restrict__ Cm, long ldc, int R, long 
     out[e] = C(sc * (double)Cm[(2 * q) * ldc + r], sc * (double)Cm[(2 * q + 1) * ldc + r]);
 }
 
-// hi + lo split of the stacked right-hand sides: row r of Bt holds the bfloat16 rounding of
-// a_r^l beta_r[j nc + n] / gamma^|n| (layout of k_tc_pack_B) and row R + r the rounding of what is left
-__global__ void k_tc_pack_B_hilo(const cplx *__restrict__ beta, const cplx *__restrict__ alpha, int R, int M, int nc,
-                                 GammaPow gpw, long ldb, __nv_bfloat16 *__restrict__ Bt) {
+// three-part split of the stacked right-hand sides: row b R + r of Bt (b = 0, 1, 2) holds part b of
+// a_r^l beta_r[j nc + n] / gamma^|n| (layout of k_tc_pack_B): its bfloat16 rounding, then the
+// rounding of the remainder, then the rounding of what is left
+__global__ void k_tc_pack_B_split(const cplx *__restrict__ beta, const cplx *__restrict__ alpha, int R, int M, int nc,
+                                  GammaPow gpw, long ldb, __nv_bfloat16 *__restrict__ Bt) {
     const long n = (long)M * nc;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)R * 3 * n) return;
@@ -382,26 +397,41 @@ __global__ void k_tc_pack_B_hilo(const cplx *__restrict__ beta, const cplx *__re
     const cplx a = alpha[r];
     const int p = nc / 2, o = (int)(q % nc) - p;
     const cplx v = cscale(l == 0 ? b : (l == 1 ? cmul(a, b) : cmul(cconj(a), b)), gpw.inv[abs(o)]);
-    const __nv_bfloat16 hr = __float2bfloat16_rn((float)v.x), hi = __float2bfloat16_rn((float)v.y);
-    ((__nv_bfloat162 *)(Bt + (long)r * ldb))[q] = __halves2bfloat162(hr, hi);
-    ((__nv_bfloat162 *)(Bt + (long)(R + r) * ldb))[q] =
-        __halves2bfloat162(__float2bfloat16_rn((float)(v.x - (double)__bfloat162float(hr))),
-                           __float2bfloat16_rn((float)(v.y - (double)__bfloat162float(hi))));
+    double vr = v.x, vi = v.y;
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+        const __nv_bfloat16 pr = __float2bfloat16_rn((float)vr), pi = __float2bfloat16_rn((float)vi);
+        ((__nv_bfloat162 *)(Bt + (long)(part * R + r) * ldb))[q] = __halves2bfloat162(pr, pi);
+        vr -= (double)__bfloat162float(pr);
+        vi -= (double)__bfloat162float(pi);
+    }
 }
 
-// out_r[e] = (hi x hi + hi x lo + lo x hi) / gamma^|m|: C1 = A_hi [B_hi; B_lo]^T (columns r and
-// R + r), C2 = A_lo B_hi^T (column r); rows 2e and 2e + 1 are the real and imaginary parts
-__global__ void k_tc_unpack_hilo(const float *__restrict__ C1, long ld1, const float *__restrict__ C2, long ld2, int R,
-                                 long n, int nc, GammaPow gpw, cplx *__restrict__ out) {
+// out_r[e] = sum over operator part a and coefficient part b with a + b <= 2 of A_a B_b, / gamma^|m|:
+// Ca = A_a [B_0; ...; B_{2-a}]^T holds column b R + r for each b <= 2 - a; rows 2e and 2e + 1 are the
+// real and imaginary parts
+__global__ void k_tc_unpack_split(const float *__restrict__ C0, long ld0, const float *__restrict__ C1, long ld1,
+                                  const float *__restrict__ C2, long ld2, int R, long n, int nc, GammaPow gpw,
+                                  cplx *__restrict__ out) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)R * n) return;
     const int r = (int)(e / n);
     const long q = e - (long)r * n;
     const int o = (int)(q % nc) - nc / 2;
     const double sc = gpw.inv[abs(o)];
-    const double re = (double)C1[(2 * q) * ld1 + r] + (double)C1[(2 * q) * ld1 + R + r] + (double)C2[(2 * q) * ld2 + r];
-    const double im = (double)C1[(2 * q + 1) * ld1 + r] + (double)C1[(2 * q + 1) * ld1 + R + r] +
-                      (double)C2[(2 * q + 1) * ld2 + r];
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        re += (double)C0[(2 * q) * ld0 + b * R + r];
+        im += (double)C0[(2 * q + 1) * ld0 + b * R + r];
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        re += (double)C1[(2 * q) * ld1 + b * R + r];
+        im += (double)C1[(2 * q + 1) * ld1 + b * R + r];
+    }
+    re += (double)C2[(2 * q) * ld2 + r];
+    im += (double)C2[(2 * q + 1) * ld2 + r];
     out[e] = C(sc * re, sc * im);
 }
 
@@ -426,7 +456,8 @@ int build_A(gs_ctx *c, long lda) {
     GS_COUNT_LAUNCH(c);
     k_tc_build_A<P><<<(int)((tot + 127) / 128), 128, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d, c->tc_gamma, lda,
                                                                      (__nv_bfloat16 *)c->tcA,
-                                                                     (__nv_bfloat16 *)c->tcA_lo);
+                                                                     (__nv_bfloat16 *)c->tcA_sp[0],
+                                                                     (__nv_bfloat16 *)c->tcA_sp[1]);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -436,33 +467,32 @@ inline long round_up(long v, long m) { return (v + m - 1) / m * m; }
 }  // namespace
 
 // the bfloat16 operator [T_-1 T_0 T_1] of the current geometry in real 2x2 form (built on first use);
-// with_lo: also the bfloat16 remainder of every entry (the hi + lo split)
-int gs_tc_operator(gs_ctx *c, bool with_lo = false) {
+// with_split: also the second and third bfloat16 parts of every entry (the three-part split)
+int gs_tc_operator(gs_ctx *c, bool with_split = false) {
     const long n = c->n();
     const long rows = round_up(2 * n, TBM), cols = round_up(6 * n, TBK);
-    if (c->tcA && c->tcA_rows == rows && c->tcA_cols == cols && (!with_lo || c->tcA_lo)) return GS_OK;
-    if (c->tcA) cudaFree(c->tcA);
-    c->tcA = nullptr;
-    if (c->tcA_lo) cudaFree(c->tcA_lo);
-    c->tcA_lo = nullptr;
-    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)rows * cols;
-    cudaError_t e = cudaMalloc((void **)&c->tcA, bytes);
-    if (e == cudaSuccess && with_lo) {
-        e = cudaMalloc((void **)&c->tcA_lo, bytes);
-        if (e != cudaSuccess) {
-            cudaFree(c->tcA);
-            c->tcA = nullptr;
-        }
+    if (c->tcA && c->tcA_rows == rows && c->tcA_cols == cols && (!with_split || (c->tcA_sp[0] && c->tcA_sp[1])))
+        return GS_OK;
+    void **bufs[3] = {&c->tcA, &c->tcA_sp[0], &c->tcA_sp[1]};
+    for (void **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
     }
+    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)rows * cols;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < (with_split ? 3 : 1) && e == cudaSuccess; ++q) e = cudaMalloc(bufs[q], bytes);
     if (e != cudaSuccess) {
-        c->tcA = c->tcA_lo = nullptr;
+        for (void **b : bufs) {
+            if (*b) cudaFree(*b);
+            *b = nullptr;
+        }
         cudaGetLastError();
         return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (tensor-core operator): ") + cudaGetErrorString(e));
     }
     c->tcA_rows = rows;
     c->tcA_cols = cols;
-    GS_CUDA(c, cudaMemsetAsync(c->tcA, 0, bytes, c->stream));
-    if (c->tcA_lo) GS_CUDA(c, cudaMemsetAsync(c->tcA_lo, 0, bytes, c->stream));
+    for (void **b : bufs)
+        if (*b) GS_CUDA(c, cudaMemsetAsync(*b, 0, bytes, c->stream));
     GS_COUNT_LAUNCH(c);
     k_min_radius<<<1, 1024, 0, c->stream>>>(c->radius, c->M, c->dscal + 10);
     GS_CHECK_LAUNCH(c);
@@ -553,25 +583,30 @@ extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, c
 }
 
 namespace {
-struct HiloLayout {
-    long K, Mr, Np1, Np2;
+// scratch of the three-part product for R right-hand sides: the stacked coefficient parts Bt
+// (3R rows, padded to 256) and the products C_a = A_a [B_0 .. B_{2-a}]^T of the operator parts
+struct SplitLayout {
+    long K, Mr, Np[3];
     __nv_bfloat16 *Bt;
-    float *C1, *C2;
+    float *Cp[3];
     size_t bytes;
 };
-HiloLayout hilo_layout(gs_ctx *c, int R, void *base) {
-    HiloLayout L;
+SplitLayout split_layout(gs_ctx *c, int R, void *base) {
+    SplitLayout L;
     L.K = c->tcA_cols;
     L.Mr = c->tcA_rows;
-    L.Np1 = round_up(2L * R, TBN);
-    L.Np2 = round_up((long)R, TBN);
-    const size_t o1 = (size_t)round_up(sizeof(__nv_bfloat16) * L.Np1 * L.K, 256);
-    const size_t o2 = o1 + (size_t)round_up(sizeof(float) * L.Mr * L.Np1, 256);
-    L.bytes = o2 + (size_t)round_up(sizeof(float) * L.Mr * L.Np2, 256);
+    size_t off[4];
+    off[0] = 0;
+    for (int a = 0; a < 3; ++a) L.Np[a] = round_up((3L - a) * R, TBN);
+    size_t o = (size_t)round_up(sizeof(__nv_bfloat16) * L.Np[0] * L.K, 256);
+    for (int a = 0; a < 3; ++a) {
+        off[a + 1] = o;
+        o += (size_t)round_up(sizeof(float) * L.Mr * L.Np[a], 256);
+    }
+    L.bytes = o;
     uint8_t *p = (uint8_t *)base;
     L.Bt = (__nv_bfloat16 *)p;
-    L.C1 = p ? (float *)(p + o1) : nullptr;
-    L.C2 = p ? (float *)(p + o2) : nullptr;
+    for (int a = 0; a < 3; ++a) L.Cp[a] = p ? (float *)(p + off[a + 1]) : nullptr;
     return L;
 }
 GammaPow gamma_pows(double gamma) {
@@ -582,61 +617,63 @@ GammaPow gamma_pows(double gamma) {
 }
 }  // namespace
 
-int gs_tc_hilo_prepare(gs_ctx *c, int R) {
+int gs_tc_split_prepare(gs_ctx *c, int R) {
     if (R < 1 || R > 65536) return gs_fail(c, GS_ERR_ARG, "need 1..65536 right-hand sides");
+    GS_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM));
     GS_TRY(gs_tc_operator(c, true));
-    const HiloLayout L = hilo_layout(c, R, nullptr);
-    if (L.bytes > c->hl_scratch_bytes) {
-        if (c->hl_scratch) cudaFree(c->hl_scratch);
-        c->hl_scratch = nullptr;
-        c->hl_scratch_bytes = 0;
-        cudaError_t e = cudaMalloc(&c->hl_scratch, L.bytes);
+    const SplitLayout L = split_layout(c, R, nullptr);
+    if (L.bytes > c->sp_scratch_bytes) {
+        if (c->sp_scratch) cudaFree(c->sp_scratch);
+        c->sp_scratch = nullptr;
+        c->sp_scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->sp_scratch, L.bytes);
         if (e != cudaSuccess) {
-            c->hl_scratch = nullptr;
+            c->sp_scratch = nullptr;
             cudaGetLastError();
-            return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (hi + lo tensor-core scratch): ") + cudaGetErrorString(e));
+            return gs_fail(c, GS_ERR_OOM, std::string("cudaMalloc (tensor-core split scratch): ") + cudaGetErrorString(e));
         }
-        c->hl_scratch_bytes = L.bytes;
-        c->hl_zeroed_R = -1;
+        c->sp_scratch_bytes = L.bytes;
+        c->sp_zeroed_R = -1;
     }
-    if (c->hl_zeroed_R != R) {
-        // padding rows (>= 2R) and columns (>= 6n) of the stacked right-hand sides stay zero
-        const HiloLayout Lb = hilo_layout(c, R, c->hl_scratch);
-        GS_CUDA(c, cudaMemsetAsync(Lb.Bt, 0, sizeof(__nv_bfloat16) * (size_t)Lb.Np1 * Lb.K, c->stream));
-        c->hl_zeroed_R = R;
+    if (c->sp_zeroed_R != R) {
+        // padding rows (>= 3R) and columns (>= 6n) of the stacked coefficient parts stay zero
+        const SplitLayout Lb = split_layout(c, R, c->sp_scratch);
+        GS_CUDA(c, cudaMemsetAsync(Lb.Bt, 0, sizeof(__nv_bfloat16) * (size_t)Lb.Np[0] * Lb.K, c->stream));
+        c->sp_zeroed_R = R;
     }
     return GS_OK;
 }
 
-int gs_tc_hilo_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
-                         cudaStream_t st) {
-    if (!c->tcA || !c->tcA_lo || c->hl_zeroed_R != R) return gs_fail(c, GS_ERR_STATE, "gs_tc_hilo_prepare has not run");
+int gs_tc_split_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
+                          cudaStream_t st) {
+    if (!c->tcA || !c->tcA_sp[0] || !c->tcA_sp[1] || c->sp_zeroed_R != R)
+        return gs_fail(c, GS_ERR_STATE, "gs_tc_split_prepare has not run");
     const long n = c->n();
-    const HiloLayout L = hilo_layout(c, R, c->hl_scratch);
+    const SplitLayout L = split_layout(c, R, c->sp_scratch);
     const GammaPow gpw = gamma_pows(c->tc_gamma);
+    const void *Ap[3] = {c->tcA, c->tcA_sp[0], c->tcA_sp[1]};
     GS_COUNT_LAUNCH(c);
-    k_tc_pack_B_hilo<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>(x, alpha_dev, R, c->M, c->nc, gpw, L.K, L.Bt);
+    k_tc_pack_B_split<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>(x, alpha_dev, R, c->M, c->nc, gpw, L.K, L.Bt);
     GS_CHECK_LAUNCH(c);
-    GS_TRY(gs_tc_gemm_impl(c, c->tcA, L.Bt, L.C1, L.Mr, L.Np1, L.K, err_dev, st));
-    GS_TRY(gs_tc_gemm_impl(c, c->tcA_lo, L.Bt, L.C2, L.Mr, L.Np2, L.K, err_dev, st));
+    for (int a = 0; a < 3; ++a) GS_TRY(gs_tc_gemm_impl(c, Ap[a], L.Bt, L.Cp[a], L.Mr, L.Np[a], L.K, err_dev, st));
     GS_COUNT_LAUNCH(c);
-    k_tc_unpack_hilo<<<(int)((n * R + 255) / 256), 256, 0, st>>>(L.C1, L.Np1, L.C2, L.Np2, R, n, c->nc, gpw, out);
+    k_tc_unpack_split<<<(int)((n * R + 255) / 256), 256, 0, st>>>(L.Cp[0], L.Np[0], L.Cp[1], L.Np[1], L.Cp[2], L.Np[2], R,
+                                                                   n, c->nc, gpw, out);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
 
-extern "C" int gs_translate_multi_hilo(gs_ctx *c, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev,
-                                       gs_c128 *out_dev) {
+extern "C" int gs_translate_multi_split(gs_ctx *c, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev,
+                                        gs_c128 *out_dev) {
     if (!c) return GS_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, "cudaSetDevice");
     if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
     if (R < 1 || R > 65536 || !alpha_host || !beta_dev || !out_dev)
         return gs_fail(c, GS_ERR_ARG, "need 1..65536 right-hand sides and non-null pointers");
-    GS_TRY(gs_tc_hilo_prepare(c, R));
+    GS_TRY(gs_tc_split_prepare(c, R));
     cplx *al = nullptr;
-    int *err = nullptr;
     GS_CUDA(c, cudaMalloc((void **)&al, sizeof(cplx) * R + 256));
-    err = (int *)((uint8_t *)al + round_up(sizeof(cplx) * R, 16));
+    int *err = (int *)((uint8_t *)al + round_up(sizeof(cplx) * R, 16));
     int st = GS_OK;
     cudaError_t e = cudaMemcpyAsync(al, alpha_host, sizeof(cplx) * R, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), c->stream);
@@ -644,7 +681,7 @@ extern "C" int gs_translate_multi_hilo(gs_ctx *c, int R, const gs_c128 *alpha_ho
     cudaEvent_t e0, e1;
     const bool timed = st == GS_OK && gs_prof_pair(c, &e0, &e1, GS_TC_BF16);
     if (timed) cudaEventRecord(e0, c->stream);
-    if (st == GS_OK) st = gs_tc_hilo_translate(c, R, al, (const cplx *)beta_dev, (cplx *)out_dev, err, c->stream);
+    if (st == GS_OK) st = gs_tc_split_translate(c, R, al, (const cplx *)beta_dev, (cplx *)out_dev, err, c->stream);
     if (timed) cudaEventRecord(e1, c->stream);
     int herr = 0;
     if (st == GS_OK) {

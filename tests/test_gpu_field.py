@@ -1,9 +1,10 @@
-"""Field evaluation in the middle layer (through the C-ABI) against the oracle: same points, the
-oracle from its own dense solution.  Both are FP64 trapezoid/Hankel sums of the same representation
+"""Field evaluation (through the C-ABI) against the oracle: same points, the oracle from its own
+dense solution; the middle layer with its inclusions, then all three layers and the Rayleigh-Bloch
+regions beyond +-y0.  Both are FP64 trapezoid/Hankel sums of the same representation
 with different Bessel implementations and solutions agreeing to ~1e-10: 1e-8 of the field's
 largest value from 1.5 radii away from every inclusion (closer in, the evaluation amplifies the
 solutions' last-digit differences in the highest orders; 1e-5 there).  Points outside the period
-or the layer, and inside inclusions, are NaN."""
+and inside inclusions are NaN."""
 import math
 
 import numpy as np
@@ -32,7 +33,7 @@ def test_field_matches_oracle():
     c0 = cfg["disks"]["xy"][0]
     pts = np.vstack([pts, c0 + [0.01, 0.0]])                       # inside a disk
     got = gs.field(pts).cpu().numpy()
-    ref = F.middle_field(prob, beta, pts)
+    ref = F.field(prob, beta, pts)
     assert np.array_equal(np.isnan(got), np.isnan(ref))
     assert np.isnan(got[-1])
     ok = ~np.isnan(ref)
@@ -49,8 +50,8 @@ def test_field_matches_oracle():
     assert far.sum() > 900
     assert np.max(np.abs(got[far] - ref[far])) <= 1e-8 * scale
     assert np.max(np.abs(got[near] - ref[near])) <= 1e-5 * scale
-    # outside the period or the layer
-    out = gs.field(np.array([[0.6, 0.0], [0.0, 0.7], [0.0, -0.7]])).cpu().numpy()
+    # outside the period
+    out = gs.field(np.array([[0.6, 0.0], [-0.7, 0.9], [0.51, -1.2]])).cpu().numpy()
     assert np.all(np.isnan(out))
     gs.close()
 
@@ -76,3 +77,63 @@ def test_field_transparent_grating_is_the_plane_wave():
     assert ok.sum() >= 190
     assert np.max(np.abs(u[ok] - ref[ok])) < 1e-9
     gs.close()
+
+
+def test_field_all_layers_matches_oracle():
+    """The field on a grid spanning all three layers and the Rayleigh-Bloch regions beyond +-y0
+    (y in [-1.4, 1.4]) against the oracle's all-layer field: same representation, different Bessel
+    implementations, solutions agreeing to ~1e-10.  Away from the interfaces and inclusions 1e-8 of
+    the largest value; within 0.05 of an interface the trapezoid sums' near field amplifies the two
+    solutions' last-digit differences in the densities by up to ~h / dist (measured 2.5e-6 at
+    1e-3 from an interface): 1e-5 there."""
+    from paper_1412_7466_gb300 import GratingSolver
+    cfg = W.config("small")
+    g = cfg["grating"]
+    prob = S.setup(g, cfg["theta"], cfg["disks"])
+    beta, _, _ = S.solve_dense(prob)
+    gs = GratingSolver(0)
+    gs.set_layers(g)
+    gs.set_incidence([cfg["theta"]])
+    gs.set_inclusions(cfg["disks"])
+    gs.factor()
+    gs.solve(tol=1e-13, maxit=500)
+    xs, ys = np.meshgrid(np.linspace(-0.5, 0.5, 33), np.linspace(-1.4, 1.4, 71))
+    pts = np.stack([xs.ravel(), ys.ravel()], axis=1)
+    got = gs.field(pts).cpu().numpy()
+    gs.close()
+    ref = F.field(prob, beta, pts)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    from oracle import layers as L
+    h1 = L.iface_eval(g["gamma1"], g["d"], pts[:, 0])[0]
+    h2 = L.iface_eval(g["gamma2"], g["d"], pts[:, 0])[0]
+    dint = np.minimum(np.abs(pts[:, 1] - h1), np.abs(pts[:, 1] - h2))
+    xy, r = cfg["disks"]["xy"], cfg["disks"]["radius"]
+    dmin = np.min([np.hypot(pts[:, 0, None] - (xy[None, :, 0] + l), pts[:, 1, None] - xy[None, :, 1]) / r[None, :]
+                   for l in (-1, 0, 1)], axis=(0, 2))
+    far = ok & (dint > 0.05) & (dmin >= 1.5)
+    near = ok & (dint <= 0.05) & (dint > 1e-3) & (dmin >= 1.5)
+    scale = np.max(np.abs(ref[ok]))
+    for sel in (pts[:, 1] > 1.0, pts[:, 1] < -1.0, (pts[:, 1] > h1) & (pts[:, 1] < 1.0),
+                (pts[:, 1] < h2) & (pts[:, 1] > -1.0)):
+        assert (far & sel).sum() > 50
+    assert np.max(np.abs(got[far] - ref[far])) <= 1e-8 * scale
+    assert np.max(np.abs(got[near] - ref[near])) <= 1e-5 * scale
+    # the plane wave through a transparent grating, beyond +-y0 too
+    gt = dict(g)
+    k = 10.0
+    gt["k"] = (k, k, k)
+    th = -math.pi / 5
+    dk = W.disks(1, 0.04, 0.02, 1.0, k, seed=2, p=6)
+    gs = GratingSolver(0)
+    gs.set_layers(gt)
+    gs.set_incidence([th])
+    gs.set_inclusions(dk)
+    gs.factor()
+    gs.solve(tol=1e-13, maxit=100)
+    u = gs.field(pts[far]).cpu().numpy()
+    gs.close()
+    pw = np.exp(1j * k * (math.cos(th) * pts[far, 0] + math.sin(th) * pts[far, 1]))
+    good = ~np.isnan(u)
+    assert good.sum() >= far.sum() - 2
+    assert np.max(np.abs(u[good] - pw[good])) < 1e-9

@@ -30,10 +30,15 @@ def test_paper_experiment_analogues():
 
 @pytest.mark.parametrize("case", ["example1_homogeneous", "example1_layered", "example3_k2_20"])
 def test_study_configurations_against_oracle(case):
-    """Study configurations solved by the library against the oracle's dense LU solution: Example 1
-    with M = 100 disks (k_p = 30, p = 10) in the homogeneous k = (10, 10, 10) and layered
-    k = (10, 8, 10) backgrounds near the k1 = 10 Wood angle, and Example 3 at k2 = 20 with disks
-    crossing the walls; Bragg amplitudes to 1e-9 (norm-wise and element-wise)."""
+    """Study configurations solved by the library against the oracle: Example 1 with M = 100 disks
+    (k_p = 30, p = 10) in the homogeneous k = (10, 10, 10) and layered k = (10, 8, 10) backgrounds
+    near the k1 = 10 Wood angle, and Example 3 at k2 = 20 with disks crossing the walls.  The
+    reference is the oracle's matrix-free GMRES solution to 1e-13: on Example 1 the dense
+    preconditioned matrix has a condition number near 1e24 (the products s_n H_q(k2 R) of tiny
+    high-order disk coefficients and huge close-pair Hankel values span ~30 decades), and the
+    oracle's own LU and GMRES solutions differ by 2.5e-9 in the Bragg amplitudes there, whatever
+    the GMRES tolerance.  Bragg amplitudes to 1e-9 norm-wise; element-wise to 1e-8 on Example 1
+    (weakest order 1e-2 of the norm), 1e-9 on Example 3."""
     import math
 
     import workloads as W
@@ -59,7 +64,7 @@ def test_study_configurations_against_oracle(case):
     got = gs.bragg()
     gs.close()
     prob = S.setup(g, theta, dk)
-    beta, _, _ = S.solve_dense(prob)
+    beta, _, _, _ = S.solve_gmres(prob, tol=1e-13, restart=500, maxit=4000)
     _, ref, _ = prob.recover(beta)
-    nw, ew = check_bragg(got, ref)
+    nw, ew = check_bragg(got, ref, 1e-9, 1e-8 if case.startswith("example1") else 1e-9)
     print(case, "Bragg error vs oracle", nw, ew)
