@@ -64,6 +64,17 @@ typedef struct {
     double eps_pinv;
 } gs_layers;
 
+/* Polarisation (Sec. 2): GS_TM (default, u the electric field; [u] = [d_n u] = 0 on the interfaces)
+ * or GS_TE (u the magnetic field; [u] = [(1/eps) d_n u] = 0, eps_j proportional to k_j^2 for a
+ * constant permeability; Sec. 7 leaves it to future work).  TE scales each layer's potentials by its
+ * permittivity relative to the middle layer, w_j = (k_j/k_2)^2 (which keeps the system of the second
+ * kind), the flux rows by 1/w_j, uses the TE disk coefficients and the TE energy identity
+ * sum k_{1,n}|c_n|^2/w1 + sum k_{3,n}|d_n|^2/w3 = k1|sin theta|/w1 for gs_bragg's flux error.
+ * Changing it discards every factorisation; kept across gs_set_layers. */
+#define GS_TM 0
+#define GS_TE 1
+int gs_set_polarization(gs_ctx *ctx, int pol);
+
 /* Disk inclusions (Sec. 4): M centres xy[2*i], xy[2*i+1] (host, unit cell x in [-d/2, d/2)),
  * radii and interior wavenumbers kp (host, length M), multipole order p (1 <= p <= 16). */
 typedef struct {
@@ -105,6 +116,14 @@ int gs_set_incidence(gs_ctx *ctx, int n_angles, const double *theta);
 /* Disks; GS_ERR_GEOMETRY if two disks overlap (minimum image in x) or a disk touches an
  * interface's extreme height band.  Requires gs_set_layers first. */
 int gs_set_inclusions(gs_ctx *ctx, const gs_inclusions *inc);
+
+/* Lossy inclusions (complex permittivity, Sec. 7): kp_im (host, length M of the current inclusions,
+ * >= 0) is the imaginary part of each disk's interior wavenumber kp + i kp_im; NULL makes all disks
+ * lossless again.  The disk coefficients then use J_n of complex argument (power series, for
+ * |kp R| <= 12; GS_ERR_ARG beyond).  gs_bragg's flux error then measures the absorbed fraction.
+ * Invalidates the inclusion part of the factorisation (call gs_factor again); gs_set_inclusions
+ * resets the disks to lossless.  The batched solves take lossless disks. */
+int gs_set_inclusion_loss(gs_ctx *ctx, const double *kp_im);
 
 /* Builds, on the GPU in FP64, what the solve needs (Sec. 3 and Sec. 5).  Per incidence angle, once
  * for the grating: assembles the empty-grating matrix A (Eq. matA) and right-hand side f (Eq. Arhs),

@@ -29,6 +29,8 @@ GS_FP64 = 0
 GS_C64 = 1
 GS_PROBE_F32X2 = 2
 GS_TC_BF16 = 3
+GS_TM = 0
+GS_TE = 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -64,6 +66,8 @@ _SIGS = {
     "gs_set_layers": (ctypes.c_int, [_vp, ctypes.POINTER(gs_layers)]),
     "gs_set_incidence": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "gs_set_inclusions": (ctypes.c_int, [_vp, ctypes.POINTER(gs_inclusions)]),
+    "gs_set_polarization": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "gs_set_inclusion_loss": (ctypes.c_int, [_vp, _dp]),
     "gs_factor": (ctypes.c_int, [_vp]),
     "gs_dims": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
     "gs_get_A": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
@@ -250,6 +254,10 @@ class GratingSolver:
                       n_wall1=g["n_wall"][0], n_wall2=g["n_wall"][1], n_wall3=g["n_wall"][2],
                       n_bound=g["n_bound"], eps_pinv=g["eps_pinv"])
         self._check(self.lib.gs_set_layers(self.ctx, ctypes.byref(L)), "gs_set_layers")
+        pol = g.get("pol", "TM")
+        if pol not in ("TM", "TE"):
+            raise ValueError("polarisation must be 'TM' or 'TE'")
+        self._check(self.lib.gs_set_polarization(self.ctx, GS_TE if pol == "TE" else GS_TM), "gs_set_polarization")
         self.grating = g
 
     def set_incidence(self, thetas):
@@ -258,11 +266,16 @@ class GratingSolver:
         self.thetas = a.copy()
 
     def set_inclusions(self, disks: dict):
+        """Disks {"xy", "radius", "kp", "p"}; a complex kp (Im kp >= 0) makes the disks lossy."""
         xy, pxy = _arr(disks["xy"])
         r, pr = _arr(disks["radius"])
-        kp, pkp = _arr(disks["kp"])
+        kpc = np.asarray(disks["kp"])
+        kp, pkp = _arr(np.real(kpc))
         I = gs_inclusions(M=xy.shape[0], p=int(disks["p"]), xy=pxy, radius=pr, kp=pkp)
         self._check(self.lib.gs_set_inclusions(self.ctx, ctypes.byref(I)), "gs_set_inclusions")
+        if np.iscomplexobj(kpc) and np.any(np.imag(kpc) != 0):
+            ki, pki = _arr(np.imag(kpc))
+            self._check(self.lib.gs_set_inclusion_loss(self.ctx, pki), "gs_set_inclusion_loss")
         self.M, self.p = xy.shape[0], int(disks["p"])
 
     def factor(self):

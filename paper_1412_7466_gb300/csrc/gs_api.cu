@@ -297,6 +297,7 @@ void gs_destroy(gs_ctx *c) {
     dfree(c->xy);
     dfree(c->radius);
     dfree(c->kp);
+    dfree(c->kp_im);
     dfree(c->s);
     dfree(c->dscal);
     dfree(c->dcount);
@@ -380,7 +381,7 @@ int gs_set_layers(gs_ctx *c, const gs_layers *L) {
         if (!(h2max < h1min) || !(L->y0 > h1max) || !(-L->y0 < h2min))
             return gs_fail(c, GS_ERR_GEOMETRY, "interfaces must satisfy -y0 < Gamma2 < Gamma1 < y0");
     }
-    for (int q = 0; q < 2; ++q) GS_TRY(dalloc(c, &c->curve[q], 7 * (size_t)N));
+    for (int q = 0; q < 2; ++q) GS_TRY(dalloc(c, &c->curve[q], 8 * (size_t)N));
     GS_TRY(dalloc(c, &c->wall_y[0], y.nw1));
     GS_TRY(dalloc(c, &c->wall_y[1], y.nw2));
     GS_TRY(dalloc(c, &c->wall_y[2], y.nw3));
@@ -492,7 +493,41 @@ int gs_set_inclusions(gs_ctx *c, const gs_inclusions *I) {
     GS_CUDA(c, cudaMemcpyAsync(c->radius, I->radius, sizeof(double) * c->M, cudaMemcpyHostToDevice, c->stream));
     GS_CUDA(c, cudaMemcpyAsync(c->kp, I->kp, sizeof(double) * c->M, cudaMemcpyHostToDevice, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    dfree(c->kp_im);   // new inclusions are lossless until gs_set_inclusion_loss
+    c->radius_h.assign(I->radius, I->radius + c->M);
+    c->kp_h.assign(I->kp, I->kp + c->M);
     c->have_inc = true;
+    return GS_OK;
+}
+
+int gs_set_polarization(gs_ctx *c, int pol) {
+    CTX_GUARD(c);
+    if (pol != GS_TM && pol != GS_TE) return gs_fail(c, GS_ERR_ARG, "polarisation must be GS_TM or GS_TE");
+    if (pol != c->pol) {
+        free_factor(c);   // the grating's matrix, right-hand side and the disk coefficients change
+        c->pol = pol;
+    }
+    return GS_OK;
+}
+
+int gs_set_inclusion_loss(gs_ctx *c, const double *kp_im) {
+    CTX_GUARD(c);
+    if (!c->have_inc) return gs_fail(c, GS_ERR_STATE, "gs_set_inclusions must come first");
+    free_geometry(c);
+    dfree(c->kp_im);
+    if (!kp_im) return GS_OK;
+    bool any = false;
+    for (int i = 0; i < c->M; ++i) {
+        if (!std::isfinite(kp_im[i]) || kp_im[i] < 0.0)
+            return gs_fail(c, GS_ERR_ARG, "disk " + std::to_string(i) + ": Im kp must be finite and >= 0");
+        if (kp_im[i] > 0.0 && std::hypot(c->kp_h[i], kp_im[i]) * c->radius_h[i] > 12.0)
+            return gs_fail(c, GS_ERR_ARG, "disk " + std::to_string(i) + ": |kp R| > 12 for a lossy disk");
+        any = any || kp_im[i] > 0.0;
+    }
+    if (!any) return GS_OK;
+    GS_TRY(dalloc(c, &c->kp_im, c->M));
+    GS_CUDA(c, cudaMemcpyAsync(c->kp_im, kp_im, sizeof(double) * c->M, cudaMemcpyHostToDevice, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
     return GS_OK;
 }
 

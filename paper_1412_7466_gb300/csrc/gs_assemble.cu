@@ -17,10 +17,10 @@ constexpr int TPB = 256;
 inline int nblk(long n, int t = TPB) { return (int)((n + t - 1) / t); }
 
 struct Curve {
-    const double *x, *px, *py, *nx, *ny, *sp, *w;
+    const double *x, *px, *py, *nx, *ny, *sp, *w, *curv;
 };
 Curve curve_of(const double *base, int N) {
-    return Curve{base, base + N, base + 2 * N, base + 3 * N, base + 4 * N, base + 5 * N, base + 6 * N};
+    return Curve{base, base + N, base + 2 * N, base + 3 * N, base + 4 * N, base + 5 * N, base + 6 * N, base + 7 * N};
 }
 
 // ---- geometry -------------------------------------------------------------------------------
@@ -30,12 +30,13 @@ __global__ void k_curve_nodes(int N, double d, double h0, int nf, const double *
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double x = -0.5 * d + (i + 0.5) * d / N;
-    double h = h0, hp = 0.0;
+    double h = h0, hp = 0.0, hpp = 0.0;
     for (int m = 1; m <= nf; ++m) {
         double om = 2.0 * GS_PI * m / d, s, c;
         sincos(om * x, &s, &c);
         h += ca[m - 1] * c + sa[m - 1] * s;
         hp += -ca[m - 1] * om * s + sa[m - 1] * om * c;
+        hpp += -(ca[m - 1] * c + sa[m - 1] * s) * om * om;
     }
     double sp = sqrt(1.0 + hp * hp);
     out[i] = x;
@@ -45,6 +46,7 @@ __global__ void k_curve_nodes(int N, double d, double h0, int nf, const double *
     out[4 * N + i] = 1.0 / sp;
     out[5 * N + i] = sp;
     out[6 * N + i] = sp * d / N;
+    out[7 * N + i] = hpp / (sp * sp * sp);   // signed curvature with respect to the upward normal
 }
 
 // Gauss-Legendre nodes on [lo, hi], ascending, by Newton iteration on P_n.
@@ -122,10 +124,12 @@ __device__ __forceinline__ void log_coeffs(double Rx, double Ry, double tnx, dou
     out[3] = c * k * (k * J0 * Rnx * Rny * ir * ir - 2.0 * J1 * Rnx * Rny * ir * ir * ir + J1 * nn * ir);
 }
 
-// Self blocks of one interface: differences of the ka and kb operators (S, D, N, T), near
-// copies with Bloch phases, Kress-corrected.  Writes A11-type blocks:
-//   [row_v, col_mu] = I + D,  [row_v, col_sig] = S,  [row_n, col_mu] = T,  [row_n, col_sig] = -I + N.
-__global__ void k_self_ops(int N, double d, Curve cv, cplx alpha, double ka, double kb,
+// Self blocks of one interface: differences of the ka and kb operators, wa S_ka - wb S_kb,
+// wa D_ka - wb D_kb, N_ka - N_kb, T_ka - T_kb (the weights are the TE permittivity ratios of the two
+// sides, 1 for TM), near copies with Bloch phases, Kress-corrected.  Writes A11-type blocks:
+//   [row_v, col_mu] = (wa + wb)/2 I + D,  [row_v, col_sig] = S,  [row_n, col_mu] = T,
+//   [row_n, col_sig] = -I + N.
+__global__ void k_self_ops(int N, double d, Curve cv, cplx alpha, double ka, double kb, double wa, double wb,
                            const double *R, cplx *A, int lda, int row_v, int row_n, int col_mu,
                            int col_sig) {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,8 +144,8 @@ __global__ void k_self_ops(int N, double d, Curve cv, cplx alpha, double ka, dou
         K4 a = layer_kernels(Rx, Ry, cv.nx[i], cv.ny[i], cv.nx[j], cv.ny[j], ka);
         K4 b = layer_kernels(Rx, Ry, cv.nx[i], cv.ny[i], cv.nx[j], cv.ny[j], kb);
         cplx ph = (l == 0) ? C(1, 0) : (l == 1 ? alpha : ainv);
-        F[0] = cadd(F[0], cmul(ph, csub(a.S, b.S)));
-        F[1] = cadd(F[1], cmul(ph, csub(a.D, b.D)));
+        F[0] = cadd(F[0], cmul(ph, csub(cscale(a.S, wa), cscale(b.S, wb))));
+        F[1] = cadd(F[1], cmul(ph, csub(cscale(a.D, wa), cscale(b.D, wb))));
         F[2] = cadd(F[2], cmul(ph, csub(a.N, b.N)));
         F[3] = cadd(F[3], cmul(ph, csub(a.T, b.T)));
     }
@@ -160,20 +164,27 @@ __global__ void k_self_ops(int N, double d, Curve cv, cplx alpha, double ka, dou
             double la[4], lb[4];
             log_coeffs(Rx, Ry, cv.nx[i], cv.ny[i], cv.nx[j], cv.ny[j], ka, la);
             log_coeffs(Rx, Ry, cv.nx[i], cv.ny[i], cv.nx[j], cv.ny[j], kb, lb);
-            for (int q = 0; q < 4; ++q) L[q] = psi * 0.5 * (la[q] - lb[q]) * cv.sp[j];
+            for (int q = 0; q < 4; ++q) {
+                const double w_a = q < 2 ? wa : 1.0, w_b = q < 2 ? wb : 1.0;
+                L[q] = psi * 0.5 * (w_a * la[q] - w_b * lb[q]) * cv.sp[j];
+            }
             ph = (lstar == 0.0) ? C(1, 0) : (lstar > 0.0 ? alpha : ainv);
         }
         double s = sin(GS_PI * (double)(i - j) / N);
         double corr = W - h * log(4.0 * s * s);
         for (int q = 0; q < 4; ++q) out[q] = cadd(cscale(F[q], hw), cscale(ph, corr * L[q]));
     } else {
-        // diagonal: limits of the kernel differences (log r coefficient K1, remainder Krest)
+        // diagonal: limits of the kernel differences (log r coefficient K1, remainder Krest): for S
+        // from (i/4) H0(kr) = -log(r)/(2 pi) + i/4 - (log(k/2) + gamma)/(2 pi) + o(1); for D the
+        // Laplace double layer's limit kappa/(4 pi) (kappa the curvature), which cancels unless the
+        // weights differ; N's curvature term and T's hypersingular part cancel in the differences
         double sp = cv.sp[i];
         double lg = log(sp * sp * d * d / (4.0 * GS_PI * GS_PI));
         double dk2 = ka * ka - kb * kb;
         double la = log(ka / 2.0), lb = log(kb / 2.0);
-        double K1[4] = {0.0, 0.0, 0.0, -dk2 / (4.0 * GS_PI)};
-        cplx Kr[4] = {C(-(la - lb) / (2.0 * GS_PI), 0.0), C(0, 0), C(0, 0),
+        double K1[4] = {-(wa - wb) / (2.0 * GS_PI), 0.0, 0.0, -dk2 / (4.0 * GS_PI)};
+        cplx Kr[4] = {C(-(wa * (la + GS_EULER) - wb * (lb + GS_EULER)) / (2.0 * GS_PI), 0.25 * (wa - wb)),
+                      C((wa - wb) * cv.curv[i] / (4.0 * GS_PI), 0.0), C(0, 0),
                       C(-(ka * ka * la - kb * kb * lb) / (4.0 * GS_PI) +
                             dk2 * (1.0 - 2.0 * GS_EULER) / (8.0 * GS_PI),
                         dk2 / 8.0)};
@@ -183,7 +194,7 @@ __global__ void k_self_ops(int N, double d, Curve cv, cplx alpha, double ka, dou
             v.y += h * sp * Kr[q].y;
             out[q] = v;
         }
-        out[1].x += 1.0;   // I + D
+        out[1].x += 0.5 * (wa + wb);   // (wa + wb)/2 I + D
         out[2].x -= 1.0;   // -I + N
     }
     A[(size_t)(col_sig + j) * lda + row_v + i] = out[0];
@@ -234,9 +245,10 @@ __global__ void k_potentials(Targets tg, Curve cv, int S, double k, int nsh, dou
     p = &A[(size_t)(col_sig + s) * lda + rn]; *p = cadd(*p, cscale(aN, f));
 }
 
-// J-expansion columns: coef * (J_n(k|x-x0|) e^{in theta}, its normal derivative), n = -Q..Q,
-// using d_x f_n = (k/2)(f_{n-1} - f_{n+1}), d_y f_n = (ik/2)(f_{n-1} + f_{n+1}).
-__global__ void k_jexp(Targets tg, double cx, double cy, double k, int Q, cplx coef, cplx *A, int lda,
+// J-expansion columns: coef * J_n(k|x-x0|) e^{in theta} in the value rows and coef_n * its normal
+// derivative in the derivative rows, n = -Q..Q, using d_x f_n = (k/2)(f_{n-1} - f_{n+1}),
+// d_y f_n = (ik/2)(f_{n-1} + f_{n+1}).
+__global__ void k_jexp(Targets tg, double cx, double cy, double k, int Q, cplx coef, cplx coef_n, cplx *A, int lda,
                        int row_v, int row_n, int col0) {
     long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
     int nq = 2 * Q + 1;
@@ -253,7 +265,7 @@ __global__ void k_jexp(Targets tg, double cx, double cy, double k, int Q, cplx c
     cplx dn = cadd(cscale(fx, nx), cscale(fy, ny));
     cplx *p;
     p = &A[(size_t)(col0 + n + Q) * lda + row_v + t];  *p = cadd(*p, cmul(coef, f[1]));
-    p = &A[(size_t)(col0 + n + Q) * lda + row_n + t];  *p = cadd(*p, cmul(coef, dn));
+    p = &A[(size_t)(col0 + n + Q) * lda + row_n + t];  *p = cadd(*p, cmul(coef_n, dn));
 }
 
 // Rayleigh-Bloch columns on Gamma_u (top=1) or Gamma_d (top=0):
@@ -270,12 +282,13 @@ __global__ void k_rb(int nb, const double *bx, int K, const double *kappa, const
     A[(size_t)(col0 + n) * lda + row_n + t] = top ? cscale(ike, -1.0) : ike;
 }
 
-__global__ void k_rhs(int N, Curve cv, double kx, double ky, cplx *f, int row_v, int row_n) {
+// f = -u_inc on the Gamma1 value rows and -(1/w1) d_n u_inc on its flux rows (w1 = 1 for TM)
+__global__ void k_rhs(int N, Curve cv, double kx, double ky, double inv_w1, cplx *f, int row_v, int row_n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     cplx u = cexpi(kx * cv.px[i] + ky * cv.py[i]);
     f[row_v + i] = cscale(u, -1.0);
-    f[row_n + i] = cscale(cmuli(u), -(kx * cv.nx[i] + ky * cv.ny[i]));
+    f[row_n + i] = cscale(cmuli(u), -inv_w1 * (kx * cv.nx[i] + ky * cv.ny[i]));
 }
 
 __global__ void k_angle_scalars(int K, double k1, double k3, double kappa0, double d, double *kappa,
@@ -296,21 +309,37 @@ __global__ void k_angle_scalars(int K, double k1, double k3, double kappa0, doub
 
 // ---- disks ----------------------------------------------------------------------------------
 
-// s_n = [kp J_n'(b) J_n(a) - k2 J_n(b) J_n'(a)] / [k2 J_n(b) H_n'(a) - kp J_n'(b) H_n(a)],
-// a = k2 R, b = kp R (continuity of u and d_r u at the disk boundary, Sec. 4.1).
-__global__ void k_mie(int M, int p, const double *radius, const double *kp, double k2, cplx *s) {
+// s_n = [wp J_n'(b) J_n(a) - w2 J_n(b) J_n'(a)] / [w2 J_n(b) H_n'(a) - wp J_n'(b) H_n(a)],
+// a = k2 R, b = kp R: continuity of u and of w d_r u at the disk boundary (Sec. 4.1), the radial
+// derivative weights (wp, w2) = (kp, k2) for TM and (1/kp, 1/k2) for TE (1/eps ~ 1/k^2 times
+// d_r J_n(k r) = k J_n').  kp_im (nullable) holds Im kp of lossy inclusions: then J_n(b) is
+// complex (power series).
+__global__ void k_mie(int M, int p, const double *radius, const double *kp, const double *kp_im, double k2, int te,
+                      cplx *s) {
     int id = blockIdx.x * blockDim.x + threadIdx.x;
     int nc = 2 * p + 1;
     if (id >= M * nc) return;
     int i = id / nc, n = id % nc - p;
-    double a = k2 * radius[i], b = kp[i] * radius[i];
-    double Ja = besselj_int(n, a), Jb = besselj_int(n, b);
-    double Jpa = 0.5 * (besselj_int(n - 1, a) - besselj_int(n + 1, a));
-    double Jpb = 0.5 * (besselj_int(n - 1, b) - besselj_int(n + 1, b));
+    const double R = radius[i], a = k2 * R;
+    const cplx kpc = C(kp[i], kp_im ? kp_im[i] : 0.0);
+    const double Ja = besselj_int(n, a);
+    const double Jpa = 0.5 * (besselj_int(n - 1, a) - besselj_int(n + 1, a));
+    cplx Jb, Jpb;
+    if (kpc.y != 0.0) {
+        const cplx b = cscale(kpc, R);
+        Jb = besselj_cplx(n, b);
+        Jpb = cscale(csub(besselj_cplx(n - 1, b), besselj_cplx(n + 1, b)), 0.5);
+    } else {
+        const double b = kpc.x * R;
+        Jb = C(besselj_int(n, b), 0.0);
+        Jpb = C(0.5 * (besselj_int(n - 1, b) - besselj_int(n + 1, b)), 0.0);
+    }
     cplx Ha = C(Ja, bessely_int(n, a));
     cplx Hpa = C(Jpa, 0.5 * (bessely_int(n - 1, a) - bessely_int(n + 1, a)));
-    cplx num = C(kp[i] * Jpb * Ja - k2 * Jb * Jpa, 0.0);
-    cplx den = csub(cscale(Hpa, k2 * Jb), cscale(Ha, kp[i] * Jpb));
+    const cplx wp = te ? cdiv(C(1.0, 0.0), kpc) : kpc;
+    const double w2 = te ? 1.0 / k2 : k2;
+    const cplx num = csub(cscale(cmul(wp, Jpb), Ja), cscale(Jb, w2 * Jpa));
+    const cplx den = csub(cscale(cmul(Hpa, Jb), w2), cmul(cmul(wp, Jpb), Ha));
     s[id] = cdiv(num, den);
 }
 
@@ -516,10 +545,13 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
     cplx one = C(1, 0);
     cplx al2 = cmul(al, al), mai = cscale(ai, -1.0);
     double x1c = 0.0, y1c = 0.5 * (L.h1_0 + L.y0), y2c = 0.5 * (L.h1_0 + L.h2_0), y3c = 0.5 * (L.h2_0 - L.y0);
+    // TE: the top and bottom layers' potentials carry w1, w3 and their flux rows 1/w1, 1/w3
+    double w1, w3;
+    gs_layer_weights(c, &w1, &w3);
 
     // Gamma1 rows: u1 - u2 = -u_inc (Eq. bound1)
     GS_COUNT_LAUNCH(c);
-    k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c1, al, L.k1, L.k2, c->kress, A, lda,
+    k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c1, al, L.k1, L.k2, w1, 1.0, c->kress, A, lda,
                                                    ly.row_g1v, ly.row_g1n, ly.col_mu1, ly.col_sig1);
     Targets t1 = curve_targets(c1, N), t2 = curve_targets(c2, N);
     GS_COUNT_LAUNCH(c);
@@ -527,25 +559,25 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
                                                      A, lda, ly.row_g1v, ly.row_g1n, ly.col_mu2,
                                                      ly.col_sig2);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t1, x1c, y2c, L.k2, ly.Q2, C(-1, 0), A, lda,
+    k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t1, x1c, y2c, L.k2, ly.Q2, C(-1, 0), C(-1, 0), A, lda,
                                                             ly.row_g1v, ly.row_g1n, ly.col_a2);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)N * (2 * ly.Q1 + 1)), TPB, 0, st>>>(t1, x1c, y1c, L.k1, ly.Q1, one, A, lda,
+    k_jexp<<<nblk((long)N * (2 * ly.Q1 + 1)), TPB, 0, st>>>(t1, x1c, y1c, L.k1, ly.Q1, one, C(1.0 / w1, 0), A, lda,
                                                             ly.row_g1v, ly.row_g1n, ly.col_a1);
     // Gamma2 rows: u2 - u3 = 0
     GS_COUNT_LAUNCH(c);
-    k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c2, al, L.k2, L.k3, c->kress, A, lda,
+    k_self_ops<<<nblk((long)N * N), TPB, 0, st>>>(N, d, c2, al, L.k2, L.k3, 1.0, w3, c->kress, A, lda,
                                                    ly.row_g2v, ly.row_g2n, ly.col_mu2, ly.col_sig2);
     GS_COUNT_LAUNCH(c);
     k_potentials<<<nblk((long)N * N), TPB, 0, st>>>(t2, c1, N, L.k2, 3, -d, 0.0, d, ai, one, al, 1.0, A,
                                                      lda, ly.row_g2v, ly.row_g2n, ly.col_mu1,
                                                      ly.col_sig1);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t2, x1c, y2c, L.k2, ly.Q2, one, A, lda,
+    k_jexp<<<nblk((long)N * (2 * ly.Q2 + 1)), TPB, 0, st>>>(t2, x1c, y2c, L.k2, ly.Q2, one, one, A, lda,
                                                             ly.row_g2v, ly.row_g2n, ly.col_a2);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)N * (2 * ly.Q3 + 1)), TPB, 0, st>>>(t2, x1c, y3c, L.k3, ly.Q3, C(-1, 0), A, lda,
-                                                            ly.row_g2v, ly.row_g2n, ly.col_a3);
+    k_jexp<<<nblk((long)N * (2 * ly.Q3 + 1)), TPB, 0, st>>>(t2, x1c, y3c, L.k3, ly.Q3, C(-1, 0), C(-1.0 / w3, 0), A,
+                                                            lda, ly.row_g2v, ly.row_g2n, ly.col_a3);
     // walls (Eq. bound2, cancelled form for the layer potentials)
     struct WallJob {
         int nw;
@@ -553,10 +585,11 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
         int rv, rn;
         double k, cy;
         int Q, col;
+        double w;   // TE weight of the layer's potentials
     };
-    WallJob wj[3] = {{ly.nw2, c->wall_y[1], ly.row_w2v, ly.row_w2n, L.k2, y2c, ly.Q2, ly.col_a2},
-                     {ly.nw1, c->wall_y[0], ly.row_w1v, ly.row_w1n, L.k1, y1c, ly.Q1, ly.col_a1},
-                     {ly.nw3, c->wall_y[2], ly.row_w3v, ly.row_w3n, L.k3, y3c, ly.Q3, ly.col_a3}};
+    WallJob wj[3] = {{ly.nw2, c->wall_y[1], ly.row_w2v, ly.row_w2n, L.k2, y2c, ly.Q2, ly.col_a2, 1.0},
+                     {ly.nw1, c->wall_y[0], ly.row_w1v, ly.row_w1n, L.k1, y1c, ly.Q1, ly.col_a1, w1},
+                     {ly.nw3, c->wall_y[2], ly.row_w3v, ly.row_w3n, L.k3, y3c, ly.Q3, ly.col_a3, w3}};
     for (int q = 0; q < 3; ++q) {
         const WallJob &w = wj[q];
         Targets TL = wall_targets(w.ys, w.nw, -0.5 * d), TR = wall_targets(w.ys, w.nw, 0.5 * d);
@@ -564,40 +597,40 @@ int gs_assemble_A(gs_ctx *c, const AngleData &a, cplx *A, int lda) {
         if (has1) {
             GS_COUNT_LAUNCH(c);
             k_potentials<<<nblk((long)w.nw * N), TPB, 0, st>>>(TL, c1, N, w.k, 2, d, -2.0 * d, 0.0, al2,
-                                                                mai, one, 1.0, A, lda, w.rv, w.rn,
+                                                                mai, one, w.w, A, lda, w.rv, w.rn,
                                                                 ly.col_mu1, ly.col_sig1);
         }
         if (has2) {
             GS_COUNT_LAUNCH(c);
             k_potentials<<<nblk((long)w.nw * N), TPB, 0, st>>>(TL, c2, N, w.k, 2, d, -2.0 * d, 0.0, al2,
-                                                                mai, one, 1.0, A, lda, w.rv, w.rn,
+                                                                mai, one, w.w, A, lda, w.rv, w.rn,
                                                                 ly.col_mu2, ly.col_sig2);
         }
         GS_COUNT_LAUNCH(c);
-        k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TL, x1c, w.cy, w.k, w.Q, al, A, lda, w.rv,
+        k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TL, x1c, w.cy, w.k, w.Q, al, al, A, lda, w.rv,
                                                                  w.rn, w.col);
         GS_COUNT_LAUNCH(c);
-        k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TR, x1c, w.cy, w.k, w.Q, C(-1, 0), A,
+        k_jexp<<<nblk((long)w.nw * (2 * w.Q + 1)), TPB, 0, st>>>(TR, x1c, w.cy, w.k, w.Q, C(-1, 0), C(-1, 0), A,
                                                                  lda, w.rv, w.rn, w.col);
     }
     // Gamma_u / Gamma_d (Eq. bound3)
     Targets tu = bound_targets(c->bound_x, ly.nb, L.y0), td = bound_targets(c->bound_x, ly.nb, -L.y0);
     GS_COUNT_LAUNCH(c);
-    k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(tu, c1, N, L.k1, 3, -d, 0.0, d, ai, one, al, 1.0,
+    k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(tu, c1, N, L.k1, 3, -d, 0.0, d, ai, one, al, w1,
                                                          A, lda, ly.row_uv, ly.row_un, ly.col_mu1,
                                                          ly.col_sig1);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)ly.nb * (2 * ly.Q1 + 1)), TPB, 0, st>>>(tu, x1c, y1c, L.k1, ly.Q1, one, A, lda,
+    k_jexp<<<nblk((long)ly.nb * (2 * ly.Q1 + 1)), TPB, 0, st>>>(tu, x1c, y1c, L.k1, ly.Q1, one, one, A, lda,
                                                                 ly.row_uv, ly.row_un, ly.col_a1);
     GS_COUNT_LAUNCH(c);
     k_rb<<<nblk(ly.nb * (2 * ly.K + 1)), TPB, 0, st>>>(ly.nb, c->bound_x, ly.K, a.kappa, a.k1n, 1, A, lda,
                                                       ly.row_uv, ly.row_un, ly.col_c);
     GS_COUNT_LAUNCH(c);
-    k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(td, c2, N, L.k3, 3, -d, 0.0, d, ai, one, al, 1.0,
+    k_potentials<<<nblk((long)ly.nb * N), TPB, 0, st>>>(td, c2, N, L.k3, 3, -d, 0.0, d, ai, one, al, w3,
                                                          A, lda, ly.row_dv, ly.row_dn, ly.col_mu2,
                                                          ly.col_sig2);
     GS_COUNT_LAUNCH(c);
-    k_jexp<<<nblk((long)ly.nb * (2 * ly.Q3 + 1)), TPB, 0, st>>>(td, x1c, y3c, L.k3, ly.Q3, one, A, lda,
+    k_jexp<<<nblk((long)ly.nb * (2 * ly.Q3 + 1)), TPB, 0, st>>>(td, x1c, y3c, L.k3, ly.Q3, one, one, A, lda,
                                                                 ly.row_dv, ly.row_dn, ly.col_a3);
     GS_COUNT_LAUNCH(c);
     k_rb<<<nblk(ly.nb * (2 * ly.K + 1)), TPB, 0, st>>>(ly.nb, c->bound_x, ly.K, a.kappa, a.k3n, 0, A, lda,
@@ -611,20 +644,22 @@ int gs_assemble_f(gs_ctx *c, const AngleData &a, cplx *f) {
     GS_CUDA(c, cudaMemsetAsync(f, 0, sizeof(cplx) * ly.rows, c->stream));
     Curve c1 = curve_of(c->curve[0], c->L.N);
     GS_COUNT_LAUNCH(c);
-    k_rhs<<<nblk(c->L.N), TPB, 0, c->stream>>>(c->L.N, c1, a.kappa0, c->L.k1 * sin(a.theta), f, ly.row_g1v,
+    double w1, w3;
+    gs_layer_weights(c, &w1, &w3);
+    k_rhs<<<nblk(c->L.N), TPB, 0, c->stream>>>(c->L.N, c1, a.kappa0, c->L.k1 * sin(a.theta), 1.0 / w1, f, ly.row_g1v,
                                                 ly.row_g1n);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
 
-int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, cplx *s) {
+int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, const double *kp_im, cplx *s) {
     GS_COUNT_LAUNCH(c);
-    k_mie<<<nblk(M * c->nc), TPB, 0, c->stream>>>(M, c->p, radius, kp, c->L.k2, s);
+    k_mie<<<nblk(M * c->nc), TPB, 0, c->stream>>>(M, c->p, radius, kp, kp_im, c->L.k2, c->pol != 0, s);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
 
-int gs_mie(gs_ctx *c) { return gs_mie_geo(c, c->M, c->radius, c->kp, c->s); }
+int gs_mie(gs_ctx *c) { return gs_mie_geo(c, c->M, c->radius, c->kp, c->kp_im, c->s); }
 
 int gs_assemble_B_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *B) {
     const Layout &ly = c->lay;

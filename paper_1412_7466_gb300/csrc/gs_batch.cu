@@ -358,12 +358,14 @@ __global__ void k_b_f_minus_Cx(const cplx *__restrict__ Cg, int nC, int n, const
     if (lane == 0) gout[warp] = csub(f[warp], s);
 }
 
-__global__ void k_b_flux(int K, const cplx *cd, const cplx *k1n, const cplx *k3n, double inc, double *out) {
+// relative flux error of one geometry's Bragg amplitudes (TE weights 1/w1, 1/w3; 1 for TM)
+__global__ void k_b_flux(int K, const cplx *cd, const cplx *k1n, const cplx *k3n, double inv_w1, double inv_w3,
+                         double inc, double *out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s = 0.0;
     for (int n = 0; n < 2 * K + 1; ++n) {
-        if (k1n[n].y == 0.0 && k1n[n].x > 0.0) s += k1n[n].x * cabs2(cd[n]);
-        if (k3n[n].y == 0.0 && k3n[n].x > 0.0) s += k3n[n].x * cabs2(cd[2 * K + 1 + n]);
+        if (k1n[n].y == 0.0 && k1n[n].x > 0.0) s += inv_w1 * k1n[n].x * cabs2(cd[n]);
+        if (k3n[n].y == 0.0 && k3n[n].x > 0.0) s += inv_w3 * k3n[n].x * cabs2(cd[2 * K + 1 + n]);
     }
     out[0] = fabs(s - inc) / inc;
 }
@@ -927,7 +929,7 @@ int gs_factor_batch(gs_ctx *c) {
     // coupling per geometry and angle
     GS_TRY(dalloc_b(c, &b->s, N));
     for (int g = 0; g < G; ++g)
-        GS_TRY(gs_mie_geo(c, b->M[g], b->radius + b->moff[g], b->kp + b->moff[g], b->s + b->noff[g]));
+        GS_TRY(gs_mie_geo(c, b->M[g], b->radius + b->moff[g], b->kp + b->moff[g], nullptr, b->s + b->noff[g]));
     std::vector<size_t> coff(G);
     size_t o = 0;
     for (int g = 0; g < G; ++g) {
@@ -1158,7 +1160,9 @@ int gs_bragg_batch(gs_ctx *c, int angle, int g, int *n_top, int *orders_top, gs_
     k_batch_V<<<wblk(ncd), 256, 0, st>>>(a.Vr + (size_t)ly.col_c * ly.cols, ncd, ly.cols, wbuf, a.dscale + ly.col_c, 1,
                                          nullptr, xbuf);
     GS_COUNT_LAUNCH(c);
-    k_b_flux<<<1, 1, 0, st>>>(K, xbuf, a.k1n, a.k3n, c->L.k1 * fabs(sin(a.theta)), fl);
+    double w1, w3;
+    gs_layer_weights(c, &w1, &w3);
+    k_b_flux<<<1, 1, 0, st>>>(K, xbuf, a.k1n, a.k3n, 1.0 / w1, 1.0 / w3, c->L.k1 * fabs(sin(a.theta)) / w1, fl);
     GS_CHECK_LAUNCH(c);
     double flux = 0;
     GS_CUDA(c, cudaMemcpyAsync(cd.data(), xbuf, sizeof(cplx) * ncd, cudaMemcpyDeviceToHost, st));

@@ -80,6 +80,24 @@ __device__ inline double besselj_int(int n, double x) {
     return (n < 0 && (an & 1)) ? -r : r;
 }
 // Y_n(x) for any integer n (Y_{-n} = (-1)^n Y_n).
+// J_n(z) of complex argument by its power series sum_k (-z^2/4)^k (z/2)^|n| / (k! (|n|+k)!)
+// (DLMF 10.2.2), for the disk coefficients of lossy inclusions: terms peak near k ~ |z|/2, so for
+// |z| <= 12 the cancellation costs at most ~1e3 units of the last place; callers keep |z| there.
+__device__ inline cplx besselj_cplx(int n, cplx z) {
+    const int an = n < 0 ? -n : n;
+    const cplx h = cscale(z, 0.5);
+    cplx lead = C(1.0, 0.0);                    // (z/2)^|n| / |n|!
+    for (int q = 1; q <= an; ++q) lead = cscale(cmul(lead, h), 1.0 / q);
+    const cplx w = cscale(cmul(h, h), -1.0);    // -z^2/4
+    cplx term = lead, sum = lead;
+    for (int k = 1; k < 200; ++k) {
+        term = cscale(cmul(term, w), 1.0 / ((double)k * (double)(an + k)));
+        sum = cadd(sum, term);
+        if (cabs2(term) < 1e-36 * cabs2(sum)) break;
+    }
+    return (n < 0 && (an & 1)) ? cscale(sum, -1.0) : sum;
+}
+
 __device__ __forceinline__ double bessely_int(int n, double x) {
     if (n >= 0) return yn(n, x);
     double v = yn(-n, x);

@@ -5,9 +5,10 @@
 //       + sum_q a2_q J_q(k2 |x - x2|) e^{i q theta}                                        (far copies)
 //       + sum_j sum_l alpha^l sum_n beta^j_n H_n(k2 |x - c_j - l d|) e^{i n theta}          (inclusions)
 //   top, below Gamma_u (Eq. repre1): u_inc + the potentials of Gamma1's densities at k1 (near
-//     copies) + sum_q a1_q J_q(k1 |x - x1|) e^{i q theta};  above (Eq. rad1):
+//     copies; times w1 = (k1/k2)^2 in TE polarisation) + sum_q a1_q J_q(k1 |x - x1|) e^{i q theta};
+//     above (Eq. rad1):
 //     u_inc + sum_n c_n e^{i (kappa_n x + k_{1,n} (y - y0))}
-//   bottom, above Gamma_d (Eq. repre2): the potentials of Gamma2's densities at k3 +
+//   bottom, above Gamma_d (Eq. repre2): the potentials of Gamma2's densities at k3 (times w3 in TE) +
 //     sum_q a3_q J_q(k3 |x - x3|) e^{i q theta};  below (Eq. rad2): sum_n d_n e^{i (kappa_n x - k_{3,n} (y + y0))}
 // One thread per point, FP64 throughout: interface sums by the plain trapezoid rule (accurate a few
 // node spacings away from the interfaces), J_q by Miller's backward recurrence accumulated on the
@@ -25,6 +26,7 @@ struct FieldArgs {
     const double *four;           // [h1_cos, h1_sin, h2_cos, h2_sin], nfa each
     int nf, nfa;
     double h1_0, h2_0, d, k1, k2, k3, y0, ycen, ycen1, ycen3, kx, ky;   // kx, ky: incident wave vector
+    double w1, w3;                // TE weights of the top and bottom layers' potentials (1 for TM)
     cplx alpha;
     const cplx *a;                // layer unknowns (cols)
     int col_mu1, col_sig1, col_mu2, col_sig2, col_a2, Q2, col_a1, Q1, col_a3, Q3, col_c, col_d, K;
@@ -145,13 +147,13 @@ __global__ void k_field(FieldArgs A, long npts, const double *__restrict__ pts, 
     }
     if (y > top) {
         const double Ry = y - A.ycen1;
-        cplx acc = cadd(uinc, layer_potentials(A, 0, A.k1, x, y));
+        cplx acc = cadd(uinc, cscale(layer_potentials(A, 0, A.k1, x, y), A.w1));
         u[t] = cadd(acc, jexp_sum(A.a + A.col_a1, A.Q1, A.k1 * hypot(x, Ry), atan2(Ry, x)));
         return;
     }
     if (y < bot) {
         const double Ry = y - A.ycen3;
-        const cplx acc = layer_potentials(A, 1, A.k3, x, y);
+        const cplx acc = cscale(layer_potentials(A, 1, A.k3, x, y), A.w3);
         u[t] = cadd(acc, jexp_sum(A.a + A.col_a3, A.Q3, A.k3 * hypot(x, Ry), atan2(Ry, x)));
         return;
     }
@@ -231,6 +233,7 @@ extern "C" int gs_field(gs_ctx *c, int angle, long npts, const double *xy_dev, g
     A.ycen = 0.5 * (c->L.h1_0 + c->L.h2_0);
     A.ycen1 = 0.5 * (c->L.h1_0 + c->L.y0);
     A.ycen3 = 0.5 * (c->L.h2_0 - c->L.y0);
+    gs_layer_weights(c, &A.w1, &A.w3);
     A.kx = a.kappa0;
     A.ky = c->L.k1 * std::sin(a.theta);
     A.col_a1 = ly.col_a1;

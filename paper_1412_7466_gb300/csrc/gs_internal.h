@@ -74,6 +74,9 @@ struct gs_ctx {
     double yL1 = 0, yL2 = 0;                 // interface heights at the walls
     double h1_min = 0, h2_max = 0;
 
+    // polarisation (GS_TM or GS_TE)
+    int pol = 0;
+
     // incidence
     std::vector<double> thetas;
 
@@ -81,6 +84,8 @@ struct gs_ctx {
     bool have_inc = false;
     int M = 0, p = 0, nc = 0;
     double *xy = nullptr, *radius = nullptr, *kp = nullptr;
+    double *kp_im = nullptr;                 // Im kp of lossy inclusions (null: all lossless)
+    std::vector<double> radius_h, kp_h;      // host copies of the radii and Re kp
     cplx *s = nullptr;                       // M x nc
 
     bool grating_ready = false;   // per-angle factorisation of the empty grating is built
@@ -141,6 +146,13 @@ struct gs_ctx {
     int n() const { return M * nc; }
 };
 
+// TE weights w1 = (k1/k2)^2, w3 = (k3/k2)^2 of the top and bottom layers (1, 1 for TM)
+inline void gs_layer_weights(const gs_ctx *c, double *w1, double *w3) {
+    const bool te = c->pol != 0;
+    *w1 = te ? (c->L.k1 / c->L.k2) * (c->L.k1 / c->L.k2) : 1.0;
+    *w3 = te ? (c->L.k3 / c->L.k2) * (c->L.k3 / c->L.k2) : 1.0;
+}
+
 void gs_batch_destroy(gs_ctx *c);
 void gs_angles_destroy(gs_ctx *c);
 void gs_mlp_destroy(gs_ctx *c);
@@ -174,7 +186,7 @@ int gs_mie(gs_ctx *c);
 int gs_assemble_B(gs_ctx *c, const AngleData &a, cplx *B);
 int gs_assemble_C(gs_ctx *c, const AngleData &a, cplx *Cm);
 // the same for an explicit geometry (M disks at xy; the multipole order is the context's)
-int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, cplx *s);
+int gs_mie_geo(gs_ctx *c, int M, const double *radius, const double *kp, const double *kp_im, cplx *s);
 int gs_assemble_B_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *B);
 int gs_assemble_C_geo(gs_ctx *c, const AngleData &a, int M, const double *xy, cplx *Cm);
 // per-angle grating factorisation if not built yet (gs_api.cu)

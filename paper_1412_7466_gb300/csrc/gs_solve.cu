@@ -322,13 +322,15 @@ __global__ void k_set_g0(cplx *g, int len, const double *beta) {
     if (i < len) g[i] = C(i == 0 ? beta[0] : 0.0, 0.0);
 }
 
-// Bragg amplitudes and flux error (single block): c_n = x_c[n], d_n = x_d[n] for propagating orders.
-__global__ void k_flux(int K, const cplx *cd, const cplx *k1n, const cplx *k3n, double inc, double *out) {
+// Bragg amplitudes and flux error (single block): c_n = x_c[n], d_n = x_d[n] for propagating orders;
+// the vertical energy fluxes carry 1/w1, 1/w3 in TE (w = 1 for TM), inc = k1 |sin theta| / w1.
+__global__ void k_flux(int K, const cplx *cd, const cplx *k1n, const cplx *k3n, double inv_w1, double inv_w3,
+                       double inc, double *out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s = 0.0;
     for (int n = 0; n < 2 * K + 1; ++n) {
-        if (k1n[n].y == 0.0 && k1n[n].x > 0.0) s += k1n[n].x * cabs2(cd[n]);
-        if (k3n[n].y == 0.0 && k3n[n].x > 0.0) s += k3n[n].x * cabs2(cd[2 * K + 1 + n]);
+        if (k1n[n].y == 0.0 && k1n[n].x > 0.0) s += inv_w1 * k1n[n].x * cabs2(cd[n]);
+        if (k3n[n].y == 0.0 && k3n[n].x > 0.0) s += inv_w3 * k3n[n].x * cabs2(cd[2 * K + 1 + n]);
     }
     out[0] = fabs(s - inc) / inc;
 }
@@ -815,9 +817,11 @@ int gs_bragg_impl(gs_ctx *c, const AngleData &a, cplx *cd_host, double *flux) {
     GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(ncd), 256, 0, c->stream>>>(a.Vr + (size_t)ly.col_c * ly.cols, ncd, ly.cols, ly.cols,
                                                           c->w, a.dscale + ly.col_c, c->x);
-    double inc = c->L.k1 * fabs(sin(a.theta));
+    double w1, w3;
+    gs_layer_weights(c, &w1, &w3);
+    double inc = c->L.k1 * fabs(sin(a.theta)) / w1;
     GS_COUNT_LAUNCH(c);
-    k_flux<<<1, 1, 0, c->stream>>>(ly.K, c->x, a.k1n, a.k3n, inc, c->dscal + 4);
+    k_flux<<<1, 1, 0, c->stream>>>(ly.K, c->x, a.k1n, a.k3n, 1.0 / w1, 1.0 / w3, inc, c->dscal + 4);
     GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaMemcpyAsync(cd_host, c->x, sizeof(cplx) * ncd, cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaMemcpyAsync(flux, c->dscal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
