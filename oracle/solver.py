@@ -26,7 +26,7 @@ class Problem:
     eg: lay.EmptyGrating
     pinv: lay.PInv
     disks: dict
-    s: np.ndarray        # (M, nc) disk scattering diagonal
+    s: np.ndarray        # (M, nc) disk scattering diagonal, or (M, nc, nc) blocks of general shapes
     B: np.ndarray        # B_phys, (M nc, ncols of A)
     C: np.ndarray        # (nrows of A, M nc)
     timings: dict
@@ -39,21 +39,26 @@ class Problem:
     def nc(self):
         return 2 * self.disks["p"] + 1
 
+    def apply_s(self, v):
+        """S v: the diagonal (disks) or the per-inclusion blocks (general shapes, Sec. 4.2), for a
+        vector or for the columns of a matrix."""
+        V = v.reshape(self.M, self.nc, -1)
+        out = self.s[:, :, None] * V if self.s.ndim == 2 else np.einsum("imn,inr->imr", self.s, V)
+        return out.reshape(v.shape)
+
     def lowrank(self, beta):
         """S B_phys A^+ C beta (the Schur-complement correction, Sec. 5)."""
-        z = self.B @ self.pinv.apply(self.C @ beta)
-        return (self.s.reshape(-1, *([1] * (z.ndim - 1))) * z.reshape(self.M * self.nc, -1)
-                ).reshape(z.shape) if z.ndim > 1 else self.s.ravel() * z
+        return self.apply_s(self.B @ self.pinv.apply(self.C @ beta))
 
     def rhs(self):
-        return self.s.ravel() * (self.B @ self.pinv.apply(self.eg.f))
+        return self.apply_s(self.B @ self.pinv.apply(self.eg.f))
 
     def translate(self, beta):
         return translation_apply(self.disks, self.eg.k[1], self.eg.d, self.eg.alpha, beta)
 
     def apply(self, beta):
         """L beta = beta - S (T beta) + S B_phys A^+ C beta."""
-        return beta - self.s.ravel() * self.translate(beta) + self.lowrank(beta)
+        return beta - self.apply_s(self.translate(beta)) + self.lowrank(beta)
 
     def recover(self, beta):
         """alpha = A^+ (f - C beta) (Sec. 5) and the Bragg amplitudes / flux error (Sec. 6)."""
@@ -67,7 +72,11 @@ def setup(g: dict, theta: float, disks: dict, eps=None, lapack_driver="gesdd") -
     t1 = time.perf_counter()
     pinv = lay.factor(eg, eps=eps, lapack_driver=lapack_driver)
     t2 = time.perf_counter()
-    s = inc.scattering_diagonal(disks, eg.k[1], g.get("pol", "TM"))
+    if "shape" in disks:
+        from . import shapes
+        s = shapes.scattering_blocks(disks, eg.k[1], g.get("pol", "TM"))
+    else:
+        s = inc.scattering_diagonal(disks, eg.k[1], g.get("pol", "TM"))
     B = inc.coupling_B(eg, disks)
     C = inc.coupling_C(eg, disks)
     t3 = time.perf_counter()
@@ -95,8 +104,7 @@ def translation_apply(disks, k, d, alpha, beta):
 def dense_operator(prob: Problem) -> np.ndarray:
     T = inc.translation_matrix(prob.disks["xy"], prob.eg.k[1], prob.disks["p"], prob.eg.d, prob.eg.alpha)
     BAC = prob.B @ prob.pinv.apply(prob.C)
-    s = prob.s.ravel()
-    return np.eye(T.shape[0]) - s[:, None] * T + s[:, None] * BAC
+    return np.eye(T.shape[0]) - prob.apply_s(T) + prob.apply_s(BAC)
 
 
 def solve_dense(prob: Problem):
