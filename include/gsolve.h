@@ -64,6 +64,36 @@ typedef struct {
     double eps_pinv;
 } gs_layers;
 
+/* Inclusions of one general shape (Sec. 4.1, 4.2): the star r(t) = a1 + a2 cos(a3 t), t in
+ * [0, 2 pi) (Eq. par1), rotated counter-clockwise by phi[i] about the centre xy[2i], xy[2i+1] (host
+ * arrays, copied), interior wavenumber kp (real), multipole order p.  gs_factor then computes the
+ * star's (2p+1) x (2p+1) scattering matrix s_ln on the GPU from the second-kind boundary integral
+ * equation of Eqs. intg1-intg2 on n_nodes equispaced boundary nodes (Kress's product rule for the
+ * log-singular kernel differences; TE scales the interior potentials by (kp/k2)^2), solved by
+ * Gaussian elimination with partial pivoting for the 2p+1 incident orders J_n(k2 r) e^{i n theta},
+ * and the moment integral s_ln = (i/4) int [J_l(k2 r) e^{-i l theta} sigma_n + d_n(J_l(k2 r)
+ * e^{-i l theta}) mu_n] ds; inclusion i gets e^{i phi_i (n - l)} s_ln (a counter-clockwise rotation;
+ * the paper prints e^{i phi (l - n)} with the angle measured the other way).  The preconditioner S
+ * becomes block diagonal (these blocks) in every single-geometry solve (FP64, mixed, many angles).
+ * The geometry checks and the multipole expansions use the enclosing disks of radius a1 + |a2|,
+ * which must not overlap (Sec. 4.2).  GS_ERR_ARG unless a1 > |a2|, 0 <= a3 <= 64, kp > 0 and
+ * n_nodes even in [16, 1024]; GS_ERR_GEOMETRY as gs_set_inclusions.  Batched solves and the
+ * learned warm start take disks only. */
+typedef struct {
+    int M;
+    int p;
+    const double *xy;
+    const double *phi;
+    double a1, a2;
+    int a3;
+    double kp;
+    int n_nodes;
+} gs_star_inclusions;
+int gs_set_inclusions_star(gs_ctx *ctx, const gs_star_inclusions *inc);
+/* The preconditioner's blocks S_i (M x (2p+1) x (2p+1), [i][l][n], device, caller-owned): the
+ * rotated star matrices, or the diagonal disk coefficients for disks.  Needs gs_factor. */
+int gs_get_scattering_blocks(gs_ctx *ctx, gs_c128 *S_dev);
+
 /* Polarisation (Sec. 2): GS_TM (default, u the electric field; [u] = [d_n u] = 0 on the interfaces)
  * or GS_TE (u the magnetic field; [u] = [(1/eps) d_n u] = 0, eps_j proportional to k_j^2 for a
  * constant permeability; Sec. 7 leaves it to future work).  TE scales each layer's potentials by its

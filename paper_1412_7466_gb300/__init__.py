@@ -53,6 +53,11 @@ class gs_inclusions(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("p", ctypes.c_int), ("xy", _dp), ("radius", _dp), ("kp", _dp)]
 
 
+class gs_star_inclusions(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("p", ctypes.c_int), ("xy", _dp), ("phi", _dp), ("a1", ctypes.c_double),
+                ("a2", ctypes.c_double), ("a3", ctypes.c_int), ("kp", ctypes.c_double), ("n_nodes", ctypes.c_int)]
+
+
 class gs_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int)]
@@ -67,6 +72,8 @@ _SIGS = {
     "gs_set_incidence": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "gs_set_inclusions": (ctypes.c_int, [_vp, ctypes.POINTER(gs_inclusions)]),
     "gs_set_polarization": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "gs_set_inclusions_star": (ctypes.c_int, [_vp, ctypes.POINTER(gs_star_inclusions)]),
+    "gs_get_scattering_blocks": (ctypes.c_int, [_vp, _vp]),
     "gs_set_inclusion_loss": (ctypes.c_int, [_vp, _dp]),
     "gs_factor": (ctypes.c_int, [_vp]),
     "gs_dims": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
@@ -266,7 +273,19 @@ class GratingSolver:
         self.thetas = a.copy()
 
     def set_inclusions(self, disks: dict):
-        """Disks {"xy", "radius", "kp", "p"}; a complex kp (Im kp >= 0) makes the disks lossy."""
+        """Disks {"xy", "radius", "kp", "p"}; a complex kp (Im kp >= 0) makes the disks lossy.  With
+        "shape": {"a1", "a2", "a3", "N"} and "phi" (rotation per inclusion), rotated stars of that
+        shape and interior wavenumber kp[0] (gs_set_inclusions_star)."""
+        if "shape" in disks:
+            sh = disks["shape"]
+            xy, pxy = _arr(disks["xy"])
+            ph, pph = _arr(disks["phi"])
+            I = gs_star_inclusions(M=xy.shape[0], p=int(disks["p"]), xy=pxy, phi=pph, a1=float(sh["a1"]),
+                                   a2=float(sh["a2"]), a3=int(sh["a3"]), kp=float(np.real(disks["kp"][0])),
+                                   n_nodes=int(sh["N"]))
+            self._check(self.lib.gs_set_inclusions_star(self.ctx, ctypes.byref(I)), "gs_set_inclusions_star")
+            self.M, self.p = xy.shape[0], int(disks["p"])
+            return
         xy, pxy = _arr(disks["xy"])
         r, pr = _arr(disks["radius"])
         kpc = np.asarray(disks["kp"])
@@ -304,6 +323,13 @@ class GratingSolver:
         Cm = self._cvec(d["nC"] * d["n"])
         self._check(self.lib.gs_get_coupling(self.ctx, angle, _ptr(B), _ptr(Cm)), "gs_get_coupling")
         return B.view(d["n"], d["nB"]), Cm.view(d["nC"], d["n"])
+
+    def get_scattering_blocks(self):
+        """(M, 2p+1, 2p+1) blocks of the preconditioner (the rotated star matrices, or diagonal)."""
+        nc = 2 * self.p + 1
+        t = self._cvec(self.M * nc * nc)
+        self._check(self.lib.gs_get_scattering_blocks(self.ctx, _ptr(t)), "gs_get_scattering_blocks")
+        return t.view(self.M, nc, nc)
 
     def get_scattering(self):
         t = self._cvec(self.dims()["n"])

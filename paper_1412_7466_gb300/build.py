@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsolve.so")
-SOURCES = ["gs_api.cu", "gs_assemble.cu", "gs_svd.cu", "gs_translate.cu", "gs_solve.cu", "gs_probe.cu", "gs_batch.cu", "gs_warm.cu", "gs_tc.cu", "gs_field.cu", "gs_angles.cu"]
+SOURCES = ["gs_api.cu", "gs_assemble.cu", "gs_svd.cu", "gs_translate.cu", "gs_solve.cu", "gs_probe.cu", "gs_batch.cu", "gs_warm.cu", "gs_tc.cu", "gs_field.cu", "gs_angles.cu", "gs_shape.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

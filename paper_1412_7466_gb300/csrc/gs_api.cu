@@ -94,6 +94,7 @@ void free_geometry(gs_ctx *c) {
     dfree(c->v3);
     dfree(c->v4);
     dfree(c->v5);
+    dfree(c->v6);
     dfree(c->part);
     dfree(c->b32);
     dfree(c->img32);
@@ -298,6 +299,9 @@ void gs_destroy(gs_ctx *c) {
     dfree(c->radius);
     dfree(c->kp);
     dfree(c->kp_im);
+    dfree(c->star_phi);
+    dfree(c->S0);
+    dfree(c->Sblk);
     dfree(c->s);
     dfree(c->dscal);
     dfree(c->dcount);
@@ -494,9 +498,57 @@ int gs_set_inclusions(gs_ctx *c, const gs_inclusions *I) {
     GS_CUDA(c, cudaMemcpyAsync(c->kp, I->kp, sizeof(double) * c->M, cudaMemcpyHostToDevice, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     dfree(c->kp_im);   // new inclusions are lossless until gs_set_inclusion_loss
+    dfree(c->star_phi);   // and disks until gs_set_inclusions_star says otherwise
+    dfree(c->S0);
+    dfree(c->Sblk);
+    c->is_star = false;
     c->radius_h.assign(I->radius, I->radius + c->M);
     c->kp_h.assign(I->kp, I->kp + c->M);
     c->have_inc = true;
+    return GS_OK;
+}
+
+int gs_set_inclusions_star(gs_ctx *c, const gs_star_inclusions *I) {
+    CTX_GUARD(c);
+    if (!I || I->M < 1 || !I->xy || !I->phi) return gs_fail(c, GS_ERR_ARG, "need M >= 1, xy and phi");
+    if (!(I->a1 > 0.0) || !(std::fabs(I->a2) < I->a1) || I->a3 < 0 || I->a3 > 64 || !(I->kp > 0.0) ||
+        I->n_nodes < 16 || I->n_nodes > 1024 || (I->n_nodes & 1))
+        return gs_fail(c, GS_ERR_ARG, "star: a1 > |a2|, 0 <= a3 <= 64, kp > 0, n_nodes even in [16, 1024]");
+    for (int i = 0; i < I->M; ++i)
+        if (!std::isfinite(I->phi[i])) return gs_fail(c, GS_ERR_ARG, "non-finite rotation angle");
+    // the enclosing disks (radius a1 + |a2|) carry the geometry checks and the multipole expansions
+    std::vector<double> rad(I->M, I->a1 + std::fabs(I->a2)), kp(I->M, I->kp);
+    gs_inclusions D{I->M, I->p, I->xy, rad.data(), kp.data()};
+    GS_TRY(gs_set_inclusions(c, &D));
+    GS_TRY(dalloc(c, &c->star_phi, c->M));
+    GS_TRY(dalloc(c, &c->Sblk, (size_t)c->M * c->nc * c->nc));
+    GS_CUDA(c, cudaMemcpyAsync(c->star_phi, I->phi, sizeof(double) * c->M, cudaMemcpyHostToDevice, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->star.a1 = I->a1;
+    c->star.a2 = I->a2;
+    c->star.a3 = I->a3;
+    c->star.kp = I->kp;
+    c->star.n_nodes = I->n_nodes;
+    c->is_star = true;
+    return GS_OK;
+}
+
+int gs_get_scattering_blocks(gs_ctx *c, gs_c128 *S_dev) {
+    CTX_GUARD(c);
+    if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
+    if (!S_dev) return gs_fail(c, GS_ERR_ARG, "null output");
+    const long nc = c->nc, M = c->M;
+    if (c->Sblk) {
+        GS_CUDA(c, cudaMemcpyAsync(S_dev, c->Sblk, sizeof(cplx) * M * nc * nc, cudaMemcpyDeviceToDevice, c->stream));
+    } else {   // disks: the diagonal blocks
+        std::vector<cplx> h((size_t)M * nc), out((size_t)M * nc * nc, C(0, 0));
+        GS_CUDA(c, cudaMemcpyAsync(h.data(), c->s, sizeof(cplx) * M * nc, cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (long i = 0; i < M; ++i)
+            for (long m = 0; m < nc; ++m) out[(i * nc + m) * nc + m] = h[i * nc + m];
+        GS_CUDA(c, cudaMemcpyAsync(S_dev, out.data(), sizeof(cplx) * out.size(), cudaMemcpyHostToDevice, c->stream));
+    }
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
     return GS_OK;
 }
 
@@ -545,6 +597,7 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->v3, n));
     GS_TRY(dalloc(c, &c->v4, n));
     GS_TRY(dalloc(c, &c->v5, n));
+    GS_TRY(dalloc(c, &c->v6, n));
     c->part_elems = gs_translate_scratch_elems(c->M, c->p);
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     GS_TRY(dalloc(c, &c->b32, n));
@@ -562,6 +615,7 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->gg, c->kdim + 1));
     GS_TRY(dalloc(c, &c->yy, c->kdim + 1));
     GS_TRY(gs_mie(c));
+    if (c->is_star) GS_TRY(gs_star_blocks(c));
     {
         // translation coefficient table for the FP64 product, when it fits the memory budget
         size_t bytes = sizeof(cplx) * gs_pair_table_elems(c->M, c->p);

@@ -10,6 +10,7 @@
 // neighbours across the period end.  Wall rows use the cancelled form alpha^2 u_{+1}(L) -
 // alpha^{-1} u_{-2}(L).
 #include "gs_internal.h"
+#include "gs_kernels.cuh"
 
 namespace {
 
@@ -85,44 +86,10 @@ __global__ void k_kress(int N, double *R) {
     R[m] = -(4.0 * GS_PI / N) * acc - (4.0 * GS_PI / ((double)N * N)) * ((m & 1) ? -1.0 : 1.0);
 }
 
-// ---- kernels of the layer potentials ----------------------------------------------------------
-
-struct K4 {
-    cplx S, D, N, T;
-};
-
-// S = (i/4) H0(kr); D = (ik/4) H1 R.ny/r; N = -(ik/4) H1 R.nx/r;
-// T = (ik/4)[k H0 R.nx R.ny/r^2 - 2 H1 R.nx R.ny/r^3 + H1 nx.ny/r], R = x - y.
-__device__ __forceinline__ K4 layer_kernels(double Rx, double Ry, double tnx, double tny, double snx,
-                                            double sny, double k) {
-    double r = hypot(Rx, Ry);
-    cplx H0, H1;
-    hankel01(k * r, H0, H1);
-    double Rnx = Rx * tnx + Ry * tny, Rny = Rx * snx + Ry * sny, nn = tnx * snx + tny * sny;
-    double ir = 1.0 / r;
-    K4 o;
-    o.S = cscale(cmuli(H0), 0.25);
-    o.D = cscale(cmuli(H1), 0.25 * k * Rny * ir);
-    o.N = cscale(cmuli(H1), -0.25 * k * Rnx * ir);
-    cplx t = cadd(cscale(H0, k * Rnx * Rny * ir * ir),
-                  cscale(H1, (-2.0 * Rnx * Rny * ir * ir + nn) * ir));
-    o.T = cscale(cmuli(t), 0.25 * k);
-    return o;
-}
-
-// coefficient of log r in each kernel (H_n -> (2i/pi) J_n)
-__device__ __forceinline__ void log_coeffs(double Rx, double Ry, double tnx, double tny, double snx,
-                                           double sny, double k, double out[4]) {
-    double r = hypot(Rx, Ry);
-    double J0 = j0(k * r), J1 = j1(k * r);
-    double Rnx = Rx * tnx + Ry * tny, Rny = Rx * snx + Ry * sny, nn = tnx * snx + tny * sny;
-    double ir = 1.0 / r;
-    const double c = -1.0 / (2.0 * GS_PI);
-    out[0] = c * J0;
-    out[1] = c * k * J1 * Rny * ir;
-    out[2] = -c * k * J1 * Rnx * ir;
-    out[3] = c * k * (k * J0 * Rnx * Rny * ir * ir - 2.0 * J1 * Rnx * Rny * ir * ir * ir + J1 * nn * ir);
-}
+// Kress weights for the closed-curve equations of general inclusion shapes (gs_shape.cu)
+}  // namespace
+void gs_kress_weights(int N, double *R, cudaStream_t st) { k_kress<<<nblk(N), TPB, 0, st>>>(N, R); }
+namespace {
 
 // Self blocks of one interface: differences of the ka and kb operators, wa S_ka - wb S_kb,
 // wa D_ka - wb D_kb, N_ka - N_kb, T_ka - T_kb (the weights are the TE permittivity ratios of the two

@@ -86,6 +86,15 @@ struct gs_ctx {
     double *xy = nullptr, *radius = nullptr, *kp = nullptr;
     double *kp_im = nullptr;                 // Im kp of lossy inclusions (null: all lossless)
     std::vector<double> radius_h, kp_h;      // host copies of the radii and Re kp
+    // general inclusion shape (gs_set_inclusions_star): one star, rotated per inclusion
+    bool is_star = false;
+    struct {
+        double a1 = 0, a2 = 0, kp = 0;
+        int a3 = 0, n_nodes = 0;
+    } star;
+    double *star_phi = nullptr;              // M rotation angles
+    cplx *S0 = nullptr;                      // nc x nc scattering matrix of the unrotated star
+    cplx *Sblk = nullptr;                    // M x nc x nc rotated blocks (the preconditioner)
     cplx *s = nullptr;                       // M x nc
 
     bool grating_ready = false;   // per-angle factorisation of the empty grating is built
@@ -95,6 +104,7 @@ struct gs_ctx {
     // scratch
     cplx *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;   // n each
     cplx *v4 = nullptr, *v5 = nullptr;                  // n each (refinement residual, correction)
+    cplx *v6 = nullptr;                                 // n, block preconditioner scratch (general shapes)
     cplx *g = nullptr;                                  // rows
     cplx *w = nullptr, *x = nullptr;                     // cols
     cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
@@ -210,6 +220,9 @@ int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStr
 int gs_tc_split_prepare(gs_ctx *c, int R);
 int gs_tc_split_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x, cplx *out, int *err_dev,
                           cudaStream_t st);
+// general inclusion shapes (gs_shape.cu): scattering matrix of the star and its rotated blocks
+int gs_star_blocks(gs_ctx *c);
+void gs_kress_weights(int N, double *R, cudaStream_t st);
 // tensor-core product C[M][N] = A[M][K] B[N][K]^T, bfloat16 in, FP32 out (gs_tc.cu)
 int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
                     cudaStream_t st);

@@ -164,6 +164,39 @@ __global__ void k_B_combine32(const float2 *__restrict__ B, int n, int nB, const
     if (lane == 0) y[warp] = cadd(csub(x[warp], cmul(s[warp], t[warp])), cmul(s[warp], C(re, im)));
 }
 
+// ---- general inclusion shapes: the block preconditioner (Sec. 4.2, S = diag(S_p^(m))) -------------
+
+// u[r] = (B v)[r] - t[r] (t nullable), B row-major FP64 (TB = cplx) or complex64 (TB = float2), warp
+// per row; u may alias t
+template <typename TB>
+__global__ void k_B_minus_t(const TB *__restrict__ B, int n, int nB, const cplx *__restrict__ v, const cplx *t,
+                            cplx *u) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const TB *b = B + (size_t)warp * nB;
+    cplx acc = C(0, 0);
+    for (int c = lane; c < nB; c += 32) {
+        const TB m = b[c];
+        cfma(acc, C((double)m.x, (double)m.y), __ldg(&v[c]));
+    }
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    if (lane == 0) u[warp] = t ? csub(acc, t[warp]) : acc;
+}
+
+// y[i nc + m] = x[i nc + m] + sum_n S_i[m][n] u[i nc + n] (x nullable), one thread per row
+__global__ void k_apply_blocks(const cplx *__restrict__ S, int M, int nc, const cplx *__restrict__ u,
+                               const cplx *__restrict__ x, cplx *__restrict__ y) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * nc) return;
+    const int i = (int)(e / nc), m = (int)(e % nc);
+    const cplx *Sr = S + ((size_t)i * nc + m) * nc;
+    const cplx *ui = u + (size_t)i * nc;
+    cplx acc = x ? x[e] : C(0, 0);
+    for (int n = 0; n < nc; ++n) cfma(acc, Sr[n], ui[n]);
+    y[e] = acc;
+}
+
 // g[r] = f[r] - (C x)[r] for r < nC, and f[r] for nC <= r < rows
 __global__ void k_f_minus_Cx(const cplx *__restrict__ Cm, int nC, int n, const cplx *__restrict__ x,
                              const cplx *__restrict__ f, int rows, cplx *__restrict__ g) {
@@ -410,7 +443,13 @@ int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, 
     GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
     GS_COUNT_LAUNCH(c);
-    k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, t, c->s, y);
+    if (c->Sblk) {   // general shapes: y = x + S (B v - t), in two steps through the scratch c->v6
+        k_B_minus_t<float2><<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, t, c->v6);
+        GS_COUNT_LAUNCH(c);
+        k_apply_blocks<<<(n + 255) / 256, 256, 0, c->stream>>>(c->Sblk, c->M, c->nc, c->v6, x, y);
+    } else {
+        k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, t, c->s, y);
+    }
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -432,7 +471,13 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
     GS_COUNT_LAUNCH(c);
     k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
     GS_COUNT_LAUNCH(c);
-    k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, x, tx, c->s, y);
+    if (c->Sblk) {   // general shapes: y = x + S (B v - T x), B v - T x in place of T x
+        k_B_minus_t<cplx><<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, tx, tx);
+        GS_COUNT_LAUNCH(c);
+        k_apply_blocks<<<(n + 255) / 256, 256, 0, c->stream>>>(c->Sblk, c->M, c->nc, tx, x, y);
+    } else {
+        k_B_combine<<<warps_blocks(n), 256, 0, c->stream>>>(a.B, n, nB, c->x, x, tx, c->s, y);
+    }
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -470,7 +515,15 @@ int incoming_f(gs_ctx *c, const AngleData &a, const cplx *s, cplx *y) {
 }
 }  // namespace
 
-int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) { return incoming_f(c, a, c->s, b); }
+int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b) {
+    if (!c->Sblk) return incoming_f(c, a, c->s, b);
+    // general shapes: b = S w, w = B_phys A^+ f
+    GS_TRY(incoming_f(c, a, nullptr, c->v3));
+    GS_COUNT_LAUNCH(c);
+    k_apply_blocks<<<(c->n() + 255) / 256, 256, 0, c->stream>>>(c->Sblk, c->M, c->nc, c->v3, nullptr, b);
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
 
 int gs_incoming_impl(gs_ctx *c, const AngleData &a, cplx *w) { return incoming_f(c, a, nullptr, w); }
 

@@ -579,6 +579,7 @@ int refresh_bf16(gs_ctx *c) {
 
 int angle_ready(gs_ctx *c, int angle) {
     if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
+    if (c->Sblk) return gs_fail(c, GS_ERR_STATE, "the learned warm start takes disk inclusions");
     if (angle < 0 || angle >= (int)c->ang.size()) return gs_fail(c, GS_ERR_ARG, "angle index out of range");
     if (!c->mlp || c->mlp->p != c->p)
         return gs_fail(c, GS_ERR_STATE, "no network for this multipole order (gs_mlp_set_params)");
