@@ -225,7 +225,7 @@ int gs_star_blocks(gs_ctx *c);
 void gs_kress_weights(int N, double *R, cudaStream_t st);
 // tensor-core product C[M][N] = A[M][K] B[N][K]^T, bfloat16 in, FP32 out (gs_tc.cu)
 int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
-                    cudaStream_t st);
+                    cudaStream_t st, int kslices = 1);
 // low-rank, operator, GMRES, Bragg (gs_solve.cu)
 int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x);
 int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int precision);

@@ -15,6 +15,9 @@
 //     last slice all four warps read their 32 TMEM lanes with tcgen05.ld and write C.
 //   * every wait on an mbarrier is bounded (about 2 s); a wait that gives up sets *err, the kernel
 //     still waits (bounded) for its own tensor-core work, frees its tensor memory and returns.
+//   * split K (gridDim.z slices): CTA z accumulates only its share of the K slices and writes its
+//     tile to the z-th copy of C; the caller adds the copies in FP64.  The tensor memory accumulates
+//     in FP32 along K, so shorter chains keep sums with large cancelling terms accurate.
 #include <cuda.h>
 
 #include <cuda_bf16.h>
@@ -119,6 +122,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
     const int nk = K / TBK;
+    const int kb0 = (int)((long)blockIdx.z * nk / gridDim.z), kb1 = (int)((long)(blockIdx.z + 1) * nk / gridDim.z);
+    C += (size_t)blockIdx.z * M * N;
     const uint32_t s_base = smem_u32(smem);
     const uint32_t b_full = smem_u32(bars), b_empty = smem_u32(bars + TST), b_acc = smem_u32(bars + 2 * TST);
 
@@ -146,7 +151,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         // producer: K slices of A (128 x 64) and B (256 x 64) into the stage ring
         int stage = 0;
         uint32_t phase = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(b_empty + 8 * stage, phase ^ 1)) {
                 ok = false;
                 break;
@@ -164,7 +169,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         // tensor-core issue: four K = 16 steps per slice (32 bytes along the swizzled rows)
         int stage = 0;
         uint32_t phase = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(b_full + 8 * stage, phase)) {
                 ok = false;
                 break;
@@ -173,7 +178,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const uint32_t sa = s_base + stage * TSTAGE, sb = sa + TA_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TBK / 16; ++kk)
-                umma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), (kb | kk) != 0);
+                umma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), kb != kb0 || kk != 0);
             umma_commit(b_empty + 8 * stage);
             if (++stage == TST) {
                 stage = 0;
@@ -245,11 +250,13 @@ int make_map(gs_ctx *c, CUtensorMap *m, const void *base, long rows, long cols, 
 }  // namespace
 
 // C[M][N] = A[M][K] B[N][K]^T (bfloat16 in, FP32 out) on stream st; M % 128, N % 256, K % 64 == 0,
-// 16-byte aligned rows.  err_dev: device int, set to 1 if a wait gave up.
+// 16-byte aligned rows.  err_dev: device int, set to 1 if a wait gave up.  kslices > 1 splits K:
+// C then holds kslices consecutive M x N partial products (kslices <= K / 64), to be summed.
 int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, long N, long K, int *err_dev,
-                    cudaStream_t st) {
+                    cudaStream_t st, int kslices) {
     if (M <= 0 || N <= 0 || K <= 0 || M % TBM || N % TBN || K % TBK)
         return gs_fail(c, GS_ERR_ARG, "tensor-core product needs M % 128 == 0, N % 256 == 0, K % 64 == 0");
+    if (kslices < 1 || kslices > K / TBK || kslices > 65535) return gs_fail(c, GS_ERR_ARG, "bad K split");
     if (M / TBM > 2147483647L || N / TBN > 65535 || K > 2147483647L) return gs_fail(c, GS_ERR_ARG, "size out of range");
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15) return gs_fail(c, GS_ERR_ARG, "pointers must be 16-byte aligned");
     CUtensorMap ma, mb;
@@ -268,8 +275,8 @@ int gs_tc_gemm_impl(gs_ctx *c, const void *A, const void *B, float *C, long M, l
         }
     }
     GS_COUNT_LAUNCH(c);
-    k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN)), 128, TSMEM, st>>>(ma, mb, C, (int)M, (int)N, (int)K,
-                                                                                 err_dev);
+    k_tc_gemm<<<dim3((unsigned)(M / TBM), (unsigned)(N / TBN), (unsigned)kslices), 128, TSMEM, st>>>(
+        ma, mb, C, (int)M, (int)N, (int)K, err_dev);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -408,11 +415,11 @@ __global__ void k_tc_pack_B_split(const cplx *__restrict__ beta, const cplx *__r
 }
 
 // out_r[e] = sum over operator part a and coefficient part b with a + b <= 2 of A_a B_b, / gamma^|m|:
-// Ca = A_a [B_0; ...; B_{2-a}]^T holds column b R + r for each b <= 2 - a; rows 2e and 2e + 1 are the
-// real and imaginary parts
+// Ca = A_a [B_0; ...; B_{2-a}]^T holds column b R + r for each b <= 2 - a, in S K-slice copies of
+// Mr x ld_a each (summed here in FP64); rows 2e and 2e + 1 are the real and imaginary parts
 __global__ void k_tc_unpack_split(const float *__restrict__ C0, long ld0, const float *__restrict__ C1, long ld1,
-                                  const float *__restrict__ C2, long ld2, int R, long n, int nc, GammaPow gpw,
-                                  cplx *__restrict__ out) {
+                                  const float *__restrict__ C2, long ld2, long Mr, int S, int R, long n, int nc,
+                                  GammaPow gpw, cplx *__restrict__ out) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)R * n) return;
     const int r = (int)(e / n);
@@ -420,18 +427,21 @@ __global__ void k_tc_unpack_split(const float *__restrict__ C0, long ld0, const 
     const int o = (int)(q % nc) - nc / 2;
     const double sc = gpw.inv[abs(o)];
     double re = 0.0, im = 0.0;
+    for (int z = 0; z < S; ++z) {
+        const float *c0 = C0 + (size_t)z * Mr * ld0, *c1 = C1 + (size_t)z * Mr * ld1, *c2 = C2 + (size_t)z * Mr * ld2;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        re += (double)C0[(2 * q) * ld0 + b * R + r];
-        im += (double)C0[(2 * q + 1) * ld0 + b * R + r];
-    }
+        for (int b = 0; b < 3; ++b) {
+            re += (double)c0[(2 * q) * ld0 + b * R + r];
+            im += (double)c0[(2 * q + 1) * ld0 + b * R + r];
+        }
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        re += (double)C1[(2 * q) * ld1 + b * R + r];
-        im += (double)C1[(2 * q + 1) * ld1 + b * R + r];
+        for (int b = 0; b < 2; ++b) {
+            re += (double)c1[(2 * q) * ld1 + b * R + r];
+            im += (double)c1[(2 * q + 1) * ld1 + b * R + r];
+        }
+        re += (double)c2[(2 * q) * ld2 + r];
+        im += (double)c2[(2 * q + 1) * ld2 + r];
     }
-    re += (double)C2[(2 * q) * ld2 + r];
-    im += (double)C2[(2 * q + 1) * ld2 + r];
     out[e] = C(sc * re, sc * im);
 }
 
@@ -583,10 +593,17 @@ extern "C" int gs_translate_multi(gs_ctx *c, int R, const gs_c128 *alpha_host, c
 }
 
 namespace {
+// K slices of the three-part product: each CTA's FP32 accumulation runs over 1/16 of the operator's
+// 6n columns (the slices are added in FP64), which keeps the sums' cancellation errors near those of
+// the CUDA-core complex64 translation, whose FP32 chains are similarly short
+constexpr int SPLIT_KSLICES = 16;
+
 // scratch of the three-part product for R right-hand sides: the stacked coefficient parts Bt
 // (3R rows, padded to 256) and the products C_a = A_a [B_0 .. B_{2-a}]^T of the operator parts
+// (SPLIT_KSLICES copies each)
 struct SplitLayout {
     long K, Mr, Np[3];
+    int S;
     __nv_bfloat16 *Bt;
     float *Cp[3];
     size_t bytes;
@@ -595,13 +612,14 @@ SplitLayout split_layout(gs_ctx *c, int R, void *base) {
     SplitLayout L;
     L.K = c->tcA_cols;
     L.Mr = c->tcA_rows;
+    L.S = (int)std::min<long>(SPLIT_KSLICES, L.K / TBK);
     size_t off[4];
     off[0] = 0;
     for (int a = 0; a < 3; ++a) L.Np[a] = round_up((3L - a) * R, TBN);
     size_t o = (size_t)round_up(sizeof(__nv_bfloat16) * L.Np[0] * L.K, 256);
     for (int a = 0; a < 3; ++a) {
         off[a + 1] = o;
-        o += (size_t)round_up(sizeof(float) * L.Mr * L.Np[a], 256);
+        o += (size_t)round_up(sizeof(float) * L.S * L.Mr * L.Np[a], 256);
     }
     L.bytes = o;
     uint8_t *p = (uint8_t *)base;
@@ -655,10 +673,11 @@ int gs_tc_split_translate(gs_ctx *c, int R, const cplx *alpha_dev, const cplx *x
     GS_COUNT_LAUNCH(c);
     k_tc_pack_B_split<<<(int)((3L * n * R + 255) / 256), 256, 0, st>>>(x, alpha_dev, R, c->M, c->nc, gpw, L.K, L.Bt);
     GS_CHECK_LAUNCH(c);
-    for (int a = 0; a < 3; ++a) GS_TRY(gs_tc_gemm_impl(c, Ap[a], L.Bt, L.Cp[a], L.Mr, L.Np[a], L.K, err_dev, st));
+    for (int a = 0; a < 3; ++a)
+        GS_TRY(gs_tc_gemm_impl(c, Ap[a], L.Bt, L.Cp[a], L.Mr, L.Np[a], L.K, err_dev, st, L.S));
     GS_COUNT_LAUNCH(c);
-    k_tc_unpack_split<<<(int)((n * R + 255) / 256), 256, 0, st>>>(L.Cp[0], L.Np[0], L.Cp[1], L.Np[1], L.Cp[2], L.Np[2], R,
-                                                                   n, c->nc, gpw, out);
+    k_tc_unpack_split<<<(int)((n * R + 255) / 256), 256, 0, st>>>(L.Cp[0], L.Np[0], L.Cp[1], L.Np[1], L.Cp[2], L.Np[2],
+                                                                   L.Mr, L.S, R, n, c->nc, gpw, out);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }

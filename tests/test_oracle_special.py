@@ -293,8 +293,8 @@ def test_self_operator_diagonal_is_load_bearing():
     good = L.self_difference_operators(c, d, alpha, ka, kb)["T"]
     orig = L.diag_limits
 
-    def planted(a, b):
-        out = orig(a, b)
+    def planted(a, b, wa=1.0, wb=1.0):
+        out = orig(a, b, wa, wb)
         out["T"] = (out["T"][0], out["T"][1] * (1 + 1e-6))
         return out
 
