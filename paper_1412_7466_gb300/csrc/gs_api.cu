@@ -101,6 +101,11 @@ void free_geometry(gs_ctx *c) {
     dfree(c->xdf);
     dfree(c->iflag);
     dfree(c->htab);
+    dfree(c->htab32);
+    c->htab32_sp = 0;
+    c->htab32_off = false;
+    dfree(c->b3pad);
+    dfree(c->terr);
     gs_angles_destroy(c);
     if (c->tcA) cudaFree(c->tcA);
     c->tcA = nullptr;
@@ -126,6 +131,9 @@ void free_geometry(gs_ctx *c) {
     dfree(c->sn);
     dfree(c->gg);
     dfree(c->yy);
+    dfree(c->kw32);
+    dfree(c->dpart);
+    dfree(c->npart);
     c->kdim = 0;
     c->factored = false;
 }
@@ -140,6 +148,7 @@ void free_factor(gs_ctx *c, bool keep_batch = false) {
     dfree(c->g);
     dfree(c->w);
     dfree(c->x);
+    dfree(c->x32);
     dfree(c->Vtmp);
     dfree(c->Xtmp);
     dfree(c->Vxtmp);
@@ -181,8 +190,11 @@ int check_angle(gs_ctx *c, int angle) {
 // Krylov workspace of the single-geometry solve for a restart length of up to 512
 int gs_ensure_krylov(gs_ctx *c, int restart) {
     const int want = std::max(1, std::min(restart, 512));
-    if (c->Vk && c->kdim >= want) return GS_OK;
     const long n = c->n();
+    if (!c->kw32) GS_TRY(dalloc(c, &c->kw32, n));
+    if (!c->dpart) GS_TRY(dalloc(c, &c->dpart, (size_t)GS_DOT_SPLIT * 513));
+    if (!c->npart) GS_TRY(dalloc(c, &c->npart, GS_NORM_PARTS));
+    if (c->Vk && c->kdim >= want) return GS_OK;
     c->kdim = want;
     GS_TRY(dalloc(c, &c->Vk, (size_t)(c->kdim + 1) * n));
     GS_TRY(dalloc(c, &c->kv1, n));
@@ -203,6 +215,7 @@ int gs_ensure_grating(gs_ctx *c) {
         GS_TRY(dalloc(c, &c->g, ly.rows));
         GS_TRY(dalloc(c, &c->w, ly.cols));
         GS_TRY(dalloc(c, &c->x, ly.cols));
+        GS_TRY(dalloc(c, &c->x32, ly.cols));
         GS_TRY(dalloc(c, &c->Vtmp, (size_t)ly.rows * ly.cols));
         GS_TRY(dalloc(c, &c->Xtmp, (size_t)ly.cols * ly.cols));
         GS_TRY(dalloc(c, &c->Vxtmp, (size_t)ly.cols * ly.cols));
@@ -602,6 +615,9 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->part, c->part_elems));
     GS_TRY(dalloc(c, &c->b32, n));
     GS_TRY(dalloc(c, &c->img32, 3 * (size_t)c->M));
+    GS_TRY(dalloc(c, &c->b3pad, (size_t)((3L * c->M + 31) / 32) * 32 * c->nc));
+    GS_TRY(dalloc(c, &c->terr, 1));
+    GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), c->stream));
     GS_TRY(dalloc(c, &c->xdf, n));
     GS_TRY(dalloc(c, &c->iflag, 1));
     GS_TRY(gs_build_images_c64(c, c->xy, c->M, c->img32, c->stream));
@@ -710,7 +726,8 @@ int gs_translate(gs_ctx *c, int angle, const gs_c128 *beta_dev, gs_c128 *alpha_d
     if (!beta_dev || !alpha_dev || beta_dev == (const gs_c128 *)alpha_dev)
         return gs_fail(c, GS_ERR_ARG, "null or aliased vectors");
     if (precision != GS_FP64 && precision != GS_C64) return gs_fail(c, GS_ERR_ARG, "bad precision");
-    return gs_translate_impl(c, c->ang[angle], (const cplx *)beta_dev, (cplx *)alpha_dev, precision);
+    GS_TRY(gs_translate_impl(c, c->ang[angle], (const cplx *)beta_dev, (cplx *)alpha_dev, precision));
+    return precision == GS_C64 && c->htab32 ? gs_check_table_wait(c) : GS_OK;
 }
 
 int gs_apply(gs_ctx *c, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision) {
@@ -718,7 +735,8 @@ int gs_apply(gs_ctx *c, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int pre
     GS_TRY(check_angle(c, angle));
     if (!x_dev || !y_dev || x_dev == (const gs_c128 *)y_dev) return gs_fail(c, GS_ERR_ARG, "null or aliased vectors");
     if (precision != GS_FP64 && precision != GS_C64) return gs_fail(c, GS_ERR_ARG, "bad precision");
-    return gs_apply_impl(c, c->ang[angle], (const cplx *)x_dev, (cplx *)y_dev, precision);
+    GS_TRY(gs_apply_impl(c, c->ang[angle], (const cplx *)x_dev, (cplx *)y_dev, precision));
+    return precision == GS_C64 && c->htab32 ? gs_check_table_wait(c) : GS_OK;
 }
 
 int gs_rhs(gs_ctx *c, int angle, gs_c128 *b_dev) {

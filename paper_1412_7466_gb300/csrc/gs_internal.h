@@ -1,5 +1,6 @@
 // Internal context of the gsolve library (not part of the ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -23,6 +24,10 @@ struct Layout {
 // largest |entry| of C held in double-float form: products with the inner operator's input (|x| of
 // order 1) and their sums over up to ~1e6 columns stay inside the FP32 exponent range
 #define GS_DF_LIMIT 1e30
+// inner products of the complex64 Arnoldi step: at most this many blocks share one basis vector
+#define GS_DOT_SPLIT 32
+// partial squared norms of the Arnoldi vector (one per block of the second Gram-Schmidt pass)
+#define GS_NORM_PARTS 1024
 
 struct AngleData {
     double theta = 0, kappa0 = 0;
@@ -107,6 +112,7 @@ struct gs_ctx {
     cplx *v6 = nullptr;                                 // n, block preconditioner scratch (general shapes)
     cplx *g = nullptr;                                  // rows
     cplx *w = nullptr, *x = nullptr;                     // cols
+    float2 *x32 = nullptr;                               // cols, complex64 copy of x (B_phys input, mixed form)
     cplx *Vtmp = nullptr;                                // rows x cols, QR workspace
     cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
     float2 *X32tmp = nullptr;                            // 2 x cols x cols: FP32 copy of R^* and its rotations
@@ -119,6 +125,12 @@ struct gs_ctx {
     float4 *xdf = nullptr;                               // n, double-float split of the operator input
     int *iflag = nullptr;                                // one int, device-side flag
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
+    float2 *htab32 = nullptr;                            // its complex64 copy [i][q][s], row stride htab32_sp
+    long htab32_sp = 0;                                  // 3M rounded up to 32 images
+    bool htab32_off = false;                             // no room for it: complex64 recomputes the coefficients
+    CUtensorMap tm_h32;                                  // TMA map of htab32: boxes of 32 images x (4p+1) orders
+    float2 *b3pad = nullptr;                             // complex64 phased source coefficients, 32-image tiles
+    int *terr = nullptr;                                 // device flag: a bounded wait of the table kernel gave up
     void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
     long tcA_rows = 0, tcA_cols = 0;
     double tc_gamma = 1.0;                               // order rescaling of tcA (min(1, k2 r_min))
@@ -135,6 +147,9 @@ struct gs_ctx {
     int kdim = 0;
     cplx *Vk = nullptr;                                  // (kdim+1) x n (complex64 basis: reinterpreted)
     cplx *kv1 = nullptr, *kv2 = nullptr;                 // n each: complex64-basis GMRES work vectors
+    float2 *kw32 = nullptr;                              // n, complex64 copy of the Arnoldi vector
+    cplx *dpart = nullptr;                               // GS_DOT_SPLIT x 513 partial inner products
+    double *npart = nullptr;                             // GS_NORM_PARTS partial squared norms
     cplx *Hh = nullptr;                                  // (kdim+1) x kdim column-major
     cplx *cs = nullptr, *sn = nullptr, *gg = nullptr, *yy = nullptr;
     double *dscal = nullptr;                             // device scalars
@@ -210,6 +225,13 @@ int gs_translate_impl(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out
 int gs_c64_range(gs_ctx *c);
 size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
+// complex64 pair table for the complex64 translation, built on first use when it fits (gs_translate.cu)
+int gs_ensure_table32(gs_ctx *c);
+// GS_ERR_TIMEOUT if a bounded wait of that kernel gave up since the last check (synchronises)
+int gs_check_table_wait(gs_ctx *c);
+// plain (unswizzled) 2-D tensor map over a row-major rows x cols array (gs_tc.cu)
+int gs_make_map_plain(gs_ctx *c, CUtensorMap *m, CUtensorMapDataType dt, const void *base, long rows, long cols,
+                      long row_bytes, int box_cols, int box_rows);
 // (hi, lo) float coordinates of the 3M images of M inclusions (complex64 translation), on stream st
 int gs_build_images_c64(gs_ctx *c, const double *xy, int M, float4 *img, cudaStream_t st);
 // Tensor-core translation of R concatenated coefficient vectors (R angles of the current geometry,

@@ -18,7 +18,7 @@ namespace {
 // y[r] = scale[r] * sum_c A[r, c] x[c]   (A row-major, warp per row)
 __global__ void k_gemv_rows(const cplx *__restrict__ A, int nrows, int ncols, long lda,
                             const cplx *__restrict__ x, const double *__restrict__ scale,
-                            cplx *__restrict__ y) {
+                            cplx *__restrict__ y, float2 *__restrict__ y32 = nullptr) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nrows) return;
     const cplx *a = A + (size_t)warp * lda;
@@ -26,7 +26,11 @@ __global__ void k_gemv_rows(const cplx *__restrict__ A, int nrows, int ncols, lo
     for (int c = lane; c < ncols; c += 32) cfma(s, a[c], __ldg(&x[c]));
     s.x = warp_sum(s.x);
     s.y = warp_sum(s.y);
-    if (lane == 0) y[warp] = scale ? cscale(s, scale[warp]) : s;
+    if (lane == 0) {
+        const cplx r = scale ? cscale(s, scale[warp]) : s;
+        y[warp] = r;
+        if (y32) y32[warp] = make_float2((float)r.x, (float)r.y);   // y32: complex64 copy (nullable)
+    }
 }
 
 // y[r] = sum_c A[r, c] x[c] for few long rows (C: ~1300 rows of M (2p+1) columns), FP64: one block
@@ -141,21 +145,32 @@ __global__ void __launch_bounds__(GEMV_DF_THREADS) k_gemv_rows_df(const float4 *
     }
 }
 
-// y[r] = x[r] - s[r] t[r] + s[r] (B v)[r] with B complex64 (FP32 products), warp per row
-__global__ void k_B_combine32(const float2 *__restrict__ B, int n, int nB, const cplx *__restrict__ v,
+// y[r] = x[r] - s[r] t[r] + s[r] (B v)[r] with B and v complex64 (FP32 products), warp per row.  v
+// arrives as complex64 (converted once by its producer): an FP64 -> FP32 conversion per entry of B
+// would run at the FP64 pipe's rate and bound the kernel, not HBM.  Two accumulator pairs per lane
+// keep two loads of each row in flight.
+__global__ void k_B_combine32(const float2 *__restrict__ B, int n, int nB, const float2 *__restrict__ v,
                               const cplx *__restrict__ x, const cplx *__restrict__ t, const cplx *__restrict__ s,
                               cplx *__restrict__ y) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const float2 *b = B + (size_t)warp * nB;
-    float re = 0.f, im = 0.f;
-    for (int c = lane; c < nB; c += 32) {
-        const float2 m = b[c];
-        const cplx vv = __ldg(&v[c]);
-        const float wr = (float)vv.x, wi = (float)vv.y;
-        re = fmaf(m.x, wr, fmaf(-m.y, wi, re));
-        im = fmaf(m.x, wi, fmaf(m.y, wr, im));
+    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+    int c = lane;
+    for (; c + 32 < nB; c += 64) {
+        const float2 m0 = __ldcs(&b[c]), m1 = __ldcs(&b[c + 32]);
+        const float2 w0 = __ldg(&v[c]), w1 = __ldg(&v[c + 32]);
+        re0 = fmaf(m0.x, w0.x, fmaf(-m0.y, w0.y, re0));
+        im0 = fmaf(m0.x, w0.y, fmaf(m0.y, w0.x, im0));
+        re1 = fmaf(m1.x, w1.x, fmaf(-m1.y, w1.y, re1));
+        im1 = fmaf(m1.x, w1.y, fmaf(m1.y, w1.x, im1));
     }
+    if (c < nB) {
+        const float2 m0 = __ldcs(&b[c]), w0 = __ldg(&v[c]);
+        re0 = fmaf(m0.x, w0.x, fmaf(-m0.y, w0.y, re0));
+        im0 = fmaf(m0.x, w0.y, fmaf(m0.y, w0.x, im0));
+    }
+    float re = re0 + re1, im = im0 + im1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -286,49 +301,74 @@ __global__ void k_sub(const cplx *a, const cplx *b, long n, cplx *y) {
 }
 
 // Givens step for Hessenberg column j (column-major, leading dimension ld): applies the previous
-// rotations, forms the new one, updates g and writes the residual estimate |g[j+1]| to res.  The
-// column and the rotations are staged in shared memory; the sequential part runs on one thread.
+// rotations, forms the new one, updates g and writes the residual estimate |g[j+1]| to res.
+// Applying rotations 0..j-1 in turn to the column is a linear recurrence in the value carried down
+// it: with carry_0 = h_0,
+//   h'_i = c_i carry_i + s_i h_{i+1},   carry_{i+1} = -conj(s_i) carry_i + c_i h_{i+1},
+// so carry_{i+1} = A_i h_0 + B_i with (A_i, B_i) the composition of the affine maps
+// x -> -conj(s_k) x + c_k h_{k+1}, k <= i; the block forms all compositions by an inclusive scan
+// (|s_k| <= 1, so the products stay bounded) instead of j dependent steps on one thread.  Launch
+// with GS_KMAX threads (j < GS_KMAX).
 constexpr int GS_KMAX = 512;
-__global__ void k_givens(cplx *H, int ld, int j, cplx *cs, cplx *sn, cplx *g, double *res) {
-    __shared__ cplx h[GS_KMAX + 1], c_[GS_KMAX], s_[GS_KMAX];
+__global__ void __launch_bounds__(GS_KMAX) k_givens(cplx *H, int ld, int j, cplx *cs, cplx *sn, cplx *g,
+                                                   double *res) {
+    __shared__ cplx mA[GS_KMAX], mB[GS_KMAX];
     cplx *col = H + (size_t)j * ld;
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) h[i] = col[i];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        c_[i] = cs[i];
-        s_[i] = sn[i];
+    const int t = threadIdx.x;
+    const cplx h0 = col[0], hj1 = col[j + 1];
+    cplx ct = C(1, 0), st = C(0, 0), hn = C(0, 0), a = C(1, 0), b = C(0, 0);
+    if (t < j) {
+        ct = cs[t];
+        st = sn[t];
+        hn = col[t + 1];
+        a = cscale(cconj(st), -1.0);
+        b = cmul(ct, hn);
     }
+    mA[t] = a;
+    mB[t] = b;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < j; ++i) {
-            cplx t = cadd(cmul(c_[i], h[i]), cmul(s_[i], h[i + 1]));
-            h[i + 1] = cadd(cmul(cscale(cconj(s_[i]), -1.0), h[i]), cmul(c_[i], h[i + 1]));
-            h[i] = t;
+    for (int off = 1; off < GS_KMAX; off <<= 1) {
+        cplx pa = C(1, 0), pb = C(0, 0);
+        if (t >= off) {
+            pa = mA[t - off];
+            pb = mB[t - off];
         }
-        cplx a = h[j], b = h[j + 1];
-        double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
-        double rr = hypot(aa, bb);
+        __syncthreads();
+        if (t >= off) {   // (a, b) after (pa, pb): x -> a (pa x + pb) + b
+            const cplx na = cmul(mA[t], pa), nb = cadd(cmul(mA[t], pb), mB[t]);
+            mA[t] = na;
+            mB[t] = nb;
+        }
+        __syncthreads();
+    }
+    if (t < j) {
+        const cplx carry = t == 0 ? h0 : cadd(cmul(mA[t - 1], h0), mB[t - 1]);
+        col[t] = cadd(cmul(ct, carry), cmul(st, hn));
+    }
+    if (t == 0) {
+        const cplx av = j == 0 ? h0 : cadd(cmul(mA[j - 1], h0), mB[j - 1]), bv = hj1;
+        const double aa = sqrt(cabs2(av)), bb = sqrt(cabs2(bv));
+        const double rr = hypot(aa, bb);
         cplx c, s;
         if (rr == 0.0) {
             c = C(1, 0);
             s = C(0, 0);
         } else if (aa == 0.0) {
             c = C(0, 0);
-            s = cscale(cconj(b), 1.0 / bb);
+            s = cscale(cconj(bv), 1.0 / bb);
         } else {
             c = C(aa / rr, 0.0);
-            s = cmul(cscale(a, 1.0 / aa), cscale(cconj(b), 1.0 / rr));
+            s = cmul(cscale(av, 1.0 / aa), cscale(cconj(bv), 1.0 / rr));
         }
         cs[j] = c;
         sn[j] = s;
-        h[j] = cadd(cmul(c, a), cmul(s, b));
-        h[j + 1] = C(0, 0);
-        cplx gj = g[j];
+        col[j] = cadd(cmul(c, av), cmul(s, bv));
+        col[j + 1] = C(0, 0);
+        const cplx gj = g[j];
         g[j + 1] = cmul(cscale(cconj(s), -1.0), gj);
         g[j] = cmul(c, gj);
         res[0] = sqrt(cabs2(g[j + 1]));
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = h[i];
 }
 
 // back substitution H[0:k,0:k] y = g[0:k] (upper triangular), column-oriented: one thread divides,
@@ -441,14 +481,14 @@ int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, 
     GS_COUNT_LAUNCH(c);
     k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
     GS_COUNT_LAUNCH(c);
-    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x);
+    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x, c->x32);
     GS_COUNT_LAUNCH(c);
     if (c->Sblk) {   // general shapes: y = x + S (B v - t), in two steps through the scratch c->v6
         k_B_minus_t<float2><<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, t, c->v6);
         GS_COUNT_LAUNCH(c);
         k_apply_blocks<<<(n + 255) / 256, 256, 0, c->stream>>>(c->Sblk, c->M, c->nc, c->v6, x, y);
     } else {
-        k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, x, t, c->s, y);
+        k_B_combine32<<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x32, x, t, c->s, y);
     }
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -540,50 +580,112 @@ __global__ void k_axpy_inplace(cplx *x, const cplx *y, long n) {
 // checked against their true residual, keep the basis in complex64 and do these products in FP32
 // (block sums in FP64); the operator still takes and returns FP64 vectors.
 
-// h[i] (+)= V_i^* w for i < cnt, V complex64, w complex128 (FP32 products), block per basis vector
-__global__ void k_dots32(const float2 *__restrict__ Vb, long n, const cplx *__restrict__ w, int cnt,
-                         cplx *__restrict__ h, int accumulate) {
-    const int i = blockIdx.x;
+// Partial inner products part[q ld + i] = V_i^* w over the q-th of Q element ranges, V and w complex64
+// (FP32 products, FP64 block sums); grid (cnt, Q).  With Q = 1 the sum goes straight to h[i].  A
+// block per basis vector alone leaves most SMs idle early in a cycle (few vectors), so short
+// cycles split each vector over Q blocks; k_dots_reduce adds the Q partials in a fixed order.
+__global__ void k_dots32(const float2 *__restrict__ Vb, long n, const float2 *__restrict__ w, int cnt,
+                         cplx *__restrict__ out, int ld, int accumulate) {
+    const int i = blockIdx.x, q = blockIdx.y, Q = gridDim.y;
     if (i >= cnt) return;
     __shared__ double sh[32];
     const float2 *v = Vb + (size_t)i * n;
-    float re = 0.f, im = 0.f;
-    for (long e = threadIdx.x; e < n; e += blockDim.x) {
-        const float2 a = v[e];
-        const cplx b = w[e];
-        const float br = (float)b.x, bi = (float)b.y;
-        re = fmaf(a.x, br, fmaf(a.y, bi, re));   // conj(a) b
-        im = fmaf(a.x, bi, fmaf(-a.y, br, im));
+    const long e0 = n * q / Q, e1 = n * (q + 1) / Q;
+    float re = 0.f, im = 0.f, re1 = 0.f, im1 = 0.f;
+    long e = e0 + threadIdx.x;
+    for (; e + blockDim.x < e1; e += 2 * blockDim.x) {
+        const float2 a = v[e], b = w[e], a1 = v[e + blockDim.x], b1 = w[e + blockDim.x];
+        re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));   // conj(a) b
+        im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+        re1 = fmaf(a1.x, b1.x, fmaf(a1.y, b1.y, re1));
+        im1 = fmaf(a1.x, b1.y, fmaf(-a1.y, b1.x, im1));
     }
-    const double R = block_sum((double)re, sh), I = block_sum((double)im, sh);
+    if (e < e1) {
+        const float2 a = v[e], b = w[e];
+        re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+        im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+    }
+    const double R = block_sum((double)re + (double)re1, sh), I = block_sum((double)im + (double)im1, sh);
     if (threadIdx.x == 0) {
         const cplx r = C(R, I);
-        h[i] = accumulate ? cadd(h[i], r) : r;
+        if (Q == 1)
+            out[i] = accumulate ? cadd(out[i], r) : r;
+        else
+            out[(size_t)q * ld + i] = r;
     }
 }
 
-// w (+/-)= sum_{i < cnt} coef[i] V_i (sign -1: subtract), products in FP32; cnt <= GS_KMAX + 1
-__global__ void k_combo32(cplx *__restrict__ w, const float2 *__restrict__ Vb, long n, const cplx *__restrict__ coef,
-                          int cnt, float sign) {
+// h[i] (+)= sum_q part[q ld + i], q = 0..Q-1 in order
+__global__ void k_dots_reduce(const cplx *__restrict__ part, int Q, int ld, int cnt, cplx *__restrict__ h,
+                              int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    cplx r = C(0, 0);
+    for (int q = 0; q < Q; ++q) r = cadd(r, part[(size_t)q * ld + i]);
+    h[i] = accumulate ? cadd(h[i], r) : r;
+}
+
+// w (+/-)= sum_{i < cnt} coef[i] V_i, products in FP32 (eight vectors per pass, so eight loads of the
+// basis are in flight per thread); cnt <= GS_KMAX + 1.  Optionally writes the complex64 copy w32 of
+// the result and, per block, the partial squared norm of the result to npart[blockIdx.x].
+__global__ void __launch_bounds__(128) k_combo32(cplx *__restrict__ w, const float2 *__restrict__ Vb, long n,
+                                                 const cplx *__restrict__ coef, int cnt, float sign,
+                                                 float2 *__restrict__ w32, double *__restrict__ npart) {
     __shared__ float2 cf[513];
+    __shared__ double sh[32];
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = make_float2((float)coef[i].x, (float)coef[i].y);
     __syncthreads();
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    float sr = 0.f, si = 0.f;
-    for (int i = 0; i < cnt; ++i) {
-        const float2 v = Vb[(size_t)i * n + e], c = cf[i];
-        sr = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr));
-        si = fmaf(c.x, v.y, fmaf(c.y, v.x, si));
+    double nrm = 0.0;
+    if (e < n) {
+        float sr[8], si[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sr[u] = si[u] = 0.f;
+        int i = 0;
+        for (; i + 8 <= cnt; i += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 v = Vb[(size_t)(i + u) * n + e], c = cf[i + u];
+                sr[u] = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr[u]));
+                si[u] = fmaf(c.x, v.y, fmaf(c.y, v.x, si[u]));
+            }
+        }
+        for (; i < cnt; ++i) {
+            const float2 v = Vb[(size_t)i * n + e], c = cf[i];
+            sr[0] = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr[0]));
+            si[0] = fmaf(c.x, v.y, fmaf(c.y, v.x, si[0]));
+        }
+        float tr = 0.f, ti = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            tr += sr[u];
+            ti += si[u];
+        }
+        const cplx r = cadd(w[e], C((double)(sign * tr), (double)(sign * ti)));
+        w[e] = r;
+        if (w32) w32[e] = make_float2((float)r.x, (float)r.y);
+        nrm = cabs2(r);
     }
-    w[e] = cadd(w[e], C((double)(sign * sr), (double)(sign * si)));
+    if (npart) {
+        nrm = block_sum(nrm, sh);
+        if (threadIdx.x == 0) npart[blockIdx.x] = nrm;
+    }
 }
 
-// dst = src / norm[0] in complex64; records norm into Hsub (complex) if given
+// dst = src / nv in complex64, nv = norm[0], or nv = sqrt(sum of np partials npart[0..np-1]) when
+// npart is given (added in the same order by every block); records nv into Hsub (complex) if given
 __global__ void k_store32(const cplx *__restrict__ src, long n, const double *norm, float2 *__restrict__ dst,
-                          cplx *Hsub) {
+                          cplx *Hsub, const double *__restrict__ npart = nullptr, int np = 0) {
+    __shared__ double sh[32];
+    double nv;
+    if (npart) {
+        double t = 0.0;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) t += npart[k];
+        nv = sqrt(block_sum(t, sh));
+    } else {
+        nv = norm[0];
+    }
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const double nv = norm[0];
     if (e == 0 && Hsub) *Hsub = C(nv, 0.0);
     if (e >= n) return;
     const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
@@ -655,7 +757,7 @@ int gmres_core(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cplx 
             GS_COUNT_LAUNCH(c);
             k_scale_by_inv<<<eb, 256, 0, st>>>(w, n, ds + 3, w, h + j + 1);
             GS_COUNT_LAUNCH(c);
-            k_givens<<<1, 128, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
+            k_givens<<<1, GS_KMAX, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
             GS_CHECK_LAUNCH(c);
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
@@ -698,6 +800,20 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
     float2 *V = (float2 *)c->Vk;
     cplx *r = c->v2, *vj = c->kv1, *w = c->kv2;
     double *ds = c->dscal;
+    const int eb128 = (int)((n + 127) / 128);
+    const bool fused_norm = eb128 <= GS_NORM_PARTS;   // the second CGS pass leaves the norm partials
+    // h[0..cnt) = V^* w32, split over up to GS_DOT_SPLIT blocks per basis vector early in a cycle
+    auto dots = [&](int cnt, cplx *dst) -> int {
+        const int Q = std::min(GS_DOT_SPLIT, std::max(1, (2 * c->sms + cnt - 1) / cnt));
+        GS_COUNT_LAUNCH(c);
+        k_dots32<<<dim3(cnt, Q), 256, 0, st>>>(V, n, c->kw32, cnt, Q == 1 ? dst : c->dpart, 513, 0);
+        if (Q > 1) {
+            GS_COUNT_LAUNCH(c);
+            k_dots_reduce<<<(cnt + 255) / 256, 256, 0, st>>>(c->dpart, Q, 513, cnt, dst, 0);
+        }
+        GS_CHECK_LAUNCH(c);
+        return GS_OK;
+    };
     int it = 0;
     bool first = true;
     double est = 1.0;
@@ -729,22 +845,29 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
             GS_TRY(gs_apply_impl(c, a, vj, w, GS_C64));
             ++it;
             cplx *h = c->Hh + (size_t)j * ld;
+            // CGS2 on the complex64 basis: w32 = complex64 copy of w for the inner products; the
+            // second pass also leaves the partial squared norms of the new vector
             GS_COUNT_LAUNCH(c);
-            k_dots32<<<j + 1, 256, 0, st>>>(V, n, w, j + 1, h, 0);
+            k_to_c64_vec<<<eb, 256, 0, st>>>(w, n, c->kw32);
+            GS_TRY(dots(j + 1, h));
             GS_COUNT_LAUNCH(c);
-            k_combo32<<<eb, 256, 0, st>>>(w, V, n, h, j + 1, -1.f);
+            k_combo32<<<eb128, 128, 0, st>>>(w, V, n, h, j + 1, -1.f, c->kw32, nullptr);
+            GS_TRY(dots(j + 1, c->yy));
             GS_COUNT_LAUNCH(c);
-            k_dots32<<<j + 1, 256, 0, st>>>(V, n, w, j + 1, c->yy, 0);
-            GS_COUNT_LAUNCH(c);
-            k_combo32<<<eb, 256, 0, st>>>(w, V, n, c->yy, j + 1, -1.f);
+            k_combo32<<<eb128, 128, 0, st>>>(w, V, n, c->yy, j + 1, -1.f, nullptr, fused_norm ? c->npart : nullptr);
             GS_COUNT_LAUNCH(c);
             k_add_vec<<<1, 256, 0, st>>>(h, c->yy, j + 1);
+            if (fused_norm) {
+                GS_COUNT_LAUNCH(c);
+                k_store32<<<eb, 256, 0, st>>>(w, n, nullptr, V + (size_t)(j + 1) * n, h + j + 1, c->npart, eb128);
+            } else {
+                GS_COUNT_LAUNCH(c);
+                k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
+                GS_COUNT_LAUNCH(c);
+                k_store32<<<eb, 256, 0, st>>>(w, n, ds + 3, V + (size_t)(j + 1) * n, h + j + 1);
+            }
             GS_COUNT_LAUNCH(c);
-            k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
-            GS_COUNT_LAUNCH(c);
-            k_store32<<<eb, 256, 0, st>>>(w, n, ds + 3, V + (size_t)(j + 1) * n, h + j + 1);
-            GS_COUNT_LAUNCH(c);
-            k_givens<<<1, 128, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
+            k_givens<<<1, GS_KMAX, 0, st>>>(c->Hh, ld, j, c->cs, c->sn, c->gg, ds + 2);
             GS_CHECK_LAUNCH(c);
             GS_CUDA(c, cudaMemcpyAsync(c->hscal + 2, ds + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
@@ -755,7 +878,7 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
         GS_COUNT_LAUNCH(c);
         k_backsolve<<<1, 256, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
         GS_COUNT_LAUNCH(c);
-        k_combo32<<<eb, 256, 0, st>>>(x, V, n, c->yy, kk, 1.f);
+        k_combo32<<<eb128, 128, 0, st>>>(x, V, n, c->yy, kk, 1.f, nullptr, nullptr);
         GS_CHECK_LAUNCH(c);
         if (est <= tol) {
             GS_TRY(gs_apply_impl(c, a, x, r, GS_C64));
@@ -846,6 +969,7 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
     }
     a.iters = total;
     a.relres = rel;
+    if (o.precision == GS_C64 && c->htab32) GS_TRY(gs_check_table_wait(c));
     return rel <= o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
 }
 

@@ -28,6 +28,7 @@
 #include <string>
 
 #include "gs_internal.h"
+#include "gs_tma.cuh"
 
 namespace {
 
@@ -37,46 +38,11 @@ constexpr int TB_BYTES = TBN * TBK * 2;               // 32 KB
 constexpr int TSTAGE = TA_BYTES + TB_BYTES;           // 48 KB
 constexpr int TSMEM = TST * TSTAGE + 1024 + 256;      // stages (1024-aligned) + barriers
 constexpr int TMEM_COLS = 256;
-constexpr long long WAIT_CYCLES = 4000000000LL;      // ~2 s at 2 GHz
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B bfloat16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
                            ((uint32_t)(TBM >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// waits for the phase of the given parity to complete; false after WAIT_CYCLES
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
-        "[%2];" ::"r"(dst),
-        "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
 
 // shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte swizzle:
 // start address >> 4 (bits 0-13), leading byte offset (unused for this layout; 16 B), stride byte
@@ -248,6 +214,23 @@ int make_map(gs_ctx *c, CUtensorMap *m, const void *base, long rows, long cols, 
 }
 
 }  // namespace
+
+// 2-D tensor map over a row-major rows x cols array (row stride row_bytes, a multiple of 16), box
+// box_cols x box_rows elements, no swizzle (a box lands in shared memory row after row);
+// out-of-range elements of a box read as zero
+int gs_make_map_plain(gs_ctx *c, CUtensorMap *m, CUtensorMapDataType dt, const void *base, long rows, long cols,
+                      long row_bytes, int box_cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return gs_fail(c, GS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gs_fail(c, GS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+    return GS_OK;
+}
 
 // C[M][N] = A[M][K] B[N][K]^T (bfloat16 in, FP32 out) on stream st; M % 128, N % 256, K % 64 == 0,
 // 16-byte aligned rows.  err_dev: device int, set to 1 if a wait gave up.  kslices > 1 splits K:

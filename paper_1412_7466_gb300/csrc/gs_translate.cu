@@ -13,12 +13,14 @@
 // unrolled for the compile-time order P).  Warp-shuffle reductions combine the lanes.  The source
 // images are split into `nsplit` chunks across blockIdx.y to fill the SMs; a second kernel
 // sums the chunk partials in a fixed order (deterministic).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "gs_internal.h"
 #include "gs_pair.cuh"
+#include "gs_tma.cuh"
 
 namespace {
 
@@ -244,8 +246,14 @@ k_translate_c64(const float4 *__restrict__ img, int M, const cplxf *__restrict__
 // (2.35 GB at M = 1000, p = 12), read in 0.35 ms at HBM speed against 12.5 ms of FP64 products.
 // Layout h[i][q][s] with the source image s = (l+1) M + j fastest, so a warp (target i, 32 sources)
 // reads each q as one coalesced 512-byte segment.  The self pair (i, l = 0) holds zeros.
-template <int P>
-__global__ void k_pair_table(const double *__restrict__ xy, int M, double k, double d, cplx *__restrict__ h) {
+__device__ __forceinline__ void put_h(cplx *o, cplx v) { *o = v; }
+__device__ __forceinline__ void put_h(float2 *o, cplx v) { *o = make_float2((float)v.x, (float)v.y); }
+
+// T = cplx: the FP64 table (row stride SP = 3M); T = float2: the complex64 table of the complex64
+// translation, rounded from the same FP64 values (row stride SP = 3M rounded up to 32 images, so
+// that every row starts on a 256-byte boundary for the tensor copies)
+template <int P, typename T>
+__global__ void k_pair_table(const double *__restrict__ xy, int M, double k, double d, T *__restrict__ h, long SP) {
     constexpr int NQ = 4 * P + 1;
     const long S = 3L * M;
     const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,10 +262,10 @@ __global__ void k_pair_table(const double *__restrict__ xy, int M, double k, dou
     const long s = id - (long)i * S;
     const int l = (int)(s / M) - 1;
     const int j = (int)(s - (long)(l + 1) * M);
-    cplx *o = h + (size_t)i * NQ * S + s;
+    T *o = h + (size_t)i * NQ * SP + s;
     if (l == 0 && j == i) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) o[(size_t)q * S] = C(0.0, 0.0);
+        for (int q = 0; q < NQ; ++q) put_h(o + (size_t)q * SP, C(0.0, 0.0));
         return;
     }
     const double dx = xy[2 * i] - (xy[2 * j] + l * d), dy = xy[2 * i + 1] - xy[2 * j + 1];
@@ -266,12 +274,12 @@ __global__ void k_pair_table(const double *__restrict__ xy, int M, double k, dou
     hankel01(z, Hm1, Hc);
     const cplx u1 = C(dx / R, dy / R);
     cplx up = u1;
-    o[(size_t)(2 * P) * S] = Hm1;
+    put_h(o + (size_t)(2 * P) * SP, Hm1);
 #pragma unroll
     for (int q = 1; q <= 2 * P; ++q) {
-        o[(size_t)(2 * P + q) * S] = cmul(Hc, up);
+        put_h(o + (size_t)(2 * P + q) * SP, cmul(Hc, up));
         cplx hm = cmul(Hc, cconj(up));
-        o[(size_t)(2 * P - q) * S] = (q & 1) ? C(-hm.x, -hm.y) : hm;
+        put_h(o + (size_t)(2 * P - q) * SP, (q & 1) ? C(-hm.x, -hm.y) : hm);
         if (q < 2 * P) {
             const cplx Hn = csub(cscale(Hc, q * twoz), Hm1);
             Hm1 = Hc;
@@ -279,6 +287,138 @@ __global__ void k_pair_table(const double *__restrict__ xy, int M, double k, dou
             up = cmul(up, u1);
         }
     }
+}
+
+// complex64 table from the FP64 one (row strides S and SP)
+__global__ void k_table_to_c64(const cplx *__restrict__ h, long rows, long S, long SP, float2 *__restrict__ h32) {
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= rows * S) return;
+    const long r = id / S, s = id - r * S;
+    const cplx v = h[id];
+    h32[r * SP + s] = make_float2((float)v.x, (float)v.y);
+}
+
+// b3[s][n] = alpha^l beta_j[n] in complex64 for the source images s = (l+1) M + j, zero for the
+// padding images up to a whole number of 32-image tiles (the phase is applied in FP64)
+__global__ void k_beta_to_b3(const cplx *__restrict__ beta, int M, int nc, long ntot, cplx alpha,
+                             float2 *__restrict__ b3) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ntot) return;
+    const long s = e / nc;
+    const int n = (int)(e - s * nc);
+    float2 v = make_float2(0.f, 0.f);
+    if (s < 3L * M) {
+        const int l1 = (int)(s / M), j = (int)(s - (long)l1 * M);
+        const cplx b = beta[(size_t)j * nc + n];
+        const cplx r = l1 == 1 ? b : cmul(l1 == 2 ? alpha : cconj(alpha), b);
+        v = make_float2((float)r.x, (float)r.y);
+    }
+    b3[e] = v;
+}
+
+// ---- complex64 translation from the complex64 table ---------------------------------------------
+// Each block (WARPS targets) walks its share of the 32-image tiles through a two-stage ring in shared
+// memory: per stage, one TMA tensor copy per warp brings that target's (4p+1) x 32 coefficients
+// h[i][q][t0 .. t0+31] (out-of-range images and rows read as zero), and one bulk copy the tile's
+// phased source coefficients b3 (32 x (2p+1)); a single mbarrier per stage counts all of them.  The
+// lanes then apply the Toeplitz block of packed FMAs exactly as the recomputing kernel does, with
+// the coefficients read from shared memory instead of recurred: the copies of the next tile are in
+// flight meanwhile, so the kernel runs at the FP32 pipe's rate while streaming the table (1.18 GB
+// at M = 1000, p = 12) from HBM.  The self pair holds zeros in the table, so no lane branches.
+// Every wait is bounded (~1 s); a wait that gives up makes the whole block stop, wait (bounded) for
+// its copies still in flight, set *err and return without writing.
+template <int P, int WARPS>
+struct Tab32Layout {
+    static constexpr int NC = 2 * P + 1, NQ = 4 * P + 1;
+    static constexpr int HT = NQ * TILE * 8;            // one warp's coefficient box (bytes)
+    static constexpr int BT = TILE * NC * 8;            // the tile's source coefficients
+    static constexpr int ST = WARPS * HT + BT;          // one stage
+    static constexpr int RED = WARPS * 2 * NC * 33 * 4; // lane sums, reusing stage memory at the end
+    static constexpr int SMEM = 2 * ST + 16 + 1024;     // two stages, two mbarriers, alignment slack
+    static_assert(HT % 128 == 0 && BT % 128 == 0, "tensor-copy destinations must stay 128-byte aligned");
+    static_assert(RED <= 2 * ST, "lane-sum buffer must fit in the stage memory");
+};
+
+template <int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_translate_c64_tab(const __grid_constant__ CUtensorMap tmH, const float2 *__restrict__ b3, int M, int nsplit,
+                    cplx *__restrict__ out, int *__restrict__ err) {
+    using L = Tab32Layout<P, WARPS>;
+    constexpr int NC = L::NC;
+    constexpr long long WAIT = 2000000000LL;   // ~1 s
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s_base = smem_u32(smem), b_full = smem_u32(smem + 2 * L::ST);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WARPS + warp;
+    const int ntile = (3 * M + TILE - 1) / TILE;
+    const int tb0 = (int)((long)ntile * blockIdx.y / nsplit), tb1 = (int)((long)ntile * (blockIdx.y + 1) / nsplit);
+    if (threadIdx.x == 0) {
+        mbar_init(b_full, 1);
+        mbar_init(b_full + 8, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int tb, int st) {
+        const uint32_t bar = b_full + 8 * st, dst = s_base + st * L::ST;
+        mbar_expect_tx(bar, L::ST);
+        for (int w = 0; w < WARPS; ++w)
+            tma_load_2d(dst + w * L::HT, &tmH, bar, tb * TILE, (blockIdx.x * WARPS + w) * L::NQ);
+        bulk_load(dst + WARPS * L::HT, b3 + (size_t)tb * TILE * NC, L::BT, bar);
+    };
+    if (threadIdx.x == 0) {
+        if (tb0 < tb1) issue(tb0, 0);
+        if (tb0 + 1 < tb1) issue(tb0 + 1, 1);
+    }
+    cplxf Pa[NC], Qa[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) Pa[m] = Qa[m] = CF(0.f, 0.f);
+    for (int tb = tb0; tb < tb1; ++tb) {
+        const int st = (tb - tb0) & 1;
+        if (!__syncthreads_and(mbar_wait(b_full + 8 * st, ((tb - tb0) >> 1) & 1, WAIT))) {
+            if (threadIdx.x == 0) {   // copies of tiles tb and tb + 1 may still be in flight
+                mbar_wait(b_full + 8 * st, ((tb - tb0) >> 1) & 1, WAIT);
+                if (tb + 1 < tb1) mbar_wait(b_full + 8 * (st ^ 1), ((tb + 1 - tb0) >> 1) & 1, WAIT);
+                atomicExch(err, 1);
+            }
+            return;
+        }
+        const cplxf *hs = (const cplxf *)(smem + st * L::ST + warp * L::HT);
+        const cplxf *bs = (const cplxf *)(smem + st * L::ST + WARPS * L::HT);
+        cplxf b[NC];
+#pragma unroll
+        for (int n = 0; n < NC; ++n) b[n] = bs[lane * NC + n];
+        {
+            const cplxf h0 = hs[(2 * P) * TILE + lane];
+            const cplxf hr = CF(h0.x, h0.x), hi = CF(h0.y, h0.y);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                Pa[m] = __ffma2_rn(hr, b[m], Pa[m]);
+                Qa[m] = __ffma2_rn(hi, b[m], Qa[m]);
+            }
+        }
+#pragma unroll
+        for (int q = 1; q <= 2 * P; ++q) {
+            const cplxf hq = hs[(2 * P + q) * TILE + lane], hmq = hs[(2 * P - q) * TILE + lane];
+            const cplxf pr = CF(hq.x, hq.x), pi = CF(hq.y, hq.y), mr = CF(hmq.x, hmq.x), mi = CF(hmq.y, hmq.y);
+#pragma unroll
+            for (int m = 0; m + q < NC; ++m) {
+                Pa[m] = __ffma2_rn(pr, b[m + q], Pa[m]);
+                Qa[m] = __ffma2_rn(pi, b[m + q], Qa[m]);
+            }
+#pragma unroll
+            for (int m = q; m < NC; ++m) {
+                Pa[m] = __ffma2_rn(mr, b[m - q], Pa[m]);
+                Qa[m] = __ffma2_rn(mi, b[m - q], Qa[m]);
+            }
+        }
+        __syncthreads();   // stage st is free again
+        if (threadIdx.x == 0 && tb + 2 < tb1) issue(tb + 2, st);
+    }
+    cplxf acc[NC];
+    gs_pq_combine<NC>(Pa, Qa, acc);
+    gs_warp_sum_c64<NC>(acc, (float *)smem + warp * (2 * NC * 33), lane,
+                        (double *)(out + ((size_t)blockIdx.y * M + (i < M ? i : 0)) * NC), i < M);
 }
 
 template <int P, int WARPS>
@@ -348,9 +488,49 @@ __global__ void k_sum_partials(const cplx *part, int nsplit, long len, cplx *out
     out[e] = s;
 }
 
+// complex64 translation from the complex64 table (after gs_ensure_table32 built it)
+template <int P>
+int launch_translate_tab32(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
+    constexpr int WARPS = 4;
+    using L = Tab32Layout<P, WARPS>;
+    const int M = c->M;
+    const int gx = (M + WARPS - 1) / WARPS;
+    const int ntile = (int)((3L * M + TILE - 1) / TILE);
+    // about sixteen blocks per SM in all (two resident at a time), so the last wave stays short
+    int nsplit = (int)((c->sms * 16L + gx - 1) / gx);
+    nsplit = std::max(1, std::min(std::min(nsplit, 64), ntile));
+    const size_t need = (size_t)nsplit * M * (2 * P + 1);
+    cplx *dst = out;
+    if (nsplit > 1) {
+        if (need > c->part_elems) return gs_fail(c, GS_ERR_STATE, "translation scratch too small");
+        dst = c->part;
+    }
+    const long ntot = (long)ntile * TILE * (2 * P + 1);
+    GS_COUNT_LAUNCH(c);
+    k_beta_to_b3<<<(int)((ntot + 255) / 256), 256, 0, c->stream>>>(beta, M, 2 * P + 1, ntot, a.alpha, c->b3pad);
+    cudaEvent_t e0, e1;
+    const bool timed = gs_prof_pair(c, &e0, &e1, GS_C64);
+    if (timed) cudaEventRecord(e0, c->stream);
+    GS_COUNT_LAUNCH(c);
+    k_translate_c64_tab<P, WARPS><<<dim3(gx, nsplit), WARPS * 32, L::SMEM, c->stream>>>(c->tm_h32, c->b3pad, M, nsplit,
+                                                                                        dst, c->terr);
+    if (timed) cudaEventRecord(e1, c->stream);
+    if (nsplit > 1) {
+        const long len = (long)M * (2 * P + 1);
+        GS_COUNT_LAUNCH(c);
+        k_sum_partials<<<(int)((len + 255) / 256), 256, 0, c->stream>>>(c->part, nsplit, len, out);
+    }
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
 template <int P>
 int launch_translate(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out, int precision) {
     constexpr int WARPS = 4;
+    if (precision == GS_C64) {
+        GS_TRY(gs_ensure_table32(c));
+        if (c->htab32) return launch_translate_tab32<P>(c, a, beta, out);
+    }
     const int M = c->M;
     const int gx = (M + WARPS - 1) / WARPS;
     // enough blocks for several waves over the SMs
@@ -403,8 +583,33 @@ template <int P>
 static int build_table(gs_ctx *c) {
     const long tot = 3L * c->M * c->M;
     GS_COUNT_LAUNCH(c);
-    k_pair_table<P><<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d, c->htab);
+    k_pair_table<P, cplx><<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d, c->htab,
+                                                                           3L * c->M);
     GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// complex64 table: rounded from the FP64 table when that exists, else computed in FP64 directly;
+// its tensor map; the kernel's shared-memory attribute (set eagerly, outside any stream capture)
+template <int P>
+static int build_table32(gs_ctx *c) {
+    constexpr int NQ = 4 * P + 1;
+    const long S = 3L * c->M, SP = c->htab32_sp;
+    if (c->htab) {
+        const long tot = (long)c->M * NQ * S;
+        GS_COUNT_LAUNCH(c);
+        k_table_to_c64<<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->htab, (long)c->M * NQ, S, SP, c->htab32);
+    } else {
+        const long tot = S * c->M;
+        GS_COUNT_LAUNCH(c);
+        k_pair_table<P, float2><<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d,
+                                                                                 c->htab32, SP);
+    }
+    GS_CHECK_LAUNCH(c);
+    GS_TRY(gs_make_map_plain(c, &c->tm_h32, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, c->htab32, (long)c->M * NQ, S, SP * 8,
+                             TILE, NQ));
+    GS_CUDA(c, cudaFuncSetAttribute(k_translate_c64_tab<P, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Tab32Layout<P, 4>::SMEM));
     return GS_OK;
 }
 
@@ -423,6 +628,58 @@ int gs_build_pair_table(gs_ctx *c) {
         case 16: return build_table<16>(c);
         default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
     }
+}
+
+// The complex64 translation reads a complex64 copy of the pair table, 3M (rounded up to 32) x M x
+// (4p+1) values (1.18 GB at M = 1000, p = 12), when it fits the table budget (half the free device
+// memory unless set); otherwise (htab32_off) it recomputes the coefficients in FP32 on the fly.
+int gs_ensure_table32(gs_ctx *c) {
+    if (c->htab32 || c->htab32_off) return GS_OK;
+    const long SP = (3L * c->M + TILE - 1) / TILE * TILE;
+    const size_t bytes = sizeof(float2) * (size_t)SP * c->M * (4 * c->p + 1);
+    size_t fr = 0, totm = 0;
+    GS_CUDA(c, cudaMemGetInfo(&fr, &totm));
+    const double budget = c->table_budget_gb >= 0 ? c->table_budget_gb * 1e9 : 0.5 * (double)fr;
+    if ((double)bytes > budget || cudaMalloc((void **)&c->htab32, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->htab32 = nullptr;
+        c->htab32_off = true;
+        return GS_OK;
+    }
+    c->htab32_sp = SP;
+    int st;
+    switch (c->p) {
+        case 1: st = build_table32<1>(c); break;
+        case 2: st = build_table32<2>(c); break;
+        case 3: st = build_table32<3>(c); break;
+        case 4: st = build_table32<4>(c); break;
+        case 5: st = build_table32<5>(c); break;
+        case 6: st = build_table32<6>(c); break;
+        case 7: st = build_table32<7>(c); break;
+        case 8: st = build_table32<8>(c); break;
+        case 10: st = build_table32<10>(c); break;
+        case 12: st = build_table32<12>(c); break;
+        case 16: st = build_table32<16>(c); break;
+        default: st = gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+    if (st != GS_OK) {
+        cudaFree(c->htab32);
+        c->htab32 = nullptr;
+        c->htab32_off = true;
+    }
+    return st;
+}
+
+// GS_ERR_TIMEOUT (and the flag cleared) if a bounded wait of the table-driven complex64 translation
+// gave up since the last check; synchronises the stream
+int gs_check_table_wait(gs_ctx *c) {
+    if (!c->terr) return GS_OK;
+    int h = 0;
+    GS_CUDA(c, cudaMemcpyAsync(&h, c->terr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!h) return GS_OK;
+    GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), c->stream));
+    return gs_fail(c, GS_ERR_TIMEOUT, "complex64 translation: a device wait gave up");
 }
 
 // The complex64 translation keeps the Hankel values in their natural scale: the largest is
