@@ -54,6 +54,8 @@ except (OSError, ValueError):
 # capture of k_translate_f64_tab at M = 500 (599.58 MB over 3 * 500^2 - 500 pairs); the pair table
 # (49 complex128 per pair) is 784 B of it.  Update with a new capture whenever that kernel changes.
 TAB_DRAM_BYTES_PER_PAIR = 599.577344e6 / (3 * 500 ** 2 - 500)
+# complex64 pair table: 4p + 1 = 49 complex64 coefficients per pair image (p = 12)
+TAB32_BYTES_PER_PAIR = 49 * 8
 
 
 def load_golden(path=GOLDEN):
@@ -166,6 +168,9 @@ def parse():
     ap.add_argument("--no-warm", action="store_true")
     ap.add_argument("--warm-train", type=int, default=24, help="warm start: training sweep points")
     ap.add_argument("--warm-eval", type=int, default=6, help="warm start: held-out sweep points")
+    ap.add_argument("--warm-geometry", choices=["headline", "mixed4000"], default="headline",
+                    help="warm start: the swept geometry (mixed4000: M = 4000 disks of radius 0.004; its "
+                         "held-out points are then solved in the mixed form, FP64 GMRES taking ~40 s each)")
     ap.add_argument("--no-big", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-field", action="store_true")
@@ -173,6 +178,9 @@ def parse():
     ap.add_argument("--angles", type=int, default=16,
                     help="multi-angle variant: incidence angles of the headline geometry solved in lockstep")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--one-solve", choices=["fp64", "c64"], default=None,
+                    help="profiler capture: one warm-up solve of the headline workload, then one solve "
+                         "bracketed by cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--study", action="store_true",
                     help="disk analogues of the paper's Example 1 (homogeneous vs layered, M = 100/500/1000) "
                          "and Example 3 (k2 = 1, 10, 20, 30): GMRES iterations, time, flux; one JSON line")
@@ -407,6 +415,26 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     cfg0 = W.config("headline", seed=1)
+    if args.one_solve:
+        prec = GS_C64 if args.one_solve == "c64" else GS_FP64
+        gs = GratingSolver(local)
+        gs.set_layers(cfg0["grating"])
+        gs.set_incidence([cfg0["theta"]])
+        gs.set_inclusions(cfg0["disks"])
+        gs.factor()
+        gs.solve(tol=cfg0["tol"], maxit=4000, restart=500, precision=prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        gs.solve(tol=cfg0["tol"], maxit=4000, restart=500, precision=prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        torch.cuda.profiler.stop()
+        its, rr = gs.stats()
+        print(json.dumps({"one_solve": args.one_solve, "workload": WORKLOAD, "solve_ms": 1e3 * (t1 - t0),
+                          "iterations": its, "relres": rr, "refinement_sweeps": gs.refinement_sweeps(0)}))
+        gs.close()
+        return
     if args.kernel_only and os.environ.get("GS_BENCH_M"):
         # smaller case of the same kernel for profiler captures (same grating, disk size and order)
         cfg0["disks"] = W.disks(int(os.environ["GS_BENCH_M"]), 0.008, 0.004, 2.0, cfg0["grating"]["k"][0],
@@ -433,6 +461,7 @@ def main():
     torch.cuda.synchronize()
     couple_ms = e[1].elapsed_time(e[2])
     grating_ms = e[0].elapsed_time(e[1]) - couple_ms
+    factor_stats = gs.factor_stats(0)
 
     if args.kernel_only and os.environ.get("GS_BENCH_PRECISION") == "batch":
         # batched complex64 translation: the bench's eight uneven-M geometries at the Wood angle
@@ -849,14 +878,17 @@ def main():
         from paper_1412_7466_gb300.warmstart import SweepTrainer
         n_tr, n_ev = args.warm_train, args.warm_eval
         pts = W.sweep_points(n_tr + n_ev, seed=5)
-        geo = cfg0["disks"]
+        big_w = args.warm_geometry == "mixed4000"
+        geo = W.config("mixed4000", seed=1)["disks"] if big_w else cfg0["disks"]
+        Mw = geo["xy"].shape[0]
+        eval_prec = GS_C64 if big_w else GS_FP64
         gw = GratingSolver(local)
         tr = SweepTrainer(gw, p)
         k_lo, k_hi = 35.0, 45.0
 
         def load_point(phi, kt):
             dk = dict(geo)
-            dk["kp"] = np.full(M, 2.0 * kt)               # index 2 relative to k_top
+            dk["kp"] = np.full(Mw, 2.0 * kt)              # index 2 relative to k_top
             gw.set_layers(W.scaled_grating("headline", kt))
             gw.set_incidence([-math.pi / 2 + phi])
             gw.set_inclusions(dk)
@@ -879,7 +911,7 @@ def main():
             load_point(*pts[q])
             a_, b_ = ev(), ev()
             a_.record(stream)
-            gw.solve(tol=tol, maxit=4000, restart=500, precision=GS_FP64)
+            gw.solve(tol=tol, maxit=8000, restart=500, precision=eval_prec)
             brz = gw.bragg()
             b_.record(stream)
             b_.synchronize()
@@ -888,7 +920,7 @@ def main():
             a_, b_ = ev(), ev()
             a_.record(stream)
             b0, r0, used = gw.warm_start()
-            gw.solve(tol=tol, maxit=4000, restart=500, precision=GS_FP64, beta0=b0)
+            gw.solve(tol=tol, maxit=8000, restart=500, precision=eval_prec, beta0=b0)
             brw = gw.bragg()
             b_.record(stream)
             b_.synchronize()
@@ -898,7 +930,8 @@ def main():
             bdiff.append(float(np.linalg.norm(np.r_[brw["c"], brw["d"]] - np.r_[brz["c"], brz["d"]]) /
                                np.linalg.norm(np.r_[brz["c"], brz["d"]])))
         gw.close()
-        wres = {"value": n_ev / tw, "unit": "solves/s", "dtype": "f64 (network bf16/fp32)",
+        wres = {"value": n_ev / tw, "unit": "solves/s",
+                "dtype": ("c64 translation + f64 refinement" if big_w else "f64") + " (network bf16/fp32)",
                 "zero_start_value": n_ev / tz,
                 "gmres_iters_zero_start": it_z, "gmres_iters_warm_start": it_w,
                 "initial_relres_warm_start": rel0,
@@ -906,9 +939,11 @@ def main():
                 "train_solves": n_tr, "eval_solves": n_ev, "train_epochs": len(hist),
                 "train_loss_first_last": [hist[0], hist[-1]],
                 "collect_s": t1 - t0, "train_s": t2 - t1,
-                "sweep": "headline geometry (M=1000, r=0.008, p=12), k=(1,1.5,2) k_top, kp=2 k_top, "
-                         f"(phi, k_top) iid in [-pi/3, pi/3] x [35, 45] (seed 5); first {n_tr} points train "
-                         f"(complex64 + FP64 refinement to 1e-9), next {n_ev} evaluate (FP64 GMRES to 1e-11)",
+                "sweep": (("M=4000 geometry (r=0.004" if big_w else "headline geometry (M=1000, r=0.008")
+                          + ", p=12), k=(1,1.5,2) k_top, kp=2 k_top, "
+                          f"(phi, k_top) iid in [-pi/3, pi/3] x [35, 45] (seed 5); first {n_tr} points train "
+                          f"(complex64 + FP64 refinement to 1e-9), next {n_ev} evaluate ("
+                          + ("mixed complex64 + FP64 refinement" if big_w else "FP64 GMRES") + " to 1e-11)"),
                 "step": "warm_start (features, network, start, FP64 residual check) + solve + Bragg; "
                         "the grating factorisation per sweep point is outside the timed region"}
 
@@ -955,7 +990,7 @@ def main():
                    "l2": "inputs larger than L2: B (482 MB) and C (506 MB) are rebuilt and streamed every step"},
         "gmres_iters": r64["iters"], "bragg_rel_err_vs_oracle": res["fp64"]["err"],
         "bragg_max_elementwise_rel_err_vs_oracle": res["fp64"]["err_el"], "flux_err": res["fp64"]["flux"],
-        "grating_factor_ms": grating_ms, "coupling_ms": couple_ms,
+        "grating_factor_ms": grating_ms, "grating_factor_phases": factor_stats, "coupling_ms": couple_ms,
         "value_incl_grating_factor": 1.0 / (r64["elapsed"] / args.steps + per_step_grating),
         "pair_translations_per_s": (3 * M * M - M) * n64 / (ms64 * 1e-3) if ms64 > 0 else None,
         "roofline": {"bound": "alu", "kernel": "k_translate_f64_tab<12>", "achieved": ach64, "peak": peak64,
@@ -974,11 +1009,20 @@ def main():
             "plain_fp64": variant("fp64", value, r64, "f64"),
             "mixed_c64_ir": dict(variant("mixed_c64_ir", value_mx, rmx, "c64 translation + f64 refinement"),
                                  pre_refinement_bragg_rel_err=pre_err,
-                                 roofline={"bound": "alu", "kernel": "k_translate_c64<12>", "achieved": ach32,
+                                 roofline={"bound": "alu", "kernel": "k_translate_c64_tab<12>", "achieved": ach32,
                                            "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
                                            "peak_source": "measured: packed FP32 (fma.rn.f32x2) FMA-chain probe "
                                                           "(gs_probe_fma); scalar FFMA probe "
                                                           f"{peak32_scalar:.1f} TFLOP/s",
+                                           "flops_per_launch": flops_per_launch,
+                                           # the complex64 table streams from HBM at the same time
+                                           "hbm": {"bytes_per_launch": TAB32_BYTES_PER_PAIR * (3 * M * M),
+                                                   "achieved_gbs": TAB32_BYTES_PER_PAIR * (3 * M * M)
+                                                   / (avg32 * 1e-3) / 1e9,
+                                                   "frac": TAB32_BYTES_PER_PAIR * (3 * M * M) / (avg32 * 1e-3)
+                                                   / 1e9 / PEAKS.get("hbm_gbs", 1.0),
+                                                   "peak": PEAKS.get("hbm_gbs"),
+                                                   "unit": "GB/s"},
                                            "avg_launch_ms": avg32, "launches_timed": nmx32,
                                            "fp64_residual_launches": nmx64,
                                            "fp64_residual_ms": ms_mx64}),

@@ -214,6 +214,14 @@ int gs_get_beta(gs_ctx *ctx, int angle, gs_c128 *beta_dev);
 int gs_stats(gs_ctx *ctx, int angle, int *iters, double *relres);
 /* Number of FP64 refinement sweeps of the last GS_C64 solve (0 after an FP64 solve). */
 int gs_stats_refinement(gs_ctx *ctx, int angle, int *outer);
+/* Statistics of the angle's factorisation of the empty grating (Sec. 5 "We precompute A = U Sigma
+ * V^*"): the FP32 and FP64 one-sided Jacobi sweeps it took and, in phase_ms[6] (host, nullable),
+ * the device time in ms of its phases: assembly of A and f, pivoted QR, FP32 sweeps, orthogonal
+ * polar step and R^* V, FP64 sweeps, U = Q V_x and V Sigma; in rot32[32], rot64[32] (host,
+ * nullable) the pair rotations applied in each sweep (0 past the last).  GS_ERR_STATE before the
+ * grating is factored (gs_factor or gs_factor_batch), GS_ERR_ARG for a bad angle.  Host-only. */
+int gs_factor_stats(gs_ctx *ctx, int angle, int *sweeps32, int *sweeps64, double *phase_ms, long long *rot32,
+                    long long *rot64);
 /* Bragg amplitudes of the propagating orders (Sec. 2 rad1/rad2; Sec. 5 alpha = A^+(f - C beta)),
  * written to HOST arrays: orders_top[*n_top], c[*n_top], orders_bot[*n_bot], d[*n_bot], each of
  * capacity >= 2 K_rb + 1, and the relative flux error

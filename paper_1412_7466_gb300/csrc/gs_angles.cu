@@ -34,7 +34,8 @@ struct gs_angles {
     cplx *X = nullptr, *Y = nullptr, *T = nullptr, *b = nullptr, *r = nullptr, *dx = nullptr, *x = nullptr;
     int *active = nullptr, *jdev = nullptr, *kk = nullptr, *err = nullptr;
     cplx *Vk = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gg = nullptr, *yy = nullptr, *hp = nullptr;
-    double *nrm = nullptr, *res = nullptr;
+    double *nrm = nullptr, *res = nullptr, *npart = nullptr;   // R, R, R x SEG_NQ
+    float2 *w32 = nullptr, *cf32 = nullptr;                      // N, R x (kdim+1): complex64 CGS2 operands
     double *hbuf = nullptr;            // pinned host: R residuals + the error flag
     cudaGraphExec_t step = nullptr;
     unsigned long long step_kernels = 0;   // kernels in one replay of the step graph
@@ -86,6 +87,9 @@ void angles_free(gs_angles *A) {
     afree(A->gg);
     afree(A->yy);
     afree(A->hp);
+    afree(A->npart);
+    afree(A->w32);
+    afree(A->cf32);
     afree(A->nrm);
     afree(A->res);
     if (A->hbuf) cudaFreeHost(A->hbuf);
@@ -138,6 +142,9 @@ int angles_setup(gs_ctx *c, int restart) {
     GS_TRY(aalloc(c, &A->Vk, ((size_t)ld * N + 1) / 2));
     GS_TRY(aalloc(c, &A->H, (size_t)R * kdim * ld));
     for (cplx **v : {&A->cs, &A->sn, &A->gg, &A->yy, &A->hp}) GS_TRY(aalloc(c, v, (size_t)R * ld));
+    GS_TRY(aalloc(c, &A->cf32, (size_t)R * ld));
+    GS_TRY(aalloc(c, &A->w32, (size_t)A->N));
+    GS_TRY(aalloc(c, &A->npart, (size_t)R * SEG_NQ));
     GS_TRY(aalloc(c, &A->nrm, R));
     GS_TRY(aalloc(c, &A->res, R));
     GS_CUDA(c, cudaMallocHost((void **)&A->hbuf, sizeof(double) * (R + 1)));
@@ -172,23 +179,9 @@ int angles_step(gs_ctx *c, gs_angles *A) {
     GS_COUNT_LAUNCH(c);
     k_seg_fetch<float2><<<eb, 256, 0, st>>>(V, N, A->jdev, A->X);
     GS_TRY(angles_apply_c64(c, A, A->X, A->Y));
-    dim3 gd(A->kdim, R);
-    GS_COUNT_LAUNCH(c);
-    k_seg_dots<float2><<<gd, 256, 0, st>>>(V, N, A->Y, A->geo, nc, A->jdev, A->active, A->H, ld, A->kdim, 0);
-    GS_COUNT_LAUNCH(c);
-    k_seg_sub<float2><<<eb, 256, 0, st>>>(A->Y, V, N, A->gid, nc, A->jdev, A->active, A->H, ld, A->kdim, nullptr, 0);
-    GS_COUNT_LAUNCH(c);
-    k_seg_dots2<float2><<<gd, 256, 0, st>>>(V, N, A->Y, A->geo, nc, A->jdev, A->active, A->hp, ld);
-    GS_COUNT_LAUNCH(c);
-    k_seg_sub<float2><<<eb, 256, 0, st>>>(A->Y, V, N, A->gid, nc, A->jdev, A->active, A->H, ld, A->kdim, A->hp, ld);
-    GS_COUNT_LAUNCH(c);
-    k_seg_addh<<<R, 256, 0, st>>>(A->H, ld, A->kdim, A->hp, ld, A->jdev, A->active, R);
-    GS_COUNT_LAUNCH(c);
-    k_seg_norm<<<R, 256, 0, st>>>(A->Y, A->geo, nc, A->active, A->nrm, A->H, ld, A->kdim, A->jdev);
-    GS_COUNT_LAUNCH(c);
-    k_seg_scale<float2><<<eb, 256, 0, st>>>(A->Y, V, N, A->gid, nc, A->jdev, A->active, A->nrm);
-    GS_COUNT_LAUNCH(c);
-    k_seg_givens<<<R, 128, 0, st>>>(A->H, ld, A->kdim, A->jdev, A->active, A->cs, A->sn, A->gg, A->res, R);
+    const SegStep ss{A->geo, A->gid, A->active, A->jdev, A->H, A->hp, A->cs, A->sn, A->gg, A->nrm, A->res, A->npart,
+                     A->w32, A->cf32, N, R, A->kdim, nc};
+    GS_TRY(seg_cgs2<float2>(c, ss, V, A->Y, st));
     GS_COUNT_LAUNCH(c);
     k_inc<<<1, 32, 0, st>>>(A->jdev);
     GS_CHECK_LAUNCH(c);

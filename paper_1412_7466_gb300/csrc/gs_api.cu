@@ -101,11 +101,10 @@ void free_geometry(gs_ctx *c) {
     dfree(c->xdf);
     dfree(c->iflag);
     dfree(c->htab);
-    dfree(c->htab32);
-    c->htab32_sp = 0;
-    c->htab32_off = false;
+    dfree(c->tab32.h);
+    c->tab32.sp = 0;
+    c->tab32_off = false;
     dfree(c->b3pad);
-    dfree(c->terr);
     gs_angles_destroy(c);
     if (c->tcA) cudaFree(c->tcA);
     c->tcA = nullptr;
@@ -288,7 +287,9 @@ int gs_create(gs_ctx **out, int device, void *cuda_stream) {
     }
     if (cudaMalloc((void **)&c->dscal, sizeof(double) * 16) != cudaSuccess ||
         cudaMallocHost((void **)&c->hscal, sizeof(double) * 16) != cudaSuccess ||
-        cudaMalloc((void **)&c->dcount, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc((void **)&c->dcount, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&c->terr, sizeof(int)) != cudaSuccess || cudaMemset(c->terr, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&c->bar, 2 * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         gs_destroy(c);
         return GS_ERR_OOM;
@@ -318,6 +319,8 @@ void gs_destroy(gs_ctx *c) {
     dfree(c->s);
     dfree(c->dscal);
     dfree(c->dcount);
+    dfree(c->terr);
+    dfree(c->bar);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->hscal) cudaFreeHost(c->hscal);
     delete c;
@@ -616,8 +619,6 @@ int gs_factor(gs_ctx *c) {
     GS_TRY(dalloc(c, &c->b32, n));
     GS_TRY(dalloc(c, &c->img32, 3 * (size_t)c->M));
     GS_TRY(dalloc(c, &c->b3pad, (size_t)((3L * c->M + 31) / 32) * 32 * c->nc));
-    GS_TRY(dalloc(c, &c->terr, 1));
-    GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), c->stream));
     GS_TRY(dalloc(c, &c->xdf, n));
     GS_TRY(dalloc(c, &c->iflag, 1));
     GS_TRY(gs_build_images_c64(c, c->xy, c->M, c->img32, c->stream));
@@ -727,7 +728,7 @@ int gs_translate(gs_ctx *c, int angle, const gs_c128 *beta_dev, gs_c128 *alpha_d
         return gs_fail(c, GS_ERR_ARG, "null or aliased vectors");
     if (precision != GS_FP64 && precision != GS_C64) return gs_fail(c, GS_ERR_ARG, "bad precision");
     GS_TRY(gs_translate_impl(c, c->ang[angle], (const cplx *)beta_dev, (cplx *)alpha_dev, precision));
-    return precision == GS_C64 && c->htab32 ? gs_check_table_wait(c) : GS_OK;
+    return precision == GS_C64 && c->tab32.h ? gs_check_table_wait(c) : GS_OK;
 }
 
 int gs_apply(gs_ctx *c, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int precision) {
@@ -736,7 +737,7 @@ int gs_apply(gs_ctx *c, int angle, const gs_c128 *x_dev, gs_c128 *y_dev, int pre
     if (!x_dev || !y_dev || x_dev == (const gs_c128 *)y_dev) return gs_fail(c, GS_ERR_ARG, "null or aliased vectors");
     if (precision != GS_FP64 && precision != GS_C64) return gs_fail(c, GS_ERR_ARG, "bad precision");
     GS_TRY(gs_apply_impl(c, c->ang[angle], (const cplx *)x_dev, (cplx *)y_dev, precision));
-    return precision == GS_C64 && c->htab32 ? gs_check_table_wait(c) : GS_OK;
+    return precision == GS_C64 && c->tab32.h ? gs_check_table_wait(c) : GS_OK;
 }
 
 int gs_rhs(gs_ctx *c, int angle, gs_c128 *b_dev) {

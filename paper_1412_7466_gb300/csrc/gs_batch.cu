@@ -233,7 +233,8 @@ __global__ void k_batch_UH(const cplx *__restrict__ U, int m, int nr, int cols, 
 
 // xo[g][i] = dscale[i] sum_j Vr[i, j] w[g][j] for i < nrow
 __global__ void k_batch_V(const cplx *__restrict__ Vr, int nrow, int cols, const cplx *__restrict__ w,
-                          const double *__restrict__ dscale, int G, const int *__restrict__ active, cplx *__restrict__ xo) {
+                          const double *__restrict__ dscale, int G, const int *__restrict__ active, cplx *__restrict__ xo,
+                          float2 *__restrict__ xo32 = nullptr) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= G * nrow) return;
     int i = warp / G, g = warp % G;
@@ -244,7 +245,11 @@ __global__ void k_batch_V(const cplx *__restrict__ Vr, int nrow, int cols, const
     for (int j = lane; j < cols; j += 32) cfma(s, a[j], __ldg(&v[j]));
     s.x = warp_sum(s.x);
     s.y = warp_sum(s.y);
-    if (lane == 0) xo[(size_t)g * nrow + i] = cscale(s, dscale[i]);
+    if (lane == 0) {
+        const cplx r = cscale(s, dscale[i]);
+        xo[(size_t)g * nrow + i] = r;
+        if (xo32) xo32[(size_t)g * nrow + i] = make_float2((float)r.x, (float)r.y);   // complex64 copy
+    }
 }
 
 // y[r] = x[r] - s[r] t[r] + s[r] (B_g v_g)[r]  (x, t nullable); v_g = vv + g * ldv
@@ -273,7 +278,7 @@ __global__ void k_batch_Bcombine(const cplx *__restrict__ Ball, long Ntot, int n
 // complex64 copy of B_g (FP32 products) for the mixed form's inner operator: B acts after A^+, so its
 // rounding is not amplified; C_g x stays FP64 (it feeds A^+, whose clipped Sigma^+ would)
 __global__ void k_batch_Bcombine32(const float2 *__restrict__ Ball, long Ntot, int nB, const int *__restrict__ gid,
-                                   int nc, const int *__restrict__ active, const cplx *__restrict__ vv, int ldv,
+                                   int nc, const int *__restrict__ active, const float2 *__restrict__ vv, int ldv,
                                    const cplx *__restrict__ x, const cplx *__restrict__ t, const cplx *__restrict__ s,
                                    cplx *__restrict__ y) {
     long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -282,15 +287,24 @@ __global__ void k_batch_Bcombine32(const float2 *__restrict__ Ball, long Ntot, i
     const int g = gid[warp / nc];
     if (active && !active[g]) return;
     const float2 *b = Ball + (size_t)warp * nB;
-    const cplx *v = vv + (size_t)g * ldv;
-    float re = 0.f, im = 0.f;
-    for (int c = lane; c < nB; c += 32) {
-        const float2 m = b[c];
-        const cplx w = __ldg(&v[c]);
-        const float wr = (float)w.x, wi = (float)w.y;
-        re = fmaf(m.x, wr, fmaf(-m.y, wi, re));
-        im = fmaf(m.x, wi, fmaf(m.y, wr, im));
+    const float2 *v = vv + (size_t)g * ldv;   // complex64 (no per-entry FP64 -> FP32 conversion)
+    float re = 0.f, im = 0.f, re1 = 0.f, im1 = 0.f;
+    int c = lane;
+    for (; c + 32 < nB; c += 64) {
+        const float2 m0 = __ldcs(&b[c]), m1 = __ldcs(&b[c + 32]);
+        const float2 w0 = __ldg(&v[c]), w1 = __ldg(&v[c + 32]);
+        re = fmaf(m0.x, w0.x, fmaf(-m0.y, w0.y, re));
+        im = fmaf(m0.x, w0.y, fmaf(m0.y, w0.x, im));
+        re1 = fmaf(m1.x, w1.x, fmaf(-m1.y, w1.y, re1));
+        im1 = fmaf(m1.x, w1.y, fmaf(m1.y, w1.x, im1));
     }
+    if (c < nB) {
+        const float2 m0 = __ldcs(&b[c]), w0 = __ldg(&v[c]);
+        re = fmaf(m0.x, w0.x, fmaf(-m0.y, w0.y, re));
+        im = fmaf(m0.x, w0.y, fmaf(m0.y, w0.x, im));
+    }
+    re += re1;
+    im += im1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -407,6 +421,9 @@ struct gs_batch {
     float4 *xdf = nullptr;         // Ntot: double-float split of the operator input
     int *dflag = nullptr;          // range flag of the double-float split of C
     cplx *gC = nullptr, *w = nullptr, *xv = nullptr;   // G nC, G cols, G cols
+    float2 *xv32 = nullptr;        // G cols: complex64 copy of xv (the B_phys input of the mixed operator)
+    float2 *w32 = nullptr, *cf32 = nullptr;   // Ntot; G x (kdim+1): complex64 CGS2 operands
+    double *npart = nullptr;       // G x SEG_NQ partial squared norms
     int *active = nullptr;
     // GMRES
     int kdim = 0;
@@ -417,6 +434,13 @@ struct gs_batch {
     // graphs of one Arnoldi step, per precision, for one angle
     cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
     int step_angle[2] = {-1, -1};
+    // complex64 pair tables of all geometries (mixed inner translation; empty when they do not all
+    // fit the table budget, and the persistent recomputing kernel runs instead), with the scratch of
+    // one geometry's table translation (largest geometry)
+    std::vector<gs_tab32> tab32;
+    float2 *b3 = nullptr;
+    cplx *tpart = nullptr;
+    size_t tpart_elems = 0;
     // per-geometry statistics (per angle)
     std::vector<std::vector<int>> iters;
     std::vector<std::vector<double>> relres;
@@ -439,6 +463,9 @@ void batch_free(gs_batch *b) {
     for (auto &p : b->C2) dfree_b(p);
     for (auto &p : b->Cm) dfree_b(p);
     for (auto &p : b->beta) dfree_b(p);
+    for (auto &t : b->tab32) dfree_b(t.h);
+    dfree_b(b->b3);
+    dfree_b(b->tpart);
     dfree_b(b->items);
     dfree_b(b->counter);
     dfree_b(b->part);
@@ -459,6 +486,10 @@ void batch_free(gs_batch *b) {
     dfree_b(b->gC);
     dfree_b(b->w);
     dfree_b(b->xv);
+    dfree_b(b->xv32);
+    dfree_b(b->w32);
+    dfree_b(b->cf32);
+    dfree_b(b->npart);
     dfree_b(b->active);
     dfree_b(b->Vk);
     dfree_b(b->H);
@@ -517,6 +548,13 @@ int launch_batch_translate(gs_ctx *c, gs_batch *b, const AngleData &a, const cpl
                            const int *active) {
     cudaStream_t st = c->stream;
     const int sms = c->sms;
+    if (precision == GS_C64 && !b->tab32.empty()) {
+        // one table-driven launch per geometry (masked ones return at once)
+        for (int g = 0; g < b->G; ++g)
+            GS_TRY(gs_tab32_translate(c, b->tab32[g], b->M[g], b->p, x + b->noff[g], a.alpha, b->b3, b->tpart,
+                                      b->tpart_elems, out + b->noff[g], active ? active + g : nullptr, st));
+        return GS_OK;
+    }
     if (precision == GS_C64) {
         GS_COUNT_LAUNCH(c);
         k_b_to_c64<<<nblk(b->Ntot), 256, 0, st>>>(x, b->Ntot, b->b32);
@@ -574,11 +612,12 @@ int batch_apply(gs_ctx *c, gs_batch *b, int angle, const cplx *x, cplx *y, int p
     GS_COUNT_LAUNCH(c);
     k_batch_UH<<<wblk((long)b->G * cols), 256, 0, st>>>(a.W, ly.rows, nC, cols, b->gC, nC, a.coef, b->G, active, b->w);
     GS_COUNT_LAUNCH(c);
-    k_batch_V<<<wblk((long)b->G * nB), 256, 0, st>>>(a.Vr, nB, cols, b->w, a.dscale, b->G, active, b->xv);
+    k_batch_V<<<wblk((long)b->G * nB), 256, 0, st>>>(a.Vr, nB, cols, b->w, a.dscale, b->G, active, b->xv,
+                                                       precision == GS_C64 ? b->xv32 : nullptr);
     GS_COUNT_LAUNCH(c);
     if (precision == GS_C64) {
-        k_batch_Bcombine32<<<wblk(b->Ntot), 256, 0, st>>>(b->B32[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv, nB,
-                                                           x, b->T, b->s, y);
+        k_batch_Bcombine32<<<wblk(b->Ntot), 256, 0, st>>>(b->B32[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv32,
+                                                           nB, x, b->T, b->s, y);
     } else {
         k_batch_Bcombine<<<wblk(b->Ntot), 256, 0, st>>>(b->B[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv, nB, x,
                                                          b->T, b->s, y);
@@ -618,28 +657,13 @@ template <typename TB>
 int arnoldi_step_t(gs_ctx *c, gs_batch *b, int angle, int precision) {
     cudaStream_t st = c->stream;
     const long N = b->Ntot;
-    const int ld = b->kdim + 1, eb = nblk(N);
     TB *V = (TB *)b->Vk;
     GS_COUNT_LAUNCH(c);
-    k_seg_fetch<TB><<<eb, 256, 0, st>>>(V, N, b->jdev, b->X);
+    k_seg_fetch<TB><<<nblk(N), 256, 0, st>>>(V, N, b->jdev, b->X);
     GS_TRY(batch_apply(c, b, angle, b->X, b->Y, precision, b->active));
-    dim3 gd(b->kdim, b->G);
-    GS_COUNT_LAUNCH(c);
-    k_seg_dots<TB><<<gd, 256, 0, st>>>(V, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->H, ld, b->kdim, 0);
-    GS_COUNT_LAUNCH(c);
-    k_seg_sub<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, nullptr, 0);
-    GS_COUNT_LAUNCH(c);
-    k_seg_dots2<TB><<<gd, 256, 0, st>>>(V, N, b->Y, b->geo, b->nc, b->jdev, b->active, b->hp, ld);
-    GS_COUNT_LAUNCH(c);
-    k_seg_sub<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->H, ld, b->kdim, b->hp, ld);
-    GS_COUNT_LAUNCH(c);
-    k_seg_addh<<<b->G, 256, 0, st>>>(b->H, ld, b->kdim, b->hp, ld, b->jdev, b->active, b->G);
-    GS_COUNT_LAUNCH(c);
-    k_seg_norm<<<b->G, 256, 0, st>>>(b->Y, b->geo, b->nc, b->active, b->nrm, b->H, ld, b->kdim, b->jdev);
-    GS_COUNT_LAUNCH(c);
-    k_seg_scale<TB><<<eb, 256, 0, st>>>(b->Y, V, N, b->gid, b->nc, b->jdev, b->active, b->nrm);
-    GS_COUNT_LAUNCH(c);
-    k_seg_givens<<<b->G, 128, 0, st>>>(b->H, ld, b->kdim, b->jdev, b->active, b->cs, b->sn, b->gg, b->res, b->G);
+    const SegStep ss{b->geo, b->gid, b->active, b->jdev, b->H, b->hp, b->cs, b->sn, b->gg, b->nrm, b->res, b->npart,
+                     b->w32, b->cf32, N, b->G, b->kdim, b->nc};
+    GS_TRY(seg_cgs2<TB>(c, ss, V, b->Y, st));
     GS_COUNT_LAUNCH(c);
     k_inc<<<1, 32, 0, st>>>(b->jdev);
     GS_CHECK_LAUNCH(c);
@@ -784,6 +808,9 @@ int ensure_krylov(gs_ctx *c, gs_batch *b, int restart) {
     GS_TRY(dalloc_b(c, &b->gg, (size_t)G * ld));
     GS_TRY(dalloc_b(c, &b->yy, (size_t)G * ld));
     GS_TRY(dalloc_b(c, &b->hp, (size_t)G * ld));
+    GS_TRY(dalloc_b(c, &b->cf32, (size_t)G * ld));
+    GS_TRY(dalloc_b(c, &b->w32, (size_t)b->Ntot));
+    GS_TRY(dalloc_b(c, &b->npart, (size_t)G * SEG_NQ));
     return GS_OK;
 }
 
@@ -1003,6 +1030,7 @@ int gs_factor_batch(gs_ctx *c) {
     GS_TRY(dalloc_b(c, &b->gC, (size_t)G * ly.nC()));
     GS_TRY(dalloc_b(c, &b->w, (size_t)G * ly.cols));
     GS_TRY(dalloc_b(c, &b->xv, (size_t)G * ly.cols));
+    GS_TRY(dalloc_b(c, &b->xv32, (size_t)G * ly.cols));
     GS_TRY(dalloc_b(c, &b->active, G));
     GS_TRY(ensure_krylov(c, b, 200));
     GS_TRY(dalloc_b(c, &b->nrm, G));
@@ -1017,6 +1045,41 @@ int gs_factor_batch(gs_ctx *c) {
     GS_TRY(build_items(c, b, b->chunk));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     GS_TRY(autotune(c, b, 0));
+    // complex64 pair tables for the mixed inner translation, when all of them fit the table budget
+    for (auto &t : b->tab32) dfree_b(t.h);
+    b->tab32.clear();
+    dfree_b(b->b3);
+    dfree_b(b->tpart);
+    {
+        size_t need = 0;
+        int Mmax = 0;
+        for (int g = 0; g < G; ++g) {
+            need += gs_tab32_bytes(b->M[g], b->p);
+            Mmax = std::max(Mmax, b->M[g]);
+        }
+        size_t fr = 0, totm = 0;
+        GS_CUDA(c, cudaMemGetInfo(&fr, &totm));
+        const double budget = c->table_budget_gb >= 0 ? c->table_budget_gb * 1e9 : 0.5 * (double)fr;
+        if ((double)need <= budget) {
+            b->tab32.assign(G, gs_tab32());
+            int r = GS_OK;
+            for (int g = 0; g < G && r == GS_OK; ++g)
+                r = gs_tab32_build(c, b->xy + 2 * (size_t)b->moff[g], b->M[g], b->p, nullptr, &b->tab32[g], c->stream);
+            if (r == GS_OK) {
+                b->tpart_elems = (size_t)64 * Mmax * b->nc;
+                r = dalloc_b(c, &b->b3, (size_t)((3L * Mmax + 31) / 32) * 32 * b->nc);
+                if (r == GS_OK) r = dalloc_b(c, &b->tpart, b->tpart_elems);
+            }
+            if (r != GS_OK) {
+                for (auto &t : b->tab32) dfree_b(t.h);
+                b->tab32.clear();
+                dfree_b(b->b3);
+                dfree_b(b->tpart);
+                if (r != GS_ERR_OOM) return r;
+                cudaGetLastError();
+            }
+        }
+    }
     for (int q = 0; q < 2; ++q)
         if (b->step_exec[q]) {
             cudaGraphExecDestroy(b->step_exec[q]);

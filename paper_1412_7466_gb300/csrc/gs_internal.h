@@ -9,6 +9,14 @@
 #include "../../include/gsolve.h"
 #include "gs_common.cuh"
 
+// complex64 pair table h[i][q][s] of one geometry (s = (l+1) M + j fastest, row stride sp = 3M rounded
+// up to 32 images) and its TMA map (boxes of 32 images x (4p+1) orders)
+struct gs_tab32 {
+    float2 *h = nullptr;
+    long sp = 0;
+    CUtensorMap map;
+};
+
 // Row and column blocks of A (Eq. matA): unknowns [mu1, sigma1, mu2, sigma2, a2, a1, a3, c, d];
 // rows [Gamma1 value, Gamma1 normal, Gamma2 value, Gamma2 normal, middle walls (value, x-deriv),
 // upper walls, lower walls, Gamma_u (value, y-deriv), Gamma_d (value, y-deriv)].
@@ -51,6 +59,8 @@ struct AngleData {
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
     int sweeps32 = 0;            // FP32-guided sweeps before them
+    double phase_ms[6] = {};     // factorisation phases: assembly, QR, FP32 sweeps, polar step, FP64 sweeps, U/V
+    long long rot32[32] = {}, rot64[32] = {};   // rotations applied in each FP32 / FP64 sweep
     int iters = 0;               // GMRES iterations (all inner iterations for the mixed solve)
     int outer = 0;               // refinement sweeps of the mixed solve (0 for FP64)
     double relres = -1.0;
@@ -125,10 +135,8 @@ struct gs_ctx {
     float4 *xdf = nullptr;                               // n, double-float split of the operator input
     int *iflag = nullptr;                                // one int, device-side flag
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
-    float2 *htab32 = nullptr;                            // its complex64 copy [i][q][s], row stride htab32_sp
-    long htab32_sp = 0;                                  // 3M rounded up to 32 images
-    bool htab32_off = false;                             // no room for it: complex64 recomputes the coefficients
-    CUtensorMap tm_h32;                                  // TMA map of htab32: boxes of 32 images x (4p+1) orders
+    gs_tab32 tab32;                                      // its complex64 copy (on first complex64 use)
+    bool tab32_off = false;                              // no room for it: complex64 recomputes the coefficients
     float2 *b3pad = nullptr;                             // complex64 phased source coefficients, 32-image tiles
     int *terr = nullptr;                                 // device flag: a bounded wait of the table kernel gave up
     void *tcA = nullptr;                                 // bfloat16 [T_-1 T_0 T_1] in real 2x2 form (on demand)
@@ -155,6 +163,7 @@ struct gs_ctx {
     double *dscal = nullptr;                             // device scalars
     double *hscal = nullptr;                             // pinned host scalars
     unsigned long long *dcount = nullptr;
+    unsigned *bar = nullptr;                             // grid barrier (count, generation) of cooperative kernels
 
     // instrumentation: kernel launches issued, optional event timing of the translation kernel
     unsigned long long nlaunch = 0;
@@ -227,6 +236,13 @@ size_t gs_pair_table_elems(int M, int p);
 int gs_build_pair_table(gs_ctx *c);
 // complex64 pair table for the complex64 translation, built on first use when it fits (gs_translate.cu)
 int gs_ensure_table32(gs_ctx *c);
+size_t gs_tab32_bytes(int M, int p);
+// allocates and builds the complex64 table of M inclusions at xy (rounded from htab when given)
+int gs_tab32_build(gs_ctx *c, const double *xy, int M, int p, const cplx *htab, gs_tab32 *t, cudaStream_t st);
+// out = T beta for one geometry from its complex64 table (b3: 32-image tiles of phased coefficients,
+// part: partial sums, at least 64 M (2p+1)); active (nullable device flag): 0 -> out = 0, no work
+int gs_tab32_translate(gs_ctx *c, const gs_tab32 &t, int M, int p, const cplx *beta, cplx alpha, float2 *b3,
+                       cplx *part, size_t part_elems, cplx *out, const int *active, cudaStream_t st);
 // GS_ERR_TIMEOUT if a bounded wait of that kernel gave up since the last check (synchronises)
 int gs_check_table_wait(gs_ctx *c);
 // plain (unswizzled) 2-D tensor map over a row-major rows x cols array (gs_tc.cu)

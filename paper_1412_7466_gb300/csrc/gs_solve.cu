@@ -969,7 +969,7 @@ int gs_solve_impl(gs_ctx *c, AngleData &a, const gs_solve_opts &o, const cplx *x
     }
     a.iters = total;
     a.relres = rel;
-    if (o.precision == GS_C64 && c->htab32) GS_TRY(gs_check_table_wait(c));
+    if (o.precision == GS_C64 && c->tab32.h) GS_TRY(gs_check_table_wait(c));
     return rel <= o.tol ? GS_OK : GS_ERR_NOT_CONVERGED;
 }
 

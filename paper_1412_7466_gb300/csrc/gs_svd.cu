@@ -21,6 +21,7 @@
 // the clipped pseudo-inverse safe in the near-null directions.  A^+ g = D V Sigma^+ U^* g with
 // Sigma^+ = min(1/sigma, 1/eps) (Eq. applypA) is applied as D (P W_x) (coef .* (U^* g)) with
 // coef_j = 1/(sigma_j max(sigma_j, eps)), sigma_j = ||W_x e_j||.
+#include <algorithm>
 #include <cstring>
 
 #include "gs_internal.h"
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
     int pc = a < b ? a : b, qc = a < b ? b : a;
     cplx *wp = W + (size_t)pc * m, *wq = W + (size_t)qc * m;
     __shared__ double4 sh4[32];
-    __shared__ double rot[4];
+    __shared__ double rot[5];
     double al = 0, be = 0, gr = 0, gi = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         cplx x = wp[i], y = wq[i];
@@ -108,14 +109,15 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
             rot[0] = 1.0;
             rot[1] = cc;
             rot[2] = cc * t;
-            rot[3] = atan2(gi, gr);
+            rot[3] = gr / g;   // e^{-i phi} = conj(conj(w_p) w_q) / |.|, phi = arg(conj(w_p) w_q)
+            rot[4] = -gi / g;
             atomicAdd(nrot, 1ull);
         }
     }
     __syncthreads();
     if (rot[0] == 0.0) return;
     double cc = rot[1], ss = rot[2];
-    cplx e = cexpi(-rot[3]);   // e^{-i phi}, phi = arg(conj(w_p) w_q)
+    const cplx e = C(rot[3], rot[4]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         cplx x = wp[i], y = cmul(wq[i], e);
         wp[i] = csub(cscale(x, cc), cscale(y, ss));
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
     int pc = a < b ? a : b, qc = a < b ? b : a;
     float2 *wp = W32 + (size_t)pc * m, *wq = W32 + (size_t)qc * m;
     __shared__ float4 sh4[32];
-    __shared__ double rot[4];
+    __shared__ double rot[5];
     float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const float2 x = wp[i], y = wq[i];
@@ -198,15 +200,15 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
             rot[0] = 1.0;
             rot[1] = cc;
             rot[2] = cc * t;
-            rot[3] = atan2((double)gi, (double)gr);
+            rot[3] = (double)gr / g;   // e^{-i phi}, phi = arg(conj(w_p) w_q)
+            rot[4] = -(double)gi / g;
             atomicAdd(nrot, 1ull);
         }
     }
     __syncthreads();
     if (rot[0] == 0.0) return;
     const double cc = rot[1], ss = rot[2];
-    const cplx e = cexpi(-rot[3]);   // e^{-i phi}, phi = arg(conj(w_p) w_q)
-    const float cf = (float)cc, sf = (float)ss, er = (float)e.x, ei = (float)e.y;   // applied in FP32
+    const float cf = (float)cc, sf = (float)ss, er = (float)rot[3], ei = (float)rot[4];   // applied in FP32
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const float2 x = wp[i], y0 = wq[i];
         const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
@@ -219,6 +221,108 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
         const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
         vp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
         vq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
+    }
+}
+
+// ---- one whole FP32 sweep per launch (cooperative) -------------------------------------------------
+// The FP32 rounds are latency-bound (a round of ~845 pair rotations of 1689-long columns is ~1 us of
+// FP32 work but a launch, two dependent passes over the columns and a block reduction): one
+// cooperative launch runs all rounds of a sweep, the resident blocks taking the round's pairs in
+// turn and meeting at a grid barrier between rounds.  Columns written in one round are read by other
+// SMs in the next, so they move through L2 only (__ldcg / __stcg); the barrier publishes them with
+// __threadfence.  Every barrier wait is bounded (~1 s): a block that gives up sets *err and all
+// blocks leave at the next barrier.
+
+// Sense-reversing barrier over the grid on (count, gen); false if the wait gave up or an error is set
+__device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd((unsigned *)gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > 2000000000LL) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)err) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// rotation of one FP32 pair (pc < qc) of W32 (columns of length m) and of V (length n), as
+// k_jacobi_round_f32; all threads of the block take part; loads and stores through L2
+__device__ void jacobi_pair_f32(float2 *W32, int m, float2 *V, int n, int pc, int qc, float tol,
+                                unsigned long long *nrot, float4 *sh4, float *rot) {
+    float2 *wp = W32 + (size_t)pc * m, *wq = W32 + (size_t)qc * m;
+    float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 x = __ldcg(&wp[i]), y = __ldcg(&wq[i]);
+        al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
+        be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
+        gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));   // conj(x) y
+        gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+    }
+    block_sum4_f(al, be, gr, gi, sh4);
+    if (threadIdx.x == 0) {
+        const double g = hypot((double)gr, (double)gi);
+        if (g == 0.0 || g <= (double)tol * sqrt((double)al * (double)be)) {
+            rot[0] = 0.f;
+        } else {
+            const double zeta = ((double)be - (double)al) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cc = 1.0 / sqrt(1.0 + t * t);
+            rot[0] = 1.f;
+            rot[1] = (float)cc;
+            rot[2] = (float)(cc * t);
+            rot[3] = (float)(gr / g);    // e^{-i phi} = conj(conj(w_p) w_q) / |.|
+            rot[4] = (float)(-gi / g);
+            atomicAdd(nrot, 1ull);
+        }
+    }
+    __syncthreads();
+    if (rot[0] == 0.f) return;   // uniform over the block
+    const float cf = rot[1], sf = rot[2], er = rot[3], ei = rot[4];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 x = __ldcg(&wp[i]), y0 = __ldcg(&wq[i]);
+        const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+        __stcg(&wp[i], make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y));
+        __stcg(&wq[i], make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y));
+    }
+    float2 *vp = V + (size_t)pc * n, *vq = V + (size_t)qc * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 x = __ldcg(&vp[i]), y0 = __ldcg(&vq[i]);
+        const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+        __stcg(&vp[i], make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y));
+        __stcg(&vq[i], make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y));
+    }
+}
+
+// all npad - 1 rounds of the circle schedule; launched cooperatively (all blocks resident)
+__global__ void __launch_bounds__(JTPB) k_jacobi_sweep_f32(float2 *W32, int m, float2 *V, int n, int npad, float tol,
+                                                           unsigned long long *nrot, unsigned *bar, int *err) {
+    __shared__ float4 sh4[32];
+    __shared__ float rot[5];
+    for (int r = 0; r < npad - 1; ++r) {
+        for (int k = blockIdx.x; k < npad / 2; k += gridDim.x) {
+            const int a = k == 0 ? 0 : ((k - 1 + r) % (npad - 1)) + 1;
+            const int pb = npad - 1 - k;
+            const int b = pb == 0 ? 0 : ((pb - 1 + r) % (npad - 1)) + 1;
+            if (a < n && b < n) jacobi_pair_f32(W32, m, V, n, a < b ? a : b, a < b ? b : a, tol, nrot, sh4, rot);
+            __syncthreads();   // rot and sh4 are reused by the block's next pair
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     }
 }
 
@@ -574,6 +678,16 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     double *nrm2 = c->nrm2;
     int *perm = c->perm;
     cplx *tau = c->tau;
+    // phase timing: assembly, QR, FP32 sweeps, polar step + R^* V, FP64 sweeps, U and V Sigma
+    struct Ev {
+        cudaEvent_t e[7] = {};
+        ~Ev() {
+            for (auto &x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (auto &x : ev.e) GS_CUDA(c, cudaEventCreate(&x));
+    GS_CUDA(c, cudaEventRecord(ev.e[0], st));
     GS_TRY(gs_assemble_A(c, a, Aqr, m));
     GS_TRY(gs_assemble_f(c, a, a.f));
     GS_COUNT_LAUNCH(c);
@@ -581,6 +695,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     GS_COUNT_LAUNCH(c);
     k_colnorm_scale<<<ly.col_c - ly.col_a2, 256, 0, st>>>(Aqr, m, m, ly.col_a2, ly.col_c, a.dscale);
     // 1. QR with column pivoting
+    GS_CUDA(c, cudaEventRecord(ev.e[1], st));
     GS_COUNT_LAUNCH(c);
     k_colnorm2<<<n, 256, 0, st>>>(Aqr, m, n, nrm2);
     GS_COUNT_LAUNCH(c);
@@ -595,6 +710,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     }
     GS_CHECK_LAUNCH(c);
     // 2. one-sided Jacobi on X = R^*
+    GS_CUDA(c, cudaEventRecord(ev.e[2], st));
     GS_COUNT_LAUNCH(c);
     k_r_adjoint<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(Aqr, m, n, X);
     GS_COUNT_LAUNCH(c);
@@ -612,19 +728,47 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     k_identity_f32<<<eb, 256, 0, st>>>(V32, n);
     GS_CHECK_LAUNCH(c);
     a.sweeps32 = 0;
+    for (int q = 0; q < 32; ++q) a.rot32[q] = a.rot64[q] = 0;
+    // one cooperative launch per sweep when all its blocks can be resident, else one launch per round
+    int coop = 0, per_sm = 0, dev_coop = 0;
+    cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (dev_coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_sweep_f32, JTPB, 0) == cudaSuccess)
+        coop = std::min(npad / 2, per_sm * c->sms);
+    cudaGetLastError();
     for (int sweep = 0; sweep < 20; ++sweep) {
         GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
-        for (int r = 0; r < npad - 1; ++r) {
+        if (coop > 0) {
+            GS_CUDA(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
+            GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), st));
+            float tol32 = 1e-5f;
+            int mm = n, nn_ = n, np_ = npad;
+            void *args[] = {&X32, &mm, &V32, &nn_, &np_, &tol32, &c->dcount, &c->bar, &c->terr};
             GS_COUNT_LAUNCH(c);
-            k_jacobi_round_f32<<<npad / 2, JTPB, 0, st>>>(X32, n, V32, n, r, npad, 1e-5f, c->dcount);
+            GS_CUDA(c, cudaLaunchCooperativeKernel((const void *)k_jacobi_sweep_f32, dim3(coop), dim3(JTPB), args, 0, st));
+        } else {
+            for (int r = 0; r < npad - 1; ++r) {
+                GS_COUNT_LAUNCH(c);
+                k_jacobi_round_f32<<<npad / 2, JTPB, 0, st>>>(X32, n, V32, n, r, npad, 1e-5f, c->dcount);
+            }
         }
         GS_CHECK_LAUNCH(c);
+        if (coop > 0) {
+            int herr = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&herr, c->terr, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            if (herr) {
+                GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), st));
+                return gs_fail(c, GS_ERR_TIMEOUT, "grating factorisation: a grid barrier wait gave up");
+            }
+        }
         unsigned long long h = 0;
         GS_CUDA(c, cudaMemcpyAsync(&h, c->dcount, sizeof(h), cudaMemcpyDeviceToHost, st));
         GS_CUDA(c, cudaStreamSynchronize(st));
         a.sweeps32 = sweep + 1;
+        a.rot32[sweep] = (long long)h;
         if (h == 0) break;
     }
+    GS_CUDA(c, cudaEventRecord(ev.e[3], st));
     // 2b. V_x = the FP64 orthogonal polar factor of V32 (Newton-Schulz, V <- V (3I - V^H V)/2,
     //     quadratic from an orthogonality defect of ~1e-5), then X = R^* V_x in FP64
     const dim3 zg((n + ZG - 1) / ZG, (n + ZG - 1) / ZG);
@@ -655,6 +799,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     k_zgemm_nn<<<zg, 256, 0, st>>>(X, Vx, T, n);
     GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaMemcpyAsync(X, T, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(c, cudaEventRecord(ev.e[4], st));
     const double tol = 1e-14;
     a.sweeps = 0;
     for (int sweep = 0; sweep < 30; ++sweep) {
@@ -668,8 +813,10 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         GS_CUDA(c, cudaMemcpyAsync(&h, c->dcount, sizeof(h), cudaMemcpyDeviceToHost, st));
         GS_CUDA(c, cudaStreamSynchronize(st));
         a.sweeps = sweep + 1;
+        if (sweep < 32) a.rot64[sweep] = (long long)h;
         if (h == 0) break;
     }
+    GS_CUDA(c, cudaEventRecord(ev.e[5], st));
     GS_COUNT_LAUNCH(c);
     k_sigma<<<n, 256, 0, st>>>(X, n, n, c->L.eps_pinv, a.sigma, a.coef);
     // 3. U = Q V_x (reflectors applied to [V_x; 0] in reverse order), V Sigma = P W_x
@@ -682,5 +829,29 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     GS_COUNT_LAUNCH(c);
     k_permute_rows<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(X, n, perm, a.Vr);
     GS_CHECK_LAUNCH(c);
+    GS_CUDA(c, cudaEventRecord(ev.e[6], st));
+    GS_CUDA(c, cudaEventSynchronize(ev.e[6]));
+    for (int q = 0; q < 6; ++q) {
+        float ms = 0.f;
+        GS_CUDA(c, cudaEventElapsedTime(&ms, ev.e[q], ev.e[q + 1]));
+        a.phase_ms[q] = ms;
+    }
+    return GS_OK;
+}
+
+int gs_factor_stats(gs_ctx *c, int angle, int *sweeps32, int *sweeps64, double *phase_ms, long long *rot32,
+                    long long *rot64) {
+    if (!c) return GS_ERR_ARG;
+    if (!c->grating_ready) return gs_fail(c, GS_ERR_STATE, "the grating has not been factored");
+    if (angle < 0 || angle >= (int)c->ang.size()) return gs_fail(c, GS_ERR_ARG, "angle index out of range");
+    const AngleData &a = c->ang[angle];
+    if (sweeps32) *sweeps32 = a.sweeps32;
+    if (sweeps64) *sweeps64 = a.sweeps;
+    if (phase_ms)
+        for (int q = 0; q < 6; ++q) phase_ms[q] = a.phase_ms[q];
+    for (int q = 0; q < 32; ++q) {
+        if (rot32) rot32[q] = a.rot32[q];
+        if (rot64) rot64[q] = a.rot64[q];
+    }
     return GS_OK;
 }

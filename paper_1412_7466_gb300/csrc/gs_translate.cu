@@ -301,9 +301,9 @@ __global__ void k_table_to_c64(const cplx *__restrict__ h, long rows, long S, lo
 // b3[s][n] = alpha^l beta_j[n] in complex64 for the source images s = (l+1) M + j, zero for the
 // padding images up to a whole number of 32-image tiles (the phase is applied in FP64)
 __global__ void k_beta_to_b3(const cplx *__restrict__ beta, int M, int nc, long ntot, cplx alpha,
-                             float2 *__restrict__ b3) {
+                             float2 *__restrict__ b3, const int *__restrict__ active) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ntot) return;
+    if (e >= ntot || (active && !*active)) return;
     const long s = e / nc;
     const int n = (int)(e - s * nc);
     float2 v = make_float2(0.f, 0.f);
@@ -326,7 +326,8 @@ __global__ void k_beta_to_b3(const cplx *__restrict__ beta, int M, int nc, long 
 // flight meanwhile, so the kernel runs at the FP32 pipe's rate while streaming the table (1.18 GB
 // at M = 1000, p = 12) from HBM.  The self pair holds zeros in the table, so no lane branches.
 // Every wait is bounded (~1 s); a wait that gives up makes the whole block stop, wait (bounded) for
-// its copies still in flight, set *err and return without writing.
+// its copies still in flight, set *err and return without writing.  `active` (nullable): a device
+// flag; when it is 0 the launch does nothing (masked geometries of a batched solve).
 template <int P, int WARPS>
 struct Tab32Layout {
     static constexpr int NC = 2 * P + 1, NQ = 4 * P + 1;
@@ -342,8 +343,9 @@ struct Tab32Layout {
 template <int P, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_translate_c64_tab(const __grid_constant__ CUtensorMap tmH, const float2 *__restrict__ b3, int M, int nsplit,
-                    cplx *__restrict__ out, int *__restrict__ err) {
+                    cplx *__restrict__ out, int *__restrict__ err, const int *__restrict__ active) {
     using L = Tab32Layout<P, WARPS>;
+    if (active && !*active) return;   // a converged geometry of a batch (uniform over the block)
     constexpr int NC = L::NC;
     constexpr long long WAIT = 2000000000LL;   // ~1 s
     extern __shared__ uint8_t smem_raw[];
@@ -488,38 +490,45 @@ __global__ void k_sum_partials(const cplx *part, int nsplit, long len, cplx *out
     out[e] = s;
 }
 
-// complex64 translation from the complex64 table (after gs_ensure_table32 built it)
+// out = sum of the nsplit partials, or zero when the activity flag (nullable) is 0
+__global__ void k_sum_partials_act(const cplx *part, int nsplit, long len, cplx *out, const int *active) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    if (active && !*active) {
+        out[e] = C(0.0, 0.0);
+        return;
+    }
+    cplx s = part[e];
+    for (int c = 1; c < nsplit; ++c) s = cadd(s, part[(size_t)c * len + e]);
+    out[e] = s;
+}
+
+// complex64 translation of one geometry (M inclusions) from its table t: phased coefficients into
+// b3, the table kernel into the partials, their sum into out
 template <int P>
-int launch_translate_tab32(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out) {
+int launch_tab32(gs_ctx *c, const gs_tab32 &t, int M, const cplx *beta, cplx alpha, float2 *b3, cplx *part,
+                 size_t part_elems, cplx *out, const int *active, cudaStream_t st, bool prof) {
     constexpr int WARPS = 4;
     using L = Tab32Layout<P, WARPS>;
-    const int M = c->M;
     const int gx = (M + WARPS - 1) / WARPS;
     const int ntile = (int)((3L * M + TILE - 1) / TILE);
     // about sixteen blocks per SM in all (two resident at a time), so the last wave stays short
     int nsplit = (int)((c->sms * 16L + gx - 1) / gx);
     nsplit = std::max(1, std::min(std::min(nsplit, 64), ntile));
-    const size_t need = (size_t)nsplit * M * (2 * P + 1);
-    cplx *dst = out;
-    if (nsplit > 1) {
-        if (need > c->part_elems) return gs_fail(c, GS_ERR_STATE, "translation scratch too small");
-        dst = c->part;
-    }
+    if ((size_t)nsplit * M * (2 * P + 1) > part_elems) return gs_fail(c, GS_ERR_STATE, "translation scratch too small");
     const long ntot = (long)ntile * TILE * (2 * P + 1);
     GS_COUNT_LAUNCH(c);
-    k_beta_to_b3<<<(int)((ntot + 255) / 256), 256, 0, c->stream>>>(beta, M, 2 * P + 1, ntot, a.alpha, c->b3pad);
+    k_beta_to_b3<<<(int)((ntot + 255) / 256), 256, 0, st>>>(beta, M, 2 * P + 1, ntot, alpha, b3, active);
     cudaEvent_t e0, e1;
-    const bool timed = gs_prof_pair(c, &e0, &e1, GS_C64);
-    if (timed) cudaEventRecord(e0, c->stream);
+    const bool timed = prof && gs_prof_pair(c, &e0, &e1, GS_C64);
+    if (timed) cudaEventRecord(e0, st);
     GS_COUNT_LAUNCH(c);
-    k_translate_c64_tab<P, WARPS><<<dim3(gx, nsplit), WARPS * 32, L::SMEM, c->stream>>>(c->tm_h32, c->b3pad, M, nsplit,
-                                                                                        dst, c->terr);
-    if (timed) cudaEventRecord(e1, c->stream);
-    if (nsplit > 1) {
-        const long len = (long)M * (2 * P + 1);
-        GS_COUNT_LAUNCH(c);
-        k_sum_partials<<<(int)((len + 255) / 256), 256, 0, c->stream>>>(c->part, nsplit, len, out);
-    }
+    k_translate_c64_tab<P, WARPS><<<dim3(gx, nsplit), WARPS * 32, L::SMEM, st>>>(t.map, b3, M, nsplit, part, c->terr,
+                                                                                 active);
+    if (timed) cudaEventRecord(e1, st);
+    const long len = (long)M * (2 * P + 1);
+    GS_COUNT_LAUNCH(c);
+    k_sum_partials_act<<<(int)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, out, active);
     GS_CHECK_LAUNCH(c);
     return GS_OK;
 }
@@ -529,7 +538,9 @@ int launch_translate(gs_ctx *c, const AngleData &a, const cplx *beta, cplx *out,
     constexpr int WARPS = 4;
     if (precision == GS_C64) {
         GS_TRY(gs_ensure_table32(c));
-        if (c->htab32) return launch_translate_tab32<P>(c, a, beta, out);
+        if (c->tab32.h)
+            return launch_tab32<P>(c, c->tab32, c->M, beta, a.alpha, c->b3pad, c->part, c->part_elems, out, nullptr,
+                                   c->stream, true);
     }
     const int M = c->M;
     const int gx = (M + WARPS - 1) / WARPS;
@@ -589,25 +600,24 @@ static int build_table(gs_ctx *c) {
     return GS_OK;
 }
 
-// complex64 table: rounded from the FP64 table when that exists, else computed in FP64 directly;
-// its tensor map; the kernel's shared-memory attribute (set eagerly, outside any stream capture)
+// complex64 table of M inclusions at xy: rounded from the FP64 table htab (nullable) when given,
+// else computed in FP64 directly; its tensor map; the kernel's shared-memory attribute (set eagerly,
+// outside any stream capture)
 template <int P>
-static int build_table32(gs_ctx *c) {
+static int build_tab32(gs_ctx *c, const double *xy, int M, const cplx *htab, gs_tab32 *t, cudaStream_t st) {
     constexpr int NQ = 4 * P + 1;
-    const long S = 3L * c->M, SP = c->htab32_sp;
-    if (c->htab) {
-        const long tot = (long)c->M * NQ * S;
+    const long S = 3L * M, SP = t->sp;
+    if (htab) {
+        const long tot = (long)M * NQ * S;
         GS_COUNT_LAUNCH(c);
-        k_table_to_c64<<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->htab, (long)c->M * NQ, S, SP, c->htab32);
+        k_table_to_c64<<<(int)((tot + 255) / 256), 256, 0, st>>>(htab, (long)M * NQ, S, SP, t->h);
     } else {
-        const long tot = S * c->M;
+        const long tot = S * M;
         GS_COUNT_LAUNCH(c);
-        k_pair_table<P, float2><<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(c->xy, c->M, c->L.k2, c->L.d,
-                                                                                 c->htab32, SP);
+        k_pair_table<P, float2><<<(int)((tot + 255) / 256), 256, 0, st>>>(xy, M, c->L.k2, c->L.d, t->h, SP);
     }
     GS_CHECK_LAUNCH(c);
-    GS_TRY(gs_make_map_plain(c, &c->tm_h32, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, c->htab32, (long)c->M * NQ, S, SP * 8,
-                             TILE, NQ));
+    GS_TRY(gs_make_map_plain(c, &t->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, t->h, (long)M * NQ, S, SP * 8, TILE, NQ));
     GS_CUDA(c, cudaFuncSetAttribute(k_translate_c64_tab<P, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     Tab32Layout<P, 4>::SMEM));
     return GS_OK;
@@ -630,44 +640,78 @@ int gs_build_pair_table(gs_ctx *c) {
     }
 }
 
+size_t gs_tab32_bytes(int M, int p) {
+    const long SP = (3L * M + TILE - 1) / TILE * TILE;
+    return sizeof(float2) * (size_t)SP * M * (4 * p + 1);
+}
+
+// allocates and builds t (t->h owned by the caller afterwards); GS_ERR_OOM if the allocation fails
+int gs_tab32_build(gs_ctx *c, const double *xy, int M, int p, const cplx *htab, gs_tab32 *t, cudaStream_t st) {
+    t->sp = (3L * M + TILE - 1) / TILE * TILE;
+    if (cudaMalloc((void **)&t->h, gs_tab32_bytes(M, p)) != cudaSuccess) {
+        cudaGetLastError();
+        t->h = nullptr;
+        return GS_ERR_OOM;
+    }
+    int r;
+    switch (p) {
+        case 1: r = build_tab32<1>(c, xy, M, htab, t, st); break;
+        case 2: r = build_tab32<2>(c, xy, M, htab, t, st); break;
+        case 3: r = build_tab32<3>(c, xy, M, htab, t, st); break;
+        case 4: r = build_tab32<4>(c, xy, M, htab, t, st); break;
+        case 5: r = build_tab32<5>(c, xy, M, htab, t, st); break;
+        case 6: r = build_tab32<6>(c, xy, M, htab, t, st); break;
+        case 7: r = build_tab32<7>(c, xy, M, htab, t, st); break;
+        case 8: r = build_tab32<8>(c, xy, M, htab, t, st); break;
+        case 10: r = build_tab32<10>(c, xy, M, htab, t, st); break;
+        case 12: r = build_tab32<12>(c, xy, M, htab, t, st); break;
+        case 16: r = build_tab32<16>(c, xy, M, htab, t, st); break;
+        default: r = gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+    if (r != GS_OK) {
+        cudaFree(t->h);
+        t->h = nullptr;
+    }
+    return r;
+}
+
+int gs_tab32_translate(gs_ctx *c, const gs_tab32 &t, int M, int p, const cplx *beta, cplx alpha, float2 *b3,
+                       cplx *part, size_t part_elems, cplx *out, const int *active, cudaStream_t st) {
+    switch (p) {
+        case 1: return launch_tab32<1>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 2: return launch_tab32<2>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 3: return launch_tab32<3>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 4: return launch_tab32<4>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 5: return launch_tab32<5>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 6: return launch_tab32<6>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 7: return launch_tab32<7>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 8: return launch_tab32<8>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 10: return launch_tab32<10>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 12: return launch_tab32<12>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        case 16: return launch_tab32<16>(c, t, M, beta, alpha, b3, part, part_elems, out, active, st, false);
+        default: return gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    }
+}
+
 // The complex64 translation reads a complex64 copy of the pair table, 3M (rounded up to 32) x M x
 // (4p+1) values (1.18 GB at M = 1000, p = 12), when it fits the table budget (half the free device
-// memory unless set); otherwise (htab32_off) it recomputes the coefficients in FP32 on the fly.
+// memory unless set); otherwise (tab32_off) it recomputes the coefficients in FP32 on the fly.
 int gs_ensure_table32(gs_ctx *c) {
-    if (c->htab32 || c->htab32_off) return GS_OK;
-    const long SP = (3L * c->M + TILE - 1) / TILE * TILE;
-    const size_t bytes = sizeof(float2) * (size_t)SP * c->M * (4 * c->p + 1);
+    if (c->tab32.h || c->tab32_off) return GS_OK;
     size_t fr = 0, totm = 0;
     GS_CUDA(c, cudaMemGetInfo(&fr, &totm));
     const double budget = c->table_budget_gb >= 0 ? c->table_budget_gb * 1e9 : 0.5 * (double)fr;
-    if ((double)bytes > budget || cudaMalloc((void **)&c->htab32, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        c->htab32 = nullptr;
-        c->htab32_off = true;
+    if ((double)gs_tab32_bytes(c->M, c->p) > budget) {
+        c->tab32_off = true;
         return GS_OK;
     }
-    c->htab32_sp = SP;
-    int st;
-    switch (c->p) {
-        case 1: st = build_table32<1>(c); break;
-        case 2: st = build_table32<2>(c); break;
-        case 3: st = build_table32<3>(c); break;
-        case 4: st = build_table32<4>(c); break;
-        case 5: st = build_table32<5>(c); break;
-        case 6: st = build_table32<6>(c); break;
-        case 7: st = build_table32<7>(c); break;
-        case 8: st = build_table32<8>(c); break;
-        case 10: st = build_table32<10>(c); break;
-        case 12: st = build_table32<12>(c); break;
-        case 16: st = build_table32<16>(c); break;
-        default: st = gs_fail(c, GS_ERR_ARG, "multipole order p must be one of 1-8, 10, 12, 16");
+    const int r = gs_tab32_build(c, c->xy, c->M, c->p, c->htab, &c->tab32, c->stream);
+    if (r == GS_ERR_OOM) {
+        c->tab32_off = true;
+        return GS_OK;
     }
-    if (st != GS_OK) {
-        cudaFree(c->htab32);
-        c->htab32 = nullptr;
-        c->htab32_off = true;
-    }
-    return st;
+    if (r != GS_OK) c->tab32_off = true;
+    return r;
 }
 
 // GS_ERR_TIMEOUT (and the flag cleared) if a bounded wait of the table-driven complex64 translation
