@@ -41,3 +41,18 @@ def test_errors_without_device_are_reported():
     h = ctypes.c_void_p()
     assert lib.gs_create(ctypes.byref(h), 0, None) == GS_ERR_CUDA
     assert lib.gs_strerror(GS_ERR_CUDA).decode() == "CUDA error"
+
+
+def test_status_strings_cover_every_code():
+    """Every status the C-ABI returns, the bounded-wait timeout included, has its own message (host
+    function, no device needed)."""
+    from paper_1412_7466_gb300 import load_library
+    import paper_1412_7466_gb300 as P
+    lib = load_library()
+    codes = {name: getattr(P, name) for name in dir(P) if name.startswith("GS_ERR_") or name == "GS_OK"}
+    assert "GS_ERR_TIMEOUT" in codes
+    msgs = {name: lib.gs_strerror(v).decode() for name, v in codes.items()}
+    assert msgs["GS_ERR_TIMEOUT"] == "device wait timed out"
+    assert len(set(msgs.values())) == len(msgs), msgs            # distinct messages
+    assert "unknown status" not in msgs.values()
+    assert lib.gs_strerror(12345).decode() == "unknown status"
