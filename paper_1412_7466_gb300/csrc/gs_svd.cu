@@ -276,18 +276,21 @@ __device__ void jacobi_pair_f32(float2 *W32, int m, float2 *V, int n, int pc, in
     }
     block_sum4_f(al, be, gr, gi, sh4);
     if (threadIdx.x == 0) {
-        const double g = hypot((double)gr, (double)gi);
-        if (g == 0.0 || g <= (double)tol * sqrt((double)al * (double)be)) {
+        // FP32 throughout: the FP32 sweeps only need FP32-accurate rotations (their product V is made
+        // orthonormal to FP64 precision afterwards), and FP64 divisions and square roots here would sit
+        // on every round's critical path
+        const float g = hypotf(gr, gi);
+        if (g == 0.f || g <= tol * sqrtf(al) * sqrtf(be)) {
             rot[0] = 0.f;
         } else {
-            const double zeta = ((double)be - (double)al) / (2.0 * g);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cc = 1.0 / sqrt(1.0 + t * t);
+            const float zeta = (be - al) / (2.f * g);
+            const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+            const float cc = rsqrtf(fmaf(t, t, 1.f));
             rot[0] = 1.f;
-            rot[1] = (float)cc;
-            rot[2] = (float)(cc * t);
-            rot[3] = (float)(gr / g);    // e^{-i phi} = conj(conj(w_p) w_q) / |.|
-            rot[4] = (float)(-gi / g);
+            rot[1] = cc;
+            rot[2] = cc * t;
+            rot[3] = gr / g;   // e^{-i phi} = conj(conj(w_p) w_q) / |.|
+            rot[4] = -gi / g;
             atomicAdd(nrot, 1ull);
         }
     }
@@ -658,6 +661,41 @@ __global__ void k_apply_reflector(const cplx *Aqr, int m, int j, const cplx *tau
     }
 }
 
+// Y[:, col] = H_0 H_1 ... H_{nr-1} Y[:, col] for every column at once, block per column: the column
+// stays in shared memory (m complex values) while the reflectors are applied from the last to the
+// first, in one launch instead of one launch per reflector (the columns are independent; each
+// column's arithmetic is that of k_apply_reflector, in the same order)
+__global__ void __launch_bounds__(256) k_apply_reflectors_all(const cplx *__restrict__ Aqr, int m, int nr,
+                                                              const cplx *__restrict__ tau, cplx *__restrict__ Y,
+                                                              int ncols) {
+    extern __shared__ cplx ys[];
+    __shared__ double sh[32];
+    const int col = blockIdx.x;
+    if (col >= ncols) return;
+    cplx *y = Y + (size_t)col * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int j = nr - 1; j >= 0; --j) {
+        const cplx *v = Aqr + (size_t)j * m;
+        double wr = 0.0, wi = 0.0;
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+            const cplx vi = (i == j) ? C(1.0, 0.0) : __ldg(&v[i]);
+            const cplx yi = ys[i];
+            wr += vi.x * yi.x + vi.y * yi.y;
+            wi += vi.x * yi.y - vi.y * yi.x;
+        }
+        wr = block_sum(wr, sh);
+        wi = block_sum(wi, sh);
+        const cplx f = cmul(tau[j], C(wr, wi));
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+            const cplx vi = (i == j) ? C(1.0, 0.0) : __ldg(&v[i]);
+            ys[i] = csub(ys[i], cmul(f, vi));
+        }
+        __syncthreads();   // the next reflector's inner product reads entries other threads updated
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = ys[i];
+}
+
 // Vr (row-major) = P W_x: row perm[i] of Vr is row i of W_x (column-major n x n)
 __global__ void k_permute_rows(const cplx *Wx, int n, const int *perm, cplx *Vr) {
     long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -822,9 +860,14 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     // 3. U = Q V_x (reflectors applied to [V_x; 0] in reverse order), V Sigma = P W_x
     GS_COUNT_LAUNCH(c);
     k_pad_rows<<<(int)(((long)m * n + 255) / 256), 256, 0, st>>>(Vx, n, m, a.W);
-    for (int j = n - 1; j >= 0; --j) {
+    if ((size_t)m * sizeof(cplx) <= 48 * 1024) {   // the column fits the default shared memory
         GS_COUNT_LAUNCH(c);
-        k_apply_reflector<<<n, 256, 0, st>>>(Aqr, m, j, tau, a.W, n);
+        k_apply_reflectors_all<<<n, 256, (size_t)m * sizeof(cplx), st>>>(Aqr, m, n, tau, a.W, n);
+    } else {
+        for (int j = n - 1; j >= 0; --j) {
+            GS_COUNT_LAUNCH(c);
+            k_apply_reflector<<<n, 256, 0, st>>>(Aqr, m, j, tau, a.W, n);
+        }
     }
     GS_COUNT_LAUNCH(c);
     k_permute_rows<<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(X, n, perm, a.Vr);
