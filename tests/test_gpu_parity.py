@@ -196,6 +196,30 @@ def test_geometry_and_state_errors():
     gs.close()
 
 
+def test_factor_stats(small):
+    """gs_factor_stats: the factorisation's Jacobi sweeps ended with a sweep that rotated nothing
+    (the convergence test of the one-sided Jacobi method), its phase times are positive and add up to
+    less than the whole factorisation could take, and the call is refused before any factorisation."""
+    from paper_1412_7466_gb300 import GS_ERR_STATE, GsError
+    cfg, prob, gs = small
+    st = gs.factor_stats(0)
+    assert st["sweeps_fp32"] >= 1 and st["sweeps_fp64"] >= 1
+    assert len(st["rotations_fp32"]) == st["sweeps_fp32"] and len(st["rotations_fp64"]) == st["sweeps_fp64"]
+    assert st["rotations_fp64"][-1] == 0 and st["rotations_fp64"][0] > 0
+    n = prob.eg.A.shape[1]
+    assert max(st["rotations_fp64"]) <= n * (n - 1) // 2
+    ph = st["phase_ms"]
+    assert set(ph) == {"assemble", "qr", "jacobi_fp32", "polar_step", "jacobi_fp64", "u_v"}
+    assert all(v > 0 for v in ph.values()) and sum(ph.values()) < 60e3
+    fresh = _solver()
+    fresh.set_layers(cfg["grating"])
+    fresh.set_incidence([cfg["theta"]])
+    with pytest.raises(GsError) as e:
+        fresh.factor_stats(0)
+    assert e.value.status == GS_ERR_STATE
+    fresh.close()
+
+
 def test_translate_c64_matches_oracle(small):
     """complex64 translation: FP32 products and Hankel recurrence; the operator agrees with the
     FP64 oracle to single-precision accuracy (1e-5 relative in norm, from ~1e-7 unit roundoff
