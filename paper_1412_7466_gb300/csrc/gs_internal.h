@@ -35,7 +35,7 @@ struct Layout {
 // inner products of the complex64 Arnoldi step: at most this many blocks share one basis vector
 #define GS_DOT_SPLIT 32
 // partial squared norms of the Arnoldi vector (one per block of the second Gram-Schmidt pass)
-#define GS_NORM_PARTS 1024
+#define GS_NORM_PARTS 4096
 
 struct AngleData {
     double theta = 0, kappa0 = 0;
@@ -127,6 +127,7 @@ struct gs_ctx {
     cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
     float2 *X32tmp = nullptr;                            // 2 x cols x cols: FP32 copy of R^* and its rotations
     double *nrm2 = nullptr;                              // cols, trailing column norms
+    int *cstamp = nullptr;                               // cols, time of each column's last Jacobi rotation
     int *perm = nullptr;                                 // cols, column pivots
     cplx *tau = nullptr;                                 // cols, reflector scalars
     cplx *part = nullptr;                                // translation partials

@@ -625,42 +625,46 @@ __global__ void k_dots_reduce(const cplx *__restrict__ part, int Q, int ld, int 
     h[i] = accumulate ? cadd(h[i], r) : r;
 }
 
-// w (+/-)= sum_{i < cnt} coef[i] V_i, products in FP32 (eight vectors per pass, so eight loads of the
-// basis are in flight per thread); cnt <= GS_KMAX + 1.  Optionally writes the complex64 copy w32 of
-// the result and, per block, the partial squared norm of the result to npart[blockIdx.x].
-__global__ void __launch_bounds__(128) k_combo32(cplx *__restrict__ w, const float2 *__restrict__ Vb, long n,
+// w (+/-)= sum_{i < cnt} coef[i] V_i, products in FP32; cnt <= GS_KMAX + 1.  A block takes
+// COMBO_E = 64 consecutive elements with four thread groups, group g summing the basis vectors
+// i = g, g + 4, ... (four loads in flight per thread); the four partial sums are added in shared
+// memory in a fixed order.  With one thread per element the ~25 000-element vectors left about five
+// warps per SM, too few to cover the basis loads.  Optionally writes the complex64 copy w32 of the
+// result and, per block, the partial squared norm of the result to npart[blockIdx.x].
+constexpr int COMBO_E = 64;
+__global__ void __launch_bounds__(256) k_combo32(cplx *__restrict__ w, const float2 *__restrict__ Vb, long n,
                                                  const cplx *__restrict__ coef, int cnt, float sign,
                                                  float2 *__restrict__ w32, double *__restrict__ npart) {
     __shared__ float2 cf[513];
+    __shared__ float2 part[4][COMBO_E];
     __shared__ double sh[32];
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) cf[i] = make_float2((float)coef[i].x, (float)coef[i].y);
     __syncthreads();
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    double nrm = 0.0;
+    const int le = threadIdx.x % COMBO_E, grp = threadIdx.x / COMBO_E;
+    const long e = (long)blockIdx.x * COMBO_E + le;
     if (e < n) {
-        float sr[8], si[8];
+        float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+        int i = grp;
+        for (; i + 12 < cnt; i += 16) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sr[u] = si[u] = 0.f;
-        int i = 0;
-        for (; i + 8 <= cnt; i += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float2 v = Vb[(size_t)(i + u) * n + e], c = cf[i + u];
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = Vb[(size_t)(i + 4 * u) * n + e], c = cf[i + 4 * u];
                 sr[u] = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr[u]));
                 si[u] = fmaf(c.x, v.y, fmaf(c.y, v.x, si[u]));
             }
         }
-        for (; i < cnt; ++i) {
+        for (; i < cnt; i += 4) {
             const float2 v = Vb[(size_t)i * n + e], c = cf[i];
             sr[0] = fmaf(c.x, v.x, fmaf(-c.y, v.y, sr[0]));
             si[0] = fmaf(c.x, v.y, fmaf(c.y, v.x, si[0]));
         }
-        float tr = 0.f, ti = 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            tr += sr[u];
-            ti += si[u];
-        }
+        part[grp][le] = make_float2((sr[0] + sr[1]) + (sr[2] + sr[3]), (si[0] + si[1]) + (si[2] + si[3]));
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    if (grp == 0 && e < n) {
+        const float tr = (part[0][le].x + part[1][le].x) + (part[2][le].x + part[3][le].x);
+        const float ti = (part[0][le].y + part[1][le].y) + (part[2][le].y + part[3][le].y);
         const cplx r = cadd(w[e], C((double)(sign * tr), (double)(sign * ti)));
         w[e] = r;
         if (w32) w32[e] = make_float2((float)r.x, (float)r.y);
@@ -800,8 +804,8 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
     float2 *V = (float2 *)c->Vk;
     cplx *r = c->v2, *vj = c->kv1, *w = c->kv2;
     double *ds = c->dscal;
-    const int eb128 = (int)((n + 127) / 128);
-    const bool fused_norm = eb128 <= GS_NORM_PARTS;   // the second CGS pass leaves the norm partials
+    const int ebc = (int)((n + COMBO_E - 1) / COMBO_E);   // blocks of k_combo32
+    const bool fused_norm = ebc <= GS_NORM_PARTS;          // the second CGS pass leaves the norm partials
     // h[0..cnt) = V^* w32, split over up to GS_DOT_SPLIT blocks per basis vector early in a cycle
     auto dots = [&](int cnt, cplx *dst) -> int {
         const int Q = std::min(GS_DOT_SPLIT, std::max(1, (2 * c->sms + cnt - 1) / cnt));
@@ -851,15 +855,15 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
             k_to_c64_vec<<<eb, 256, 0, st>>>(w, n, c->kw32);
             GS_TRY(dots(j + 1, h));
             GS_COUNT_LAUNCH(c);
-            k_combo32<<<eb128, 128, 0, st>>>(w, V, n, h, j + 1, -1.f, c->kw32, nullptr);
+            k_combo32<<<ebc, 256, 0, st>>>(w, V, n, h, j + 1, -1.f, c->kw32, nullptr);
             GS_TRY(dots(j + 1, c->yy));
             GS_COUNT_LAUNCH(c);
-            k_combo32<<<eb128, 128, 0, st>>>(w, V, n, c->yy, j + 1, -1.f, nullptr, fused_norm ? c->npart : nullptr);
+            k_combo32<<<ebc, 256, 0, st>>>(w, V, n, c->yy, j + 1, -1.f, nullptr, fused_norm ? c->npart : nullptr);
             GS_COUNT_LAUNCH(c);
             k_add_vec<<<1, 256, 0, st>>>(h, c->yy, j + 1);
             if (fused_norm) {
                 GS_COUNT_LAUNCH(c);
-                k_store32<<<eb, 256, 0, st>>>(w, n, nullptr, V + (size_t)(j + 1) * n, h + j + 1, c->npart, eb128);
+                k_store32<<<eb, 256, 0, st>>>(w, n, nullptr, V + (size_t)(j + 1) * n, h + j + 1, c->npart, ebc);
             } else {
                 GS_COUNT_LAUNCH(c);
                 k_norm<<<1, 1024, 0, st>>>(w, n, ds + 3);
@@ -878,7 +882,7 @@ int gmres_core32(gs_ctx *c, const AngleData &a, const cplx *b, double bnorm, cpl
         GS_COUNT_LAUNCH(c);
         k_backsolve<<<1, 256, 0, st>>>(c->Hh, ld, kk, c->gg, c->yy);
         GS_COUNT_LAUNCH(c);
-        k_combo32<<<eb128, 128, 0, st>>>(x, V, n, c->yy, kk, 1.f, nullptr, nullptr);
+        k_combo32<<<ebc, 256, 0, st>>>(x, V, n, c->yy, kk, 1.f, nullptr, nullptr);
         GS_CHECK_LAUNCH(c);
         if (est <= tol) {
             GS_TRY(gs_apply_impl(c, a, x, r, GS_C64));
