@@ -814,11 +814,24 @@ def main():
         torch.cuda.synchronize()
         t_seq = a_.elapsed_time(b_) / 1e3
         its_s = [ga.stats(angle=q)[0] for q in range(len(ths))]
+        # the same lockstep with each angle translated from the complex64 table
+        ga.solve_angles(tol=tol, maxit=8000, restart=500, precision=GS_C64)   # warm-up (its graph)
+        a_, b_ = ev(), ev()
+        a_.record(stream)
+        ga.solve_angles(tol=tol, maxit=8000, restart=500, precision=GS_C64)
+        brs_t = [ga.bragg(angle=q) for q in range(len(ths))]
+        b_.record(stream)
+        torch.cuda.synchronize()
+        t_tab = a_.elapsed_time(b_) / 1e3
+        its_t = [ga.stats(angle=q)[0] for q in range(len(ths))]
+        sw_t = [ga.refinement_sweeps(q) for q in range(len(ths))]
         diff = max(float(np.linalg.norm(np.r_[x["c"], x["d"]] - np.r_[y["c"], y["d"]]) /
-                         np.linalg.norm(np.r_[y["c"], y["d"]])) for x, y in zip(brs_l, brs_s))
+                         np.linalg.norm(np.r_[y["c"], y["d"]])) for x, y in zip(brs_l + brs_t, brs_s + brs_s))
         ga.close()
         angres = {"value": len(ths) / t_lock, "unit": "solves/s", "dtype": "three-part bf16 tensor-core translation + f64 refinement",
                   "R": len(ths), "sequential_mixed_value": len(ths) / t_seq,
+                  "lockstep_c64_table_value": len(ths) / t_tab,
+                  "lockstep_c64_table_inner_iters": its_t, "lockstep_c64_table_refinement_sweeps": sw_t,
                   "thetas": ths, "wood_angle": th_w, "grating_factor_ms_all_angles": fac_ms,
                   "inner_iters": [x[0] for x in st_l], "refinement_sweeps": sw_l,
                   "relres": [x[1] for x in st_l], "sequential_inner_iters": its_s,

@@ -39,6 +39,7 @@ typedef struct { double re, im; } gs_c128;
 /* Precision of the inclusion-to-inclusion translation inside the matrix-vector product. */
 #define GS_FP64 0                /* complex128 throughout                                            */
 #define GS_C64 1                 /* complex64 translation with order rescaling, FP32 accumulation    */
+#define GS_MIXED_BF16 3          /* gs_solve_angles: inner translation on the tensor cores (bfloat16 parts) */
 
 /*
  * Layered grating (Sec. 2 "Problem formulation"; Sec. 3 discretisation; Sec. 6 parameters).
@@ -168,7 +169,9 @@ int gs_factor(gs_ctx *ctx);
 /* The FP64 translation reads its coefficients H_q(k2 R) e^{i q Th} (all pairs and images) from a
  * table built by gs_factor for each geometry, 3 M^2 (4p+1) complex128 values, when that fits the
  * budget (default: half of the free device memory at gs_factor); otherwise it recomputes them in
- * the kernel.  budget_gb < 0 restores the default, 0 disables the table. */
+ * the kernel.  The complex64 translation reads a complex64 copy of the same coefficients, built on
+ * the geometry's first complex64 use under the same budget (else it too recomputes them).
+ * budget_gb < 0 restores the default, 0 disables the tables built after the call. */
 int gs_set_table_budget(gs_ctx *ctx, double budget_gb);
 
 /* ---- sizes ----------------------------------------------------------------------------------- */
@@ -285,19 +288,23 @@ int gs_batch_tuning(gs_ctx *ctx, int *chunk, int *blocks_per_sm);
 
 /* ---- many incidence angles of one geometry ---------------------------------------------------- */
 /* Solves the current geometry at every incidence angle of the context (R = the n_angles given to
- * gs_set_incidence, 1 <= R <= 256) together, in the mixed form (opts->precision must be GS_C64; the
- * other fields as for gs_solve): per angle, FP64 residuals b_r - L_r beta_r and refinement to the
- * relative residual tol (Sec. 5, each angle its own quasi-periodic problem, Sec. 2 Eqs. quasi,
- * rad1-rad2); the inner GMRES advances all open angles in lockstep.  Its translation applies the
- * geometry's operator [T_-1 T_0 T_1] to all R angles' vectors at once on the tensor cores (three
- * bfloat16 parts of the operator and of the coefficients, the six products of parts whose orders
- * add up to at most 2 accumulated in FP32, single-precision accuracy; the three bfloat16 operator
- * parts take 3 x 2n x 6n x 2 bytes, 45 GB at M = 1000, p = 12; GS_ERR_OOM if they do not fit); the low-rank part runs per angle (complex64 B_phys,
- * double-float C x, FP64 A^+); each Arnoldi step of the R angles is one CUDA-graph replay.  Needs
- * gs_factor (all angles).  Per-angle results are read with gs_get_beta, gs_stats,
+ * gs_set_incidence, 1 <= R <= 256) together, in a mixed form (the other fields of opts as for
+ * gs_solve): per angle, FP64 residuals b_r - L_r beta_r and refinement to the relative residual tol
+ * (Sec. 5, each angle its own quasi-periodic problem, Sec. 2 Eqs. quasi, rad1-rad2); the inner GMRES
+ * advances all open angles in lockstep, each Arnoldi step of the R angles one CUDA-graph replay; the
+ * low-rank part runs per angle (complex64 B_phys, double-float C x, FP64 A^+).  opts->precision
+ * selects the inner translation:
+ *   GS_MIXED_BF16: the geometry's operator [T_-1 T_0 T_1] applied to all R angles' vectors at once on
+ *     the tensor cores (three bfloat16 parts of the operator and of the coefficients, the six products
+ *     of parts whose orders add up to at most 2 accumulated in FP32, single-precision accuracy; the
+ *     three operator parts take 3 x 2n x 6n x 2 bytes, 45 GB at M = 1000, p = 12; GS_ERR_OOM if they
+ *     do not fit);
+ *   GS_C64: each angle's translation from the geometry's complex64 pair table (as gs_translate with
+ *     GS_C64; GS_ERR_OOM if the table does not fit; GS_ERR_ARG under the complex64 range check).
+ * Needs gs_factor (all angles).  Per-angle results are read with gs_get_beta, gs_stats,
  * gs_stats_refinement and gs_bragg at that angle.  GS_ERR_NOT_CONVERGED if an angle misses tol
- * within maxit inner iterations (its iterate stays readable); GS_ERR_TIMEOUT if a tensor-core wait
- * gave up.  Synchronous. */
+ * within maxit inner iterations (its iterate stays readable); GS_ERR_TIMEOUT if a device wait gave
+ * up.  Synchronous. */
 int gs_solve_angles(gs_ctx *ctx, const gs_solve_opts *opts);
 
 /* ---- instrumentation (not part of the method) ------------------------------------------------ */
@@ -344,7 +351,8 @@ int gs_translate_multi(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c
  * three times the operator memory of gs_translate_multi).  Synchronous. */
 int gs_translate_multi_split(gs_ctx *ctx, int R, const gs_c128 *alpha_host, const gs_c128 *beta_dev,
                              gs_c128 *out_dev);
-#define GS_TC_BF16 3             /* gs_profile_read tag of the tensor-core product in gs_translate_multi */
+#define GS_TC_BF16 3             /* gs_profile_read tag of the tensor-core product in gs_translate_multi
+                                    (the same value as GS_MIXED_BF16) */
 
 /* ---- tensor-core product ---------------------------------------------------------------------
  * C[M][N] = A[M][K] B[N][K]^T with A, B bfloat16 (row-major, K contiguous) and C FP32 (row-major),

@@ -27,6 +27,7 @@ GS_ERR_NUMERIC = 7
 GS_ERR_TIMEOUT = 8
 GS_FP64 = 0
 GS_C64 = 1
+GS_MIXED_BF16 = 3
 GS_PROBE_F32X2 = 2
 GS_TC_BF16 = 3
 GS_TM = 0
@@ -370,10 +371,12 @@ class GratingSolver:
         return self._check(self.lib.gs_solve(self.ctx, angle, ctypes.byref(o), b0), "gs_solve", ok=ok)
 
     def solve_angles(self, tol=1e-11, maxit=4000, restart=500, inner_tol=1e-6, max_sweeps=0,
-                     allow_unconverged=False):
-        """All incidence angles of the context in lockstep (mixed form, tensor-core translation);
-        per-angle results through stats/get_beta/bragg(angle)."""
-        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart, precision=GS_C64, inner_tol=inner_tol,
+                     allow_unconverged=False, precision=None):
+        """All incidence angles of the context in lockstep (mixed form); precision GS_MIXED_BF16
+        (default: the translation of all angles at once on the tensor cores) or GS_C64 (each angle
+        from the complex64 pair table); per-angle results through stats/get_beta/bragg(angle)."""
+        o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart,
+                          precision=GS_MIXED_BF16 if precision is None else precision, inner_tol=inner_tol,
                           max_sweeps=max_sweeps)
         ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
         return self._check(self.lib.gs_solve_angles(self.ctx, ctypes.byref(o)), "gs_solve_angles", ok=ok)

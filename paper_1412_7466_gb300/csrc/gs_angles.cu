@@ -37,9 +37,11 @@ struct gs_angles {
     double *nrm = nullptr, *res = nullptr, *npart = nullptr;   // R, R, R x SEG_NQ
     float2 *w32 = nullptr, *cf32 = nullptr;                      // N, R x (kdim+1): complex64 CGS2 operands
     double *hbuf = nullptr;            // pinned host: R residuals + the error flag
-    cudaGraphExec_t step = nullptr;
-    unsigned long long step_kernels = 0;   // kernels in one replay of the step graph
-    const void *key[4] = {nullptr, nullptr, nullptr, nullptr};   // operator and scratch buffers the graph uses
+    int mode = 0;                      // inner translation: 0 tensor-core product of all R angles,
+                                       // 1 complex64 table, one launch per angle
+    cudaGraphExec_t step[2] = {nullptr, nullptr};   // step graph per mode
+    unsigned long long step_kernels[2] = {0, 0};    // kernels in one replay of each step graph
+    const void *key[2][4] = {};                     // operator and scratch buffers each graph uses
 };
 
 namespace {
@@ -93,7 +95,8 @@ void angles_free(gs_angles *A) {
     afree(A->nrm);
     afree(A->res);
     if (A->hbuf) cudaFreeHost(A->hbuf);
-    if (A->step) cudaGraphExecDestroy(A->step);
+    for (int q = 0; q < 2; ++q)
+        if (A->step[q]) cudaGraphExecDestroy(A->step[q]);
     if (A->st) cudaStreamDestroy(A->st);
     if (A->ev_in) cudaEventDestroy(A->ev_in);
     if (A->ev_out) cudaEventDestroy(A->ev_out);
@@ -153,8 +156,17 @@ int angles_setup(gs_ctx *c, int restart) {
 }
 
 // y_r = x_r - s T(a_r) x_r + s B_phys,r A_r^+ C_r x_r for every angle r (the mixed inner operator)
-int angles_apply_c64(gs_ctx *c, gs_angles *A, const cplx *x, cplx *y) {
-    GS_TRY(gs_tc_split_translate(c, A->R, A->alpha, x, A->T, A->err, c->stream));
+// inner operator of every angle; act (nullable): device flags of the angles whose translation is needed
+// (mode 1 skips the others; the tensor-core product always forms all R)
+int angles_apply_c64(gs_ctx *c, gs_angles *A, const cplx *x, cplx *y, const int *act) {
+    if (A->mode == 1) {
+        for (int r = 0; r < A->R; ++r)
+            GS_TRY(gs_tab32_translate(c, c->tab32, c->M, c->p, x + (size_t)r * A->n, c->ang[r].alpha, c->b3pad,
+                                      c->part, c->part_elems, A->T + (size_t)r * A->n, act ? act + r : nullptr,
+                                      c->stream));
+    } else {
+        GS_TRY(gs_tc_split_translate(c, A->R, A->alpha, x, A->T, A->err, c->stream));
+    }
     for (int r = 0; r < A->R; ++r)
         GS_TRY(gs_lowrank_c64(c, c->ang[r], x + (size_t)r * A->n, A->T + (size_t)r * A->n, y + (size_t)r * A->n));
     return GS_OK;
@@ -178,7 +190,7 @@ int angles_step(gs_ctx *c, gs_angles *A) {
     float2 *V = (float2 *)A->Vk;
     GS_COUNT_LAUNCH(c);
     k_seg_fetch<float2><<<eb, 256, 0, st>>>(V, N, A->jdev, A->X);
-    GS_TRY(angles_apply_c64(c, A, A->X, A->Y));
+    GS_TRY(angles_apply_c64(c, A, A->X, A->Y, A->active));
     const SegStep ss{A->geo, A->gid, A->active, A->jdev, A->H, A->hp, A->cs, A->sn, A->gg, A->nrm, A->res, A->npart,
                      A->w32, A->cf32, N, R, A->kdim, nc};
     GS_TRY(seg_cgs2<float2>(c, ss, V, A->Y, st));
@@ -189,13 +201,20 @@ int angles_step(gs_ctx *c, gs_angles *A) {
 }
 
 int angles_step_graph(gs_ctx *c, gs_angles *A) {
+    const int q = A->mode;
     const void *key[4] = {c->tcA, c->tcA_sp[0], c->tcA_sp[1], c->sp_scratch};
-    if (A->step && std::equal(key, key + 4, A->key)) return GS_OK;
-    if (A->step) {   // the tensor-core buffers were rebuilt since the capture
-        cudaGraphExecDestroy(A->step);
-        A->step = nullptr;
+    if (q == 1) {   // the complex64 table, its tiles and the translation scratch
+        key[0] = c->tab32.h;
+        key[1] = c->b3pad;
+        key[2] = c->part;
+        key[3] = nullptr;
     }
-    std::copy(key, key + 4, A->key);
+    if (A->step[q] && std::equal(key, key + 4, A->key[q])) return GS_OK;
+    if (A->step[q]) {   // the buffers were rebuilt since the capture
+        cudaGraphExecDestroy(A->step[q]);
+        A->step[q] = nullptr;
+    }
+    std::copy(key, key + 4, A->key[q]);
     cudaGraph_t gph;
     const unsigned long long l0 = c->nlaunch;
     GS_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -203,10 +222,10 @@ int angles_step_graph(gs_ctx *c, gs_angles *A) {
     cudaError_t e = cudaStreamEndCapture(c->stream, &gph);
     if (st != GS_OK) return st;
     if (e != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&A->step, gph, 0);
+    e = cudaGraphInstantiate(&A->step[q], gph, 0);
     cudaGraphDestroy(gph);
     if (e != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    A->step_kernels = c->nlaunch - l0;
+    A->step_kernels[q] = c->nlaunch - l0;
     c->nlaunch = l0;   // counted per replay
     return GS_OK;
 }
@@ -235,7 +254,7 @@ int angles_gmres(gs_ctx *c, gs_angles *A, const cplx *rhs, cplx *x, const std::v
         if (first) {
             GS_CUDA(c, cudaMemcpyAsync(A->r, rhs, sizeof(cplx) * N, cudaMemcpyDeviceToDevice, st));
         } else {
-            GS_TRY(angles_apply_c64(c, A, x, A->r));
+            GS_TRY(angles_apply_c64(c, A, x, A->r, nullptr));
             GS_COUNT_LAUNCH(c);
             k_vsub<<<eb, 256, 0, st>>>(rhs, A->r, N, A->r);
         }
@@ -261,8 +280,8 @@ int angles_gmres(gs_ctx *c, gs_angles *A, const cplx *rhs, cplx *x, const std::v
         std::fill(kk.begin(), kk.end(), 0);
         std::vector<int> live = act;
         for (int j = 0; j < kd; ++j) {
-            GS_CUDA(c, cudaGraphLaunch(A->step, st));
-            c->nlaunch += A->step_kernels;
+            GS_CUDA(c, cudaGraphLaunch(A->step[A->mode], st));
+            c->nlaunch += A->step_kernels[A->mode];
             GS_CUDA(c, cudaMemcpyAsync(A->hbuf, A->res, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
             int nlive = 0;
@@ -330,7 +349,8 @@ extern "C" int gs_solve_angles(gs_ctx *c, const gs_solve_opts *o) {
     if (cudaSetDevice(c->device) != cudaSuccess) return gs_fail(c, GS_ERR_CUDA, "cudaSetDevice");
     if (!c->factored) return gs_fail(c, GS_ERR_STATE, "gs_factor has not run");
     if (!o || !(o->tol > 0) || o->maxit < 1 || o->restart < 1) return gs_fail(c, GS_ERR_ARG, "bad options");
-    if (o->precision != GS_C64) return gs_fail(c, GS_ERR_ARG, "the multi-angle solve is the mixed form (GS_C64)");
+    if (o->precision != GS_C64 && o->precision != GS_MIXED_BF16)
+        return gs_fail(c, GS_ERR_ARG, "the multi-angle solve is a mixed form (GS_C64 or GS_MIXED_BF16)");
     const int R = (int)c->ang.size();
     if (R < 1 || R > 256) return gs_fail(c, GS_ERR_ARG, "the multi-angle solve takes 1..256 angles");
     GS_TRY(angles_setup(c, o->restart));
@@ -338,7 +358,15 @@ extern "C" int gs_solve_angles(gs_ctx *c, const gs_solve_opts *o) {
     const long n = A->n, N = A->N;
     // everything that allocates, before the step graph is captured
     for (int r = 0; r < R; ++r) GS_TRY(gs_prepare_c64(c, c->ang[r]));
-    GS_TRY(gs_tc_split_prepare(c, R));
+    A->mode = 0;
+    if (o->precision == GS_C64) {
+        GS_TRY(gs_c64_range(c));
+        GS_TRY(gs_ensure_table32(c));
+        if (!c->tab32.h) return gs_fail(c, GS_ERR_OOM, "no room for the complex64 pair table (use GS_MIXED_BF16)");
+        A->mode = 1;
+    } else {
+        GS_TRY(gs_tc_split_prepare(c, R));
+    }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     OnAnglesStream on(c);
     cudaStream_t st = c->stream;
@@ -398,6 +426,7 @@ extern "C" int gs_solve_angles(gs_ctx *c, const gs_solve_opts *o) {
         }
         GS_CHECK_LAUNCH(c);
     }
+    if (A->mode == 1) GS_TRY(gs_check_table_wait(c));
     bool ok = true;
     for (int r = 0; r < R; ++r) {
         AngleData &a = c->ang[r];

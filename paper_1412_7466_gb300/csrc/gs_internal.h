@@ -127,7 +127,6 @@ struct gs_ctx {
     cplx *Xtmp = nullptr, *Vxtmp = nullptr;              // cols x cols, Jacobi on R^*
     float2 *X32tmp = nullptr;                            // 2 x cols x cols: FP32 copy of R^* and its rotations
     double *nrm2 = nullptr;                              // cols, trailing column norms
-    int *cstamp = nullptr;                               // cols, time of each column's last Jacobi rotation
     int *perm = nullptr;                                 // cols, column pivots
     cplx *tau = nullptr;                                 // cols, reflector scalars
     cplx *part = nullptr;                                // translation partials

@@ -1,8 +1,9 @@
 """The multi-angle lockstep solve (gs_solve_angles) through the C-ABI: one geometry at several
 incidence angles -- one of them the Wood anomaly of k1, one normal incidence -- solved together with
-the tensor-core inner translation and FP64 refinement, against the oracle's dense LU solution at
-each angle (Bragg amplitudes 1e-9, norm-wise and element-wise), and against the single-angle mixed
-solve of the same context."""
+FP64 refinement and either inner translation (the tensor-core product of all angles, GS_MIXED_BF16,
+or each angle from the complex64 pair table, GS_C64), against the oracle's dense LU solution at each
+angle (Bragg amplitudes 1e-9, norm-wise and element-wise), and against the single-angle mixed solve
+of the same context."""
 import math
 
 import numpy as np
@@ -15,8 +16,9 @@ from oracle import solver as S
 pytestmark = pytest.mark.gpu
 
 
-def test_angles_small_against_oracle():
-    from paper_1412_7466_gb300 import GS_C64, GratingSolver
+@pytest.mark.parametrize("inner", ["bf16", "c64"])
+def test_angles_small_against_oracle(inner):
+    from paper_1412_7466_gb300 import GS_C64, GS_MIXED_BF16, GratingSolver
     cfg = W.config("small")
     g, dk = cfg["grating"], cfg["disks"]
     thetas = [-math.pi / 5, -1.2, W.wood_angle(g["k"][0], g["d"]), -math.pi / 2, -2.2]
@@ -25,7 +27,7 @@ def test_angles_small_against_oracle():
     gs.set_incidence(thetas)
     gs.set_inclusions(dk)
     gs.factor()
-    gs.solve_angles(tol=1e-12, maxit=2000, restart=200)
+    gs.solve_angles(tol=1e-12, maxit=2000, restart=200, precision=GS_MIXED_BF16 if inner == "bf16" else GS_C64)
     got = [gs.bragg(angle=q) for q in range(len(thetas))]
     stats = [gs.stats(angle=q) for q in range(len(thetas))]
     for q, th in enumerate(thetas):
@@ -35,7 +37,7 @@ def test_angles_small_against_oracle():
         nw, ew = check_bragg(got[q], ref)
         assert stats[q][1] <= 1e-12, (q, stats[q])
         assert got[q]["flux_err"] < 1e-10
-        print(f"angle {th:+.4f}: inner iterations {stats[q][0]}, sweeps {gs.refinement_sweeps(q)}, "
+        print(f"{inner} angle {th:+.4f}: inner iterations {stats[q][0]}, sweeps {gs.refinement_sweeps(q)}, "
               f"Bragg error {nw:.1e} / {ew:.1e}")
     # the same context's single-angle mixed solve agrees
     for q in (0, 2):
@@ -85,4 +87,9 @@ def test_angles_refuses_fp64_and_needs_factor():
     gs.factor()
     o = gs_solve_opts(tol=1e-10, maxit=100, restart=50, precision=GS_FP64, inner_tol=1e-6, max_sweeps=0)
     assert gs.lib.gs_solve_angles(gs.ctx, ctypes.byref(o)) == GS_ERR_ARG
+    # the complex64-table form needs the table: refused when the budget allows none
+    from paper_1412_7466_gb300 import GS_C64, GS_ERR_OOM
+    gs.lib.gs_set_table_budget(gs.ctx, 0.0)
+    o.precision = GS_C64
+    assert gs.lib.gs_solve_angles(gs.ctx, ctypes.byref(o)) == GS_ERR_OOM
     gs.close()
