@@ -402,7 +402,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GS_PROBE_F32X2, GS_TC_BF16, GratingSolver
+    from paper_1412_7466_gb300 import GS_C64, GS_FP64, GS_MIXED_BF16, GS_PROBE_F32X2, GS_TC_BF16, GratingSolver
 
     if args.study:
         if rank == 0:
@@ -791,12 +791,12 @@ def main():
         b_.record(stream)
         torch.cuda.synchronize()
         fac_ms = a_.elapsed_time(b_)
-        ga.solve_angles(tol=tol, maxit=8000, restart=500)          # warm-up (operators, graph)
+        ga.solve_angles(tol=tol, maxit=8000, restart=500, precision=GS_MIXED_BF16)   # warm-up (operators, graph)
         barrier()
         l0 = ga.launch_count()
         a_, b_ = ev(), ev()
         a_.record(stream)
-        ga.solve_angles(tol=tol, maxit=8000, restart=500)
+        ga.solve_angles(tol=tol, maxit=8000, restart=500, precision=GS_MIXED_BF16)
         brs_l = [ga.bragg(angle=q) for q in range(len(ths))]
         b_.record(stream)
         torch.cuda.synchronize()

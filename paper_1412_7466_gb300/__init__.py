@@ -372,11 +372,11 @@ class GratingSolver:
 
     def solve_angles(self, tol=1e-11, maxit=4000, restart=500, inner_tol=1e-6, max_sweeps=0,
                      allow_unconverged=False, precision=None):
-        """All incidence angles of the context in lockstep (mixed form); precision GS_MIXED_BF16
-        (default: the translation of all angles at once on the tensor cores) or GS_C64 (each angle
-        from the complex64 pair table); per-angle results through stats/get_beta/bragg(angle)."""
+        """All incidence angles of the context in lockstep (mixed form); precision GS_C64 (default:
+        each angle from the complex64 pair table) or GS_MIXED_BF16 (the translation of all angles at
+        once on the tensor cores); per-angle results through stats/get_beta/bragg(angle)."""
         o = gs_solve_opts(tol=tol, maxit=maxit, restart=restart,
-                          precision=GS_MIXED_BF16 if precision is None else precision, inner_tol=inner_tol,
+                          precision=GS_C64 if precision is None else precision, inner_tol=inner_tol,
                           max_sweeps=max_sweeps)
         ok = (GS_OK, GS_ERR_NOT_CONVERGED) if allow_unconverged else (GS_OK,)
         return self._check(self.lib.gs_solve_angles(self.ctx, ctypes.byref(o)), "gs_solve_angles", ok=ok)

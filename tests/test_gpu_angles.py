@@ -46,7 +46,8 @@ def test_angles_small_against_oracle(inner):
     gs.close()
 
 
-def test_angles_medium_against_oracle():
+@pytest.mark.parametrize("inner", ["c64", "bf16"])
+def test_angles_medium_against_oracle(inner):
     """150 disks, p = 8, eight angles spread over [-pi/3, pi/3] from the downward normal, the
     Wood angle among them; sampled angles against the oracle's dense solve."""
     from paper_1412_7466_gb300 import GratingSolver
@@ -59,7 +60,8 @@ def test_angles_medium_against_oracle():
     gs.set_incidence(thetas)
     gs.set_inclusions(dk)
     gs.factor()
-    gs.solve_angles(tol=1e-12, maxit=4000, restart=300)
+    from paper_1412_7466_gb300 import GS_C64, GS_MIXED_BF16
+    gs.solve_angles(tol=1e-12, maxit=4000, restart=300, precision=GS_C64 if inner == "c64" else GS_MIXED_BF16)
     for q in (0, 3, 7):
         prob = S.setup(g, thetas[q], dk)
         beta, _, _ = S.solve_dense(prob)
