@@ -221,10 +221,12 @@ int gs_stats_refinement(gs_ctx *ctx, int angle, int *outer);
  * V^*"): the FP32 and FP64 one-sided Jacobi sweeps it took and, in phase_ms[6] (host, nullable),
  * the device time in ms of its phases: assembly of A and f, pivoted QR, FP32 sweeps, orthogonal
  * polar step and R^* V, FP64 sweeps, U = Q V_x and V Sigma; in rot32[32], rot64[32] (host,
- * nullable) the pair rotations applied in each sweep (0 past the last).  GS_ERR_STATE before the
- * grating is factored (gs_factor or gs_factor_batch), GS_ERR_ARG for a bad angle.  Host-only. */
+ * nullable) the pair rotations applied in each sweep (0 past the last); in *ns_steps and ns_defect[6]
+ * (host, nullable) the Newton-Schulz steps of the polar step and the measured max |V^H V - I| before
+ * each of them and at the stop.  GS_ERR_STATE before the grating is factored (gs_factor or
+ * gs_factor_batch), GS_ERR_ARG for a bad angle.  Host-only. */
 int gs_factor_stats(gs_ctx *ctx, int angle, int *sweeps32, int *sweeps64, double *phase_ms, long long *rot32,
-                    long long *rot64);
+                    long long *rot64, int *ns_steps, double *ns_defect);
 /* Bragg amplitudes of the propagating orders (Sec. 2 rad1/rad2; Sec. 5 alpha = A^+(f - C beta)),
  * written to HOST arrays: orders_top[*n_top], c[*n_top], orders_bot[*n_bot], d[*n_bot], each of
  * capacity >= 2 K_rb + 1, and the relative flux error

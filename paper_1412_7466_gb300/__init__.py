@@ -95,7 +95,7 @@ _SIGS = {
     "gs_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
     "gs_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _dp]),
     "gs_stats_refinement": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
-    "gs_factor_stats": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _dp, _vp, _vp]),
+    "gs_factor_stats": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _dp, _vp, _vp, _ip, _dp]),
     "gs_probe_fma": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "gs_set_table_budget": (ctypes.c_int, [_vp, ctypes.c_double]),
     "gs_set_inclusions_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gs_inclusions)]),
@@ -390,11 +390,13 @@ class GratingSolver:
         """Sweeps and per-phase device times (ms) of the angle's grating factorisation."""
         s32, s64, ph = ctypes.c_int(), ctypes.c_int(), (ctypes.c_double * 6)()
         r32, r64 = (ctypes.c_longlong * 32)(), (ctypes.c_longlong * 32)()
-        self._check(self.lib.gs_factor_stats(self.ctx, angle, ctypes.byref(s32), ctypes.byref(s64), ph, r32, r64),
-                    "gs_factor_stats")
+        nss, nsd = ctypes.c_int(), (ctypes.c_double * 6)()
+        self._check(self.lib.gs_factor_stats(self.ctx, angle, ctypes.byref(s32), ctypes.byref(s64), ph, r32, r64,
+                                             ctypes.byref(nss), nsd), "gs_factor_stats")
         names = ("assemble", "qr", "jacobi_fp32", "polar_step", "jacobi_fp64", "u_v")
         return {"sweeps_fp32": s32.value, "sweeps_fp64": s64.value, "phase_ms": dict(zip(names, list(ph))),
-                "rotations_fp32": list(r32)[:s32.value], "rotations_fp64": list(r64)[:s64.value]}
+                "rotations_fp32": list(r32)[:s32.value], "rotations_fp64": list(r64)[:s64.value],
+                "newton_schulz_steps": nss.value, "newton_schulz_defects": list(nsd)[:min(nss.value + 1, 6)]}
 
     def get_beta(self, angle=0):
         t = self._cvec(self.dims()["n"])

@@ -61,6 +61,8 @@ struct AngleData {
     int sweeps32 = 0;            // FP32-guided sweeps before them
     double phase_ms[6] = {};     // factorisation phases: assembly, QR, FP32 sweeps, polar step, FP64 sweeps, U/V
     long long rot32[32] = {}, rot64[32] = {};   // rotations applied in each FP32 / FP64 sweep
+    double ns_defect[6] = {};    // measured max |V^H V - I| before each Newton-Schulz step
+    int ns_iters = 0;            // Newton-Schulz steps taken
     int iters = 0;               // GMRES iterations (all inner iterations for the mixed solve)
     int outer = 0;               // refinement sweeps of the mixed solve (0 for FP64)
     double relres = -1.0;

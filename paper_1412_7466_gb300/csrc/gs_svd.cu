@@ -813,6 +813,9 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     cplx *G = a.Vr, *T = a.W;   // n x n scratch (both are written later)
     GS_COUNT_LAUNCH(c);
     k_to_c128<<<eb, 256, 0, st>>>(V32, nn, Vx);
+    double prev_defect = 1.0;
+    for (int q = 0; q < 6; ++q) a.ns_defect[q] = 0.0;
+    a.ns_iters = 6;
     for (int it = 0; it < 6; ++it) {
         GS_COUNT_LAUNCH(c);
         k_zgemm_hn<<<zg, 256, 0, st>>>(Vx, Vx, G, n);
@@ -826,7 +829,14 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         double defect;
         std::memcpy(&defect, &hb, sizeof(defect));
         if (!(defect < 0.5)) return gs_fail(c, GS_ERR_NUMERIC, "grating factorisation: FP32 rotations not orthogonal");
+        // Stop when V is as orthogonal as FP64 can show.  A step maps a defect d to about 0.75 d^2, but
+        // the FP64 Gram matrix itself carries rounding of sqrt(n) eps to n eps (4.5e-15 to 1.9e-13 at
+        // n = 1689): a small measured defect far above the previous one's square is that rounding
+        a.ns_defect[it] = defect;
+        a.ns_iters = it;
         if (defect < 1e-14) break;
+        if (it > 0 && defect < 1e-10 && defect > 100.0 * 0.75 * prev_defect * prev_defect) break;
+        prev_defect = defect;
         GS_COUNT_LAUNCH(c);
         k_ns_step<<<eb, 256, 0, st>>>(G, n);
         GS_COUNT_LAUNCH(c);
@@ -883,7 +893,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
 }
 
 int gs_factor_stats(gs_ctx *c, int angle, int *sweeps32, int *sweeps64, double *phase_ms, long long *rot32,
-                    long long *rot64) {
+                    long long *rot64, int *ns_steps, double *ns_defect) {
     if (!c) return GS_ERR_ARG;
     if (!c->grating_ready) return gs_fail(c, GS_ERR_STATE, "the grating has not been factored");
     if (angle < 0 || angle >= (int)c->ang.size()) return gs_fail(c, GS_ERR_ARG, "angle index out of range");
@@ -896,5 +906,8 @@ int gs_factor_stats(gs_ctx *c, int angle, int *sweeps32, int *sweeps64, double *
         if (rot32) rot32[q] = a.rot32[q];
         if (rot64) rot64[q] = a.rot64[q];
     }
+    if (ns_steps) *ns_steps = a.ns_iters;
+    if (ns_defect)
+        for (int q = 0; q < 6; ++q) ns_defect[q] = a.ns_defect[q];
     return GS_OK;
 }

@@ -208,6 +208,10 @@ def test_factor_stats(small):
     assert st["rotations_fp64"][-1] == 0 and st["rotations_fp64"][0] > 0
     n = prob.eg.A.shape[1]
     assert max(st["rotations_fp64"]) <= n * (n - 1) // 2
+    # the polar step stopped at the FP64 floor: each Newton-Schulz step squared the defect until then
+    d = st["newton_schulz_defects"]
+    assert 1 <= st["newton_schulz_steps"] <= 6 and d[-1] < 1e-10
+    assert all(b < a for a, b in zip(d, d[1:]))
     ph = st["phase_ms"]
     assert set(ph) == {"assemble", "qr", "jacobi_fp32", "polar_step", "jacobi_fp64", "u_v"}
     assert all(v > 0 for v in ph.values()) and sum(ph.values()) < 60e3
