@@ -222,8 +222,10 @@ int gs_stats_refinement(gs_ctx *ctx, int angle, int *outer);
  * the device time in ms of its phases: assembly of A and f, pivoted QR, FP32 sweeps, orthogonal
  * polar step and R^* V, FP64 sweeps, U = Q V_x and V Sigma; in rot32[32], rot64[32] (host,
  * nullable) the pair rotations applied in each sweep (0 past the last); in *ns_steps and ns_defect[6]
- * (host, nullable) the Newton-Schulz steps of the polar step and the measured max |V^H V - I| before
- * each of them and at the stop.  GS_ERR_STATE before the grating is factored (gs_factor or
+ * (host, nullable) the FP64 Newton-Schulz steps of the polar step and the measured max |V^H V - I|
+ * before each of them and at the stop; where the last step was taken because the Frobenius norm x of
+ * V^H V - I before it lay below 1e-7, the value after it is the bound (3/4) x^2 + x^3/4 and not a
+ * measurement.  GS_ERR_STATE before the grating is factored (gs_factor or
  * gs_factor_batch), GS_ERR_ARG for a bad angle.  Host-only. */
 int gs_factor_stats(gs_ctx *ctx, int angle, int *sweeps32, int *sweeps64, double *phase_ms, long long *rot32,
                     long long *rot64, int *ns_steps, double *ns_defect);

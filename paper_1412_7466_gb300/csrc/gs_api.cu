@@ -287,7 +287,7 @@ int gs_create(gs_ctx **out, int device, void *cuda_stream) {
     }
     if (cudaMalloc((void **)&c->dscal, sizeof(double) * 16) != cudaSuccess ||
         cudaMallocHost((void **)&c->hscal, sizeof(double) * 16) != cudaSuccess ||
-        cudaMalloc((void **)&c->dcount, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&c->dcount, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void **)&c->terr, sizeof(int)) != cudaSuccess || cudaMemset(c->terr, 0, sizeof(int)) != cudaSuccess ||
         cudaMalloc((void **)&c->bar, 2 * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();

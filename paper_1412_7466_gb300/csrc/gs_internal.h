@@ -164,7 +164,7 @@ struct gs_ctx {
     cplx *cs = nullptr, *sn = nullptr, *gg = nullptr, *yy = nullptr;
     double *dscal = nullptr;                             // device scalars
     double *hscal = nullptr;                             // pinned host scalars
-    unsigned long long *dcount = nullptr;
+    unsigned long long *dcount = nullptr;               // two device counters (rotations; Gram defect)
     unsigned *bar = nullptr;                             // grid barrier (count, generation) of cooperative kernels
 
     // instrumentation: kernel launches issued, optional event timing of the translation kernel

@@ -23,6 +23,7 @@
 // coef_j = 1/(sigma_j max(sigma_j, eps)), sigma_j = ||W_x e_j||.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "gs_internal.h"
 
@@ -55,14 +56,9 @@ __global__ void k_identity(cplx *V, int n) {
     V[id] = C(r == c ? 1.0 : 0.0, 0.0);
 }
 
-// One round of the circle schedule: block k rotates the pair (player(k), player(npad-1-k)).
-__global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, int n, int r, int npad,
-                                                       double tol, unsigned long long *nrot) {
-    int k = blockIdx.x;
-    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
-    int a = player(k), b = player(npad - 1 - k);
-    if (a >= n || b >= n) return;
-    int pc = a < b ? a : b, qc = a < b ? b : a;
+// Rotation of the column pair (pc, qc), pc < qc, of W (columns of length m) and of V (length n) by
+// the whole block, if the pair is further than tol from orthogonal (then *nrot is incremented).
+__device__ void jacobi_pair(cplx *W, int m, cplx *V, int n, int pc, int qc, double tol, unsigned long long *nrot) {
     cplx *wp = W + (size_t)pc * m, *wq = W + (size_t)qc * m;
     __shared__ double4 sh4[32];
     __shared__ double rot[5];
@@ -131,6 +127,37 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, 
     }
 }
 
+// One round of the circle schedule: block k rotates the pair (player(k), player(npad-1-k)).
+__global__ void __launch_bounds__(JTPB) k_jacobi_round(cplx *W, int m, cplx *V, int n, int r, int npad,
+                                                       double tol, unsigned long long *nrot) {
+    const int k = blockIdx.x;
+    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
+    const int a = player(k), b = player(npad - 1 - k);
+    if (a >= n || b >= n) return;
+    jacobi_pair(W, m, V, n, a < b ? a : b, a < b ? b : a, tol, nrot);
+}
+
+// One round of listed pairs (disjoint columns): block k rotates pairs[k] = (pc, qc), pc < qc
+__global__ void __launch_bounds__(JTPB) k_jacobi_pairs(cplx *W, int m, cplx *V, int n, const int2 *pairs,
+                                                       double tol, unsigned long long *nrot) {
+    const int2 pq = pairs[blockIdx.x];
+    jacobi_pair(W, m, V, n, pq.x, pq.y, tol, nrot);
+}
+
+// The pairs (r, c), r < c, whose Gram entry G[r][c] = <w_r, w_c> (G column-major n x n) lies further
+// than tol from orthogonal, by the criterion of jacobi_pair; appended to pairs[] through *count
+__global__ void k_gram_violators(const cplx *G, int n, double tol, int2 *pairs, unsigned long long *count) {
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    const int r = (int)(id % n), c = (int)(id / n);
+    if (r >= c) return;
+    const cplx g = G[id];
+    const double ga = hypot(g.x, g.y);
+    if (ga == 0.0 || ga <= tol * sqrt(G[(size_t)r * n + r].x * G[(size_t)c * n + c].x)) return;
+    const unsigned long long k = atomicAdd(count, 1ull);
+    pairs[k] = make_int2(r, c);
+}
+
 // FP32 copy of a complex128 array
 __global__ void k_to_c64(const cplx *__restrict__ X, long n, float2 *__restrict__ Y) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,13 +197,8 @@ __device__ __forceinline__ void block_sum4_f(float &a, float &b, float &c, float
 // FP32 round on the copy W32 with the rotations accumulated in V (FP32), one block per pair: the
 // pair's rotation is computed in FP64 from FP32 dot products and applied in FP32.  (One warp per
 // pair was measured slower: a round then has too few blocks to hide the memory latency.)
-__global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, float2 *V, int n, int r, int npad,
-                                                           float tol, unsigned long long *nrot) {
-    int k = blockIdx.x;
-    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
-    int a = player(k), b = player(npad - 1 - k);
-    if (a >= n || b >= n) return;
-    int pc = a < b ? a : b, qc = a < b ? b : a;
+__device__ void rotate_pair_f32(float2 *W32, int m, float2 *V, int n, int pc, int qc, float tol,
+                                unsigned long long *nrot) {
     float2 *wp = W32 + (size_t)pc * m, *wq = W32 + (size_t)qc * m;
     __shared__ float4 sh4[32];
     __shared__ double rot[5];
@@ -222,6 +244,35 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, f
         vp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
         vq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
     }
+}
+
+__global__ void __launch_bounds__(JTPB) k_jacobi_round_f32(float2 *W32, int m, float2 *V, int n, int r, int npad,
+                                                           float tol, unsigned long long *nrot) {
+    const int k = blockIdx.x;
+    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1; };
+    const int a = player(k), b = player(npad - 1 - k);
+    if (a >= n || b >= n) return;
+    rotate_pair_f32(W32, m, V, n, a < b ? a : b, a < b ? b : a, tol, nrot);
+}
+
+// FP32 round of listed pairs (disjoint columns): block k rotates pairs[k] = (pc, qc), pc < qc
+__global__ void __launch_bounds__(JTPB) k_jacobi_pairs_f32(float2 *W32, int m, float2 *V, int n, const int2 *pairs,
+                                                           float tol, unsigned long long *nrot) {
+    const int2 pq = pairs[blockIdx.x];
+    rotate_pair_f32(W32, m, V, n, pq.x, pq.y, tol, nrot);
+}
+
+// k_gram_violators on an FP32 Gram matrix
+__global__ void k_gram_violators_f32(const float2 *G, int n, float tol, int2 *pairs, unsigned long long *count) {
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    const int r = (int)(id % n), c = (int)(id / n);
+    if (r >= c) return;
+    const float2 g = G[id];
+    const double ga = hypot((double)g.x, (double)g.y);
+    if (ga == 0.0 || ga <= (double)tol * sqrt((double)G[(size_t)r * n + r].x * (double)G[(size_t)c * n + c].x)) return;
+    const unsigned long long k = atomicAdd(count, 1ull);
+    pairs[k] = make_int2(r, c);
 }
 
 // ---- one whole FP32 sweep per launch (cooperative) -------------------------------------------------
@@ -350,17 +401,33 @@ __global__ void k_ns_step(cplx *G, int n) {
     G[id] = C((r == c ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
 }
 
-// out = max |G - I| (non-negative doubles order like their bit patterns)
-__global__ void k_offdiag_max(const cplx *G, int n, unsigned long long *out) {
+// out[0] = max |G - I| (non-negative doubles order like their bit patterns), out[1] (a double) +=
+// ||G - I||_F^2; 256 threads per block
+__global__ void __launch_bounds__(256) k_offdiag_max(const cplx *G, int n, unsigned long long *out) {
+    __shared__ double ssq[8];
     long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    double v = 0.0;
+    double v = 0.0, q = 0.0;
     if (id < (long)n * n) {
         int r = (int)(id % n), c = (int)(id / n);
         const cplx g = G[id];
-        v = hypot(g.x - (r == c ? 1.0 : 0.0), g.y);
+        const double re = g.x - (r == c ? 1.0 : 0.0);
+        v = hypot(re, g.y);
+        q = re * re + g.y * g.y;
     }
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+    for (int o = 16; o > 0; o >>= 1) {
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(v));
+        ssq[threadIdx.x >> 5] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += ssq[w];
+        atomicAdd((double *)(out + 1), t);
+    }
 }
 
 // C = A^H B, complex128, all n x n column-major
@@ -455,6 +522,81 @@ __global__ void __launch_bounds__(256) k_zgemm_hn(const cplx *__restrict__ A, co
             if (col < n) Cm[(size_t)col * n + row] = acc[i][j];
         }
     }
+}
+
+// ---- one FP32 Newton-Schulz step on the FP32 rotations (end of the FP32 sweeps) --------------------
+// V32 collects ~10^4 FP32 rotations per column and leaves the FP32 sweeps ~1e-4..1e-3 from orthogonal;
+// one FP32 step V <- V (3I - V^H V)/2 brings it to the FP32 floor (~1e-6), so that the FP64 steps
+// that follow start there.  Complex FP32 GEMMs with the tiling of the FP64 ones below.
+__device__ __forceinline__ void cfma_f(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+// C = A^H B (conj_a) or A B, complex64, all n x n column-major (64 x 64 tile per block, 4 x 4 per thread)
+template <bool CONJ_A>
+__global__ void __launch_bounds__(256) k_cgemm_f32(const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                   float2 *__restrict__ Cm, int n) {
+    constexpr int TG = 64, TK = 8;
+    __shared__ float2 As[TK][TG + 1], Bs[TK][TG + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * TG, j0 = blockIdx.y * TG;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < n; k0 += TK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < TG * TK; e += 256) {
+            if (CONJ_A) {   // (A^H)[i][k] = conj(A[k][i]); column i of A is contiguous in k
+                const int kk = e % TK, idx = e / TK;
+                float2 v = make_float2(0.f, 0.f);
+                if (i0 + idx < n && k0 + kk < n) {
+                    v = A[(size_t)(i0 + idx) * n + k0 + kk];
+                    v.y = -v.y;
+                }
+                As[kk][idx] = v;
+            } else {
+                const int i = e % TG, k = e / TG;
+                As[k][i] = (i0 + i < n && k0 + k < n) ? A[(size_t)(k0 + k) * n + i0 + i] : make_float2(0.f, 0.f);
+            }
+            const int kk = e % TK, j = e / TK;
+            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? B[(size_t)(j0 + j) * n + k0 + kk] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; ++k) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma_f(acc[i][j], a[i], b[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = i0 + ty + 16 * i;
+        if (row >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = j0 + tx + 16 * j;
+            if (col < n) Cm[(size_t)col * n + row] = acc[i][j];
+        }
+    }
+}
+
+// G <- 1.5 I - 0.5 G in complex64
+__global__ void k_ns_step_f32(float2 *G, int n) {
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)n * n) return;
+    const int r = (int)(id % n), c = (int)(id / n);
+    const float2 g = G[id];
+    G[id] = make_float2((r == c ? 1.5f : 0.f) - 0.5f * g.x, -0.5f * g.y);
 }
 
 __global__ void k_sigma(const cplx *W, int m, int n, double eps, double *sigma, double *coef) {
@@ -704,6 +846,34 @@ __global__ void k_permute_rows(const cplx *Wx, int n, const int *perm, cplx *Vr)
     Vr[(size_t)perm[i] * n + j] = Wx[id];
 }
 
+// Rounds of disjoint pairs for the nv pairs listed at dlist (device): taken in column order (so that
+// the factorisation does not depend on the order in which the device listed them), each pair goes to
+// the round after the later of its two columns' last rounds.  The pairs are written round by round
+// to dsched (device) and round r holds dsched[rstart[r] .. rstart[r+1]).
+int schedule_pairs(gs_ctx *c, const int2 *dlist, size_t nv, int n, int2 *dsched, std::vector<int> &rstart,
+                   std::vector<int2> &hp, std::vector<int2> &hs) {
+    hp.resize(nv);
+    GS_CUDA(c, cudaMemcpyAsync(hp.data(), dlist, sizeof(int2) * nv, cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::sort(hp.begin(), hp.end(), [](int2 u, int2 v) { return u.x != v.x ? u.x < v.x : u.y < v.y; });
+    std::vector<int> last(n, -1), rnd(nv);
+    int nr = 0;
+    for (size_t q = 0; q < nv; ++q) {
+        const int r = std::max(last[hp[q].x], last[hp[q].y]) + 1;
+        last[hp[q].x] = last[hp[q].y] = r;
+        rnd[q] = r;
+        nr = std::max(nr, r + 1);
+    }
+    rstart.assign(nr + 1, 0);
+    for (size_t q = 0; q < nv; ++q) ++rstart[rnd[q] + 1];
+    for (int r = 0; r < nr; ++r) rstart[r + 1] += rstart[r];
+    hs.resize(nv);
+    std::vector<int> pos(rstart.begin(), rstart.end() - 1);
+    for (size_t q = 0; q < nv; ++q) hs[pos[rnd[q]]++] = hp[q];
+    GS_CUDA(c, cudaMemcpyAsync(dsched, hs.data(), sizeof(int2) * nv, cudaMemcpyHostToDevice, c->stream));
+    return GS_OK;
+}
+
 }  // namespace
 
 int gs_factor_angle(gs_ctx *c, AngleData &a) {
@@ -767,6 +937,14 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     GS_CHECK_LAUNCH(c);
     a.sweeps32 = 0;
     for (int q = 0; q < 32; ++q) a.rot32[q] = a.rot64[q] = 0;
+    // Once a sweep has rotated fewer than half of the pairs, the next ones start from the FP32 Gram
+    // matrix X32^H X32 and rotate only the pairs it lists (as the FP64 sweeps below)
+    const dim3 zg((n + ZG - 1) / ZG, (n + ZG - 1) / ZG);
+    const long npairs = (long)n * (n - 1) / 2;
+    int2 *vlist = (int2 *)a.W, *vsched = vlist + npairs;   // a.W (m x n complex128) is free until step 2b
+    std::vector<int2> hpairs, hsched;
+    std::vector<int> rstart;
+    long long prev_rot = npairs;
     // one cooperative launch per sweep when all its blocks can be resident, else one launch per round
     int coop = 0, per_sm = 0, dev_coop = 0;
     cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, c->device);
@@ -774,8 +952,37 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         coop = std::min(npad / 2, per_sm * c->sms);
     cudaGetLastError();
     for (int sweep = 0; sweep < 20; ++sweep) {
-        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
-        if (coop > 0) {
+        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, 2 * sizeof(unsigned long long), st));
+        bool circle = true;
+        if (sweep > 0 && npairs > 0 && 2 * prev_rot < npairs) {
+            float2 *G32 = (float2 *)a.Vr;
+            GS_COUNT_LAUNCH(c);
+            k_cgemm_f32<true><<<zg, 256, 0, st>>>(X32, X32, G32, n);
+            GS_COUNT_LAUNCH(c);
+            k_gram_violators_f32<<<eb, 256, 0, st>>>(G32, n, 1e-5f, vlist, c->dcount + 1);
+            GS_CHECK_LAUNCH(c);
+            unsigned long long nv = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&nv, c->dcount + 1, sizeof(nv), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            if (nv == 0) {
+                a.sweeps32 = sweep + 1;
+                a.rot32[sweep] = 0;
+                break;
+            }
+            // listed rounds unless there are more of them than a circle sweep has
+            if ((long)nv <= npairs / 4) GS_TRY(schedule_pairs(c, vlist, nv, n, vsched, rstart, hpairs, hsched));
+            if ((long)nv <= npairs / 4 && (int)rstart.size() - 1 <= npad - 1) {
+                circle = false;
+                const int nr = (int)rstart.size() - 1;
+                for (int r = 0; r < nr; ++r) {
+                    GS_COUNT_LAUNCH(c);
+                    k_jacobi_pairs_f32<<<rstart[r + 1] - rstart[r], JTPB, 0, st>>>(X32, n, V32, n, vsched + rstart[r],
+                                                                                1e-5f, c->dcount);
+                }
+                GS_CHECK_LAUNCH(c);
+            }
+        }
+        if (circle && coop > 0) {
             GS_CUDA(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
             GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), st));
             float tol32 = 1e-5f;
@@ -783,14 +990,14 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
             void *args[] = {&X32, &mm, &V32, &nn_, &np_, &tol32, &c->dcount, &c->bar, &c->terr};
             GS_COUNT_LAUNCH(c);
             GS_CUDA(c, cudaLaunchCooperativeKernel((const void *)k_jacobi_sweep_f32, dim3(coop), dim3(JTPB), args, 0, st));
-        } else {
+        } else if (circle) {
             for (int r = 0; r < npad - 1; ++r) {
                 GS_COUNT_LAUNCH(c);
                 k_jacobi_round_f32<<<npad / 2, JTPB, 0, st>>>(X32, n, V32, n, r, npad, 1e-5f, c->dcount);
             }
         }
         GS_CHECK_LAUNCH(c);
-        if (coop > 0) {
+        if (circle && coop > 0) {
             int herr = 0;
             GS_CUDA(c, cudaMemcpyAsync(&herr, c->terr, sizeof(int), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
@@ -804,13 +1011,25 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         GS_CUDA(c, cudaStreamSynchronize(st));
         a.sweeps32 = sweep + 1;
         a.rot32[sweep] = (long long)h;
+        prev_rot = (long long)h;
         if (h == 0) break;
     }
     GS_CUDA(c, cudaEventRecord(ev.e[3], st));
-    // 2b. V_x = the FP64 orthogonal polar factor of V32 (Newton-Schulz, V <- V (3I - V^H V)/2,
-    //     quadratic from an orthogonality defect of ~1e-5), then X = R^* V_x in FP64
-    const dim3 zg((n + ZG - 1) / ZG, (n + ZG - 1) / ZG);
+    // 2b. V_x = the FP64 orthogonal polar factor of V32 (Newton-Schulz, V <- V (3I - V^H V)/2, a defect
+    //     e of V^H V - I going to 0.75 e^2 - 0.25 e^3: one step in FP32, then FP64), X = R^* V_x in FP64
     cplx *G = a.Vr, *T = a.W;   // n x n scratch (both are written later)
+    {
+        // one FP32 step first (its G32 and T32 in the n x n complex128 scratch G, two complex64 halves)
+        float2 *G32 = (float2 *)G, *T32 = (float2 *)G + nn;
+        GS_COUNT_LAUNCH(c);
+        k_cgemm_f32<true><<<zg, 256, 0, st>>>(V32, V32, G32, n);
+        GS_COUNT_LAUNCH(c);
+        k_ns_step_f32<<<eb, 256, 0, st>>>(G32, n);
+        GS_COUNT_LAUNCH(c);
+        k_cgemm_f32<false><<<zg, 256, 0, st>>>(V32, G32, T32, n);
+        GS_CHECK_LAUNCH(c);
+        GS_CUDA(c, cudaMemcpyAsync(V32, T32, sizeof(float2) * nn, cudaMemcpyDeviceToDevice, st));
+    }
     GS_COUNT_LAUNCH(c);
     k_to_c128<<<eb, 256, 0, st>>>(V32, nn, Vx);
     double prev_defect = 1.0;
@@ -819,15 +1038,16 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     for (int it = 0; it < 6; ++it) {
         GS_COUNT_LAUNCH(c);
         k_zgemm_hn<<<zg, 256, 0, st>>>(Vx, Vx, G, n);
-        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
+        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, 2 * sizeof(unsigned long long), st));
         GS_COUNT_LAUNCH(c);
         k_offdiag_max<<<eb, 256, 0, st>>>(G, n, c->dcount);
         GS_CHECK_LAUNCH(c);
-        unsigned long long hb = 0;
-        GS_CUDA(c, cudaMemcpyAsync(&hb, c->dcount, sizeof(hb), cudaMemcpyDeviceToHost, st));
+        unsigned long long hb[2] = {0, 0};
+        GS_CUDA(c, cudaMemcpyAsync(hb, c->dcount, sizeof(hb), cudaMemcpyDeviceToHost, st));
         GS_CUDA(c, cudaStreamSynchronize(st));
-        double defect;
-        std::memcpy(&defect, &hb, sizeof(defect));
+        double defect, fro2;
+        std::memcpy(&defect, &hb[0], sizeof(defect));
+        std::memcpy(&fro2, &hb[1], sizeof(fro2));
         if (!(defect < 0.5)) return gs_fail(c, GS_ERR_NUMERIC, "grating factorisation: FP32 rotations not orthogonal");
         // Stop when V is as orthogonal as FP64 can show.  A step maps a defect d to about 0.75 d^2, but
         // the FP64 Gram matrix itself carries rounding of sqrt(n) eps to n eps (4.5e-15 to 1.9e-13 at
@@ -837,11 +1057,21 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         if (defect < 1e-14) break;
         if (it > 0 && defect < 1e-10 && defect > 100.0 * 0.75 * prev_defect * prev_defect) break;
         prev_defect = defect;
+        // ||V^H V - I||_2 <= ||V^H V - I||_F, and a step leaves at most 0.75 x^2 + 0.25 x^3 of a
+        // spectral defect x: below x = 1e-7 the step about to be taken ends below 1e-14, where the
+        // loop stops anyway, so the Gram matrix need not be formed again to see it
+        const double xf = std::sqrt(fro2);
+        const bool last = xf < 1e-7;
         GS_COUNT_LAUNCH(c);
         k_ns_step<<<eb, 256, 0, st>>>(G, n);
         GS_COUNT_LAUNCH(c);
         k_zgemm_nn<<<zg, 256, 0, st>>>(Vx, G, T, n);
         GS_CUDA(c, cudaMemcpyAsync(Vx, T, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
+        if (last && it + 1 < 6) {
+            a.ns_defect[it + 1] = 0.75 * xf * xf + 0.25 * xf * xf * xf;   // the bound, not a measurement
+            a.ns_iters = it + 1;
+            break;
+        }
     }
     GS_COUNT_LAUNCH(c);
     k_zgemm_nn<<<zg, 256, 0, st>>>(X, Vx, T, n);
@@ -850,11 +1080,45 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     GS_CUDA(c, cudaEventRecord(ev.e[4], st));
     const double tol = 1e-14;
     a.sweeps = 0;
+    // From the third sweep on the pairs still to rotate are few (~1% of them, then a handful): the
+    // Gram matrix X^H X (one FP64 GEMM, at several times the FP64 rate of a dots-only circle sweep)
+    // finds them, and only they are rotated, in rounds of disjoint pairs.  A sweep ends the phase
+    // when the Gram matrix shows no pair further than tol from orthogonal or when none of the
+    // listed pairs, re-tested from its columns, needs a rotation.
     for (int sweep = 0; sweep < 30; ++sweep) {
-        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, sizeof(unsigned long long), st));
-        for (int r = 0; r < npad - 1; ++r) {
+        GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, 2 * sizeof(unsigned long long), st));
+        bool circle = true;
+        if (sweep >= 2 && npairs > 0) {
             GS_COUNT_LAUNCH(c);
-            k_jacobi_round<<<npad / 2, JTPB, 0, st>>>(X, n, Vx, n, r, npad, tol, c->dcount);
+            k_zgemm_hn<<<zg, 256, 0, st>>>(X, X, G, n);
+            GS_COUNT_LAUNCH(c);
+            k_gram_violators<<<eb, 256, 0, st>>>(G, n, tol, vlist, c->dcount + 1);
+            GS_CHECK_LAUNCH(c);
+            unsigned long long nv = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&nv, c->dcount + 1, sizeof(nv), cudaMemcpyDeviceToHost, st));
+            GS_CUDA(c, cudaStreamSynchronize(st));
+            if (nv == 0) {
+                a.sweeps = sweep + 1;
+                if (sweep < 32) a.rot64[sweep] = 0;
+                break;
+            }
+            if ((long)nv <= npairs / 4) GS_TRY(schedule_pairs(c, vlist, nv, n, vsched, rstart, hpairs, hsched));
+            if ((long)nv <= npairs / 4 && (int)rstart.size() - 1 <= npad - 1) {
+                circle = false;
+                const int nr = (int)rstart.size() - 1;
+                for (int r = 0; r < nr; ++r) {
+                    GS_COUNT_LAUNCH(c);
+                    k_jacobi_pairs<<<rstart[r + 1] - rstart[r], JTPB, 0, st>>>(X, n, Vx, n, vsched + rstart[r], tol,
+                                                                            c->dcount);
+                }
+                GS_CHECK_LAUNCH(c);
+            }
+        }
+        if (circle) {
+            for (int r = 0; r < npad - 1; ++r) {
+                GS_COUNT_LAUNCH(c);
+                k_jacobi_round<<<npad / 2, JTPB, 0, st>>>(X, n, Vx, n, r, npad, tol, c->dcount);
+            }
         }
         GS_CHECK_LAUNCH(c);
         unsigned long long h = 0;
