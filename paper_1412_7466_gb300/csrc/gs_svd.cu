@@ -380,6 +380,156 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_sweep_f32(float2 *W32, int m, f
     }
 }
 
+// ---- blocked FP32 sweep: super-columns of SC columns held in shared memory (cooperative) -----------
+// The columns are grouped into super-columns of SC; a round of the circle schedule over the
+// super-columns gives each block two of them.  The block copies their 2 SC columns of W32 into shared
+// memory, rotates all SC^2 cross pairs there in SC local rounds of SC disjoint pairs (in the first
+// round also the pairs inside each super-column), accumulates the local rotations into a 2SC x 2SC
+// unitary Q, writes the columns back and applies Q to the same columns of V in one pass.  A sweep is
+// then ceil(n / SC) - 1 grid rounds instead of n - 1, each moving the columns through L2 once, and
+// every column pair is still rotated once per sweep (a block-cyclic ordering).
+constexpr int SC = 6;
+constexpr int SCT = SC * 64;   // two warps per pair slot
+
+__device__ __forceinline__ int circle_player(int pos, int r, int np) {
+    return pos == 0 ? 0 : ((pos - 1 + r) % (np - 1)) + 1;
+}
+
+__global__ void __launch_bounds__(SCT) k_jacobi_sweep_blk_f32(float2 *W32, int m, float2 *V, int n, int nsc, int nscp,
+                                                              float tol, unsigned long long *nrot, unsigned *bar,
+                                                              int *err) {
+    extern __shared__ float2 xs[];   // 2 SC columns of length m
+    __shared__ float2 Qc[2 * SC][2 * SC];   // Qc[j][i] = Q[i][j]: column j of Q
+    __shared__ float4 red[SC][2];
+    __shared__ float rot[SC][5];
+    __shared__ int gcol[2 * SC];
+    __shared__ unsigned cnt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pr = warp >> 1, half = warp & 1, tp = threadIdx.x & 63;
+
+    // one local round: pair slot pr rotates local columns (lp, lq) if both exist
+    auto local_round = [&](int lp, int lq) {
+        const int gp = gcol[lp], gq = gcol[lq];
+        const bool live = gp >= 0 && gq >= 0;
+        if (live && gp > gq) {   // the lower global column plays p, as in the circle sweep
+            const int t = lp;
+            lp = lq;
+            lq = t;
+        }
+        float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+        if (live) {
+            const float2 *xp = xs + (size_t)lp * m, *xq = xs + (size_t)lq * m;
+            for (int i = tp; i < m; i += 64) {
+                const float2 x = xp[i], y = xq[i];
+                al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
+                be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
+                gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));   // conj(x) y
+                gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+            }
+            al = warp_sum_f(al);
+            be = warp_sum_f(be);
+            gr = warp_sum_f(gr);
+            gi = warp_sum_f(gi);
+            if (lane == 0) red[pr][half] = make_float4(al, be, gr, gi);
+        }
+        __syncthreads();
+        if (live && tp == 0) {
+            const float4 u = red[pr][0], v = red[pr][1];
+            al = u.x + v.x;
+            be = u.y + v.y;
+            gr = u.z + v.z;
+            gi = u.w + v.w;
+            const float g = hypotf(gr, gi);
+            if (g == 0.f || g <= tol * sqrtf(al) * sqrtf(be)) {
+                rot[pr][0] = 0.f;
+            } else {
+                const float zeta = (be - al) / (2.f * g);
+                const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+                const float cc = 1.f / sqrtf(fmaf(t, t, 1.f));
+                rot[pr][0] = 1.f;
+                rot[pr][1] = cc;
+                rot[pr][2] = cc * t;
+                rot[pr][3] = gr / g;
+                rot[pr][4] = -gi / g;
+                atomicAdd(&cnt, 1u);
+            }
+        }
+        __syncthreads();
+        if (live && rot[pr][0] != 0.f) {
+            const float cf = rot[pr][1], sf = rot[pr][2], er = rot[pr][3], ei = rot[pr][4];
+            float2 *xp = xs + (size_t)lp * m, *xq = xs + (size_t)lq * m;
+            for (int i = tp; i < m; i += 64) {
+                const float2 x = xp[i], y0 = xq[i];
+                const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+                xp[i] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
+                xq[i] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
+            }
+            if (tp < 2 * SC) {
+                const float2 x = Qc[lp][tp], y0 = Qc[lq][tp];
+                const float2 y = make_float2(y0.x * er - y0.y * ei, y0.x * ei + y0.y * er);
+                Qc[lp][tp] = make_float2(cf * x.x - sf * y.x, cf * x.y - sf * y.y);
+                Qc[lq][tp] = make_float2(sf * x.x + cf * y.x, sf * x.y + cf * y.y);
+            }
+        }
+        __syncthreads();
+    };
+
+    for (int r = 0; r < nscp - 1; ++r) {
+        for (int k = blockIdx.x; k < nscp / 2; k += gridDim.x) {
+            const int A = circle_player(k, r, nscp), B = circle_player(nscp - 1 - k, r, nscp);
+            if (threadIdx.x < 2 * SC) {
+                const int sc = threadIdx.x < SC ? A : B, j = sc * SC + threadIdx.x % SC;
+                gcol[threadIdx.x] = (sc < nsc && j < n) ? j : -1;
+            }
+            if (threadIdx.x < 4 * SC * SC) {
+                const int j = threadIdx.x / (2 * SC), i = threadIdx.x % (2 * SC);
+                Qc[j][i] = make_float2(i == j ? 1.f : 0.f, 0.f);
+            }
+            if (threadIdx.x == 0) cnt = 0;
+            __syncthreads();
+            for (int l = 0; l < 2 * SC; ++l) {
+                const float2 *src = W32 + (size_t)(gcol[l] >= 0 ? gcol[l] : 0) * m;
+                for (int i = threadIdx.x; i < m; i += SCT)
+                    xs[(size_t)l * m + i] = gcol[l] >= 0 ? __ldcg(&src[i]) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            if (r == 0) {   // the pairs inside each super-column: a circle over its SC columns
+                for (int t = 0; t < SC - 1; ++t) {
+                    const int u = pr % (SC / 2), base = pr < SC / 2 ? 0 : SC;
+                    local_round(base + circle_player(u, t, SC), base + circle_player(SC - 1 - u, t, SC));
+                }
+            }
+            for (int t = 0; t < SC; ++t) local_round(pr, SC + (pr + t) % SC);
+            for (int l = 0; l < 2 * SC; ++l) {
+                if (gcol[l] < 0) continue;
+                float2 *dst = W32 + (size_t)gcol[l] * m;
+                for (int i = threadIdx.x; i < m; i += SCT) __stcg(&dst[i], xs[(size_t)l * m + i]);
+            }
+            for (int row = threadIdx.x; row < n; row += SCT) {
+                float2 v[2 * SC];
+#pragma unroll
+                for (int l = 0; l < 2 * SC; ++l)
+                    v[l] = gcol[l] >= 0 ? __ldcg(&V[(size_t)gcol[l] * n + row]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 2 * SC; ++j) {
+                    if (gcol[j] < 0) continue;
+                    float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int l = 0; l < 2 * SC; ++l) {
+                        const float2 q = Qc[j][l];
+                        o.x = fmaf(v[l].x, q.x, fmaf(-v[l].y, q.y, o.x));
+                        o.y = fmaf(v[l].x, q.y, fmaf(v[l].y, q.x, o.y));
+                    }
+                    __stcg(&V[(size_t)gcol[j] * n + row], o);
+                }
+            }
+            if (threadIdx.x == 0 && cnt) atomicAdd(nrot, (unsigned long long)cnt);
+            __syncthreads();   // shared state is reused by the block's next super-column pair
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    }
+}
+
 __global__ void k_identity_f32(float2 *V, int n) {
     long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (long)n * n) return;
@@ -945,9 +1095,19 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     std::vector<int2> hpairs, hsched;
     std::vector<int> rstart;
     long long prev_rot = npairs;
-    // one cooperative launch per sweep when all its blocks can be resident, else one launch per round
-    int coop = 0, per_sm = 0, dev_coop = 0;
+    // one cooperative launch per sweep when all its blocks can be resident, else one launch per round;
+    // the blocked form when two super-columns of W32 fit the shared memory of a block
+    int coop = 0, per_sm = 0, dev_coop = 0, blk = 0, smem_optin = 0;
+    const int nsc = (n + SC - 1) / SC, nscp = nsc + (nsc & 1);
+    const size_t blk_smem = sizeof(float2) * 2 * SC * (size_t)n;
     cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, c->device);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (dev_coop && blk_smem + 4096 <= (size_t)smem_optin &&
+        cudaFuncSetAttribute(k_jacobi_sweep_blk_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk_smem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_sweep_blk_f32, SCT, blk_smem) == cudaSuccess &&
+        per_sm > 0)
+        blk = std::min(nscp / 2, per_sm * c->sms);
     if (dev_coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_sweep_f32, JTPB, 0) == cudaSuccess)
         coop = std::min(npad / 2, per_sm * c->sms);
     cudaGetLastError();
@@ -982,7 +1142,16 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
                 GS_CHECK_LAUNCH(c);
             }
         }
-        if (circle && coop > 0) {
+        if (circle && blk > 0) {
+            GS_CUDA(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
+            GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), st));
+            float tol32 = 1e-5f;
+            int mm = n, nn_ = n, nsc_ = nsc, nscp_ = nscp;
+            void *args[] = {&X32, &mm, &V32, &nn_, &nsc_, &nscp_, &tol32, &c->dcount, &c->bar, &c->terr};
+            GS_COUNT_LAUNCH(c);
+            GS_CUDA(c, cudaLaunchCooperativeKernel((const void *)k_jacobi_sweep_blk_f32, dim3(blk), dim3(SCT), args,
+                                                   blk_smem, st));
+        } else if (circle && coop > 0) {
             GS_CUDA(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
             GS_CUDA(c, cudaMemsetAsync(c->terr, 0, sizeof(int), st));
             float tol32 = 1e-5f;
@@ -997,7 +1166,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
             }
         }
         GS_CHECK_LAUNCH(c);
-        if (circle && coop > 0) {
+        if (circle && (blk > 0 || coop > 0)) {
             int herr = 0;
             GS_CUDA(c, cudaMemcpyAsync(&herr, c->terr, sizeof(int), cudaMemcpyDeviceToHost, st));
             GS_CUDA(c, cudaStreamSynchronize(st));
