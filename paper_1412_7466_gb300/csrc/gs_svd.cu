@@ -487,10 +487,15 @@ __global__ void __launch_bounds__(SCT) k_jacobi_sweep_blk_f32(float2 *W32, int m
             }
             if (threadIdx.x == 0) cnt = 0;
             __syncthreads();
-            for (int l = 0; l < 2 * SC; ++l) {
-                const float2 *src = W32 + (size_t)(gcol[l] >= 0 ? gcol[l] : 0) * m;
-                for (int i = threadIdx.x; i < m; i += SCT)
-                    xs[(size_t)l * m + i] = gcol[l] >= 0 ? __ldcg(&src[i]) : make_float2(0.f, 0.f);
+            // the 2 SC columns come in through L2 (written by other SMs in the previous round), the
+            // loads of a row index all in flight at once
+            for (int i = threadIdx.x; i < m; i += SCT) {
+                float2 v[2 * SC];
+#pragma unroll
+                for (int l = 0; l < 2 * SC; ++l)
+                    v[l] = gcol[l] >= 0 ? __ldcg(&W32[(size_t)gcol[l] * m + i]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int l = 0; l < 2 * SC; ++l) xs[(size_t)l * m + i] = v[l];
             }
             __syncthreads();
             if (r == 0) {   // the pairs inside each super-column: a circle over its SC columns
@@ -505,6 +510,7 @@ __global__ void __launch_bounds__(SCT) k_jacobi_sweep_blk_f32(float2 *W32, int m
                 float2 *dst = W32 + (size_t)gcol[l] * m;
                 for (int i = threadIdx.x; i < m; i += SCT) __stcg(&dst[i], xs[(size_t)l * m + i]);
             }
+#pragma unroll 2
             for (int row = threadIdx.x; row < n; row += SCT) {
                 float2 v[2 * SC];
 #pragma unroll
