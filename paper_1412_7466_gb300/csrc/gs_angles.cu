@@ -8,7 +8,7 @@
 //    of the complex64 translation -- for all R angles at the cost of streaming the operator three
 //    times.
 //  * Low rank: per angle, since the grating factorisation, B_phys and C depend on the angle: C x in
-//    double-float arithmetic, U^* and V Sigma in FP64, complex64 B_phys, fused combination
+//    double-float arithmetic, U^* and V Sigma in double-float, complex64 B_phys, fused combination
 //    (gs_lowrank_c64).
 //  * GMRES: segmented Arnoldi steps over the R angles (gs_seg.cuh, the kernels of the batched
 //    solver), each step captured once as a CUDA graph and replayed; the host reads one residual

@@ -83,6 +83,10 @@ void free_angle(AngleData &a) {
     dfree(a.dscale);
     dfree(a.coef);
     dfree(a.sigma);
+    dfree(a.WH2);
+    dfree(a.Vr2);
+    a.A2_off = false;
+    a.A2_ready = false;
     free_angle_geometry(a);
 }
 
@@ -99,6 +103,8 @@ void free_geometry(gs_ctx *c) {
     dfree(c->b32);
     dfree(c->img32);
     dfree(c->xdf);
+    dfree(c->adf);
+    c->adf_n = 0;
     dfree(c->iflag);
     dfree(c->htab);
     dfree(c->tab32.h);

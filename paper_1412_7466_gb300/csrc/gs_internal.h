@@ -56,6 +56,10 @@ struct AngleData {
     mutable bool C2_off = false;     // C has entries beyond GS_DF_LIMIT (or no memory for the copy):
                                      // the inner operator keeps the FP64 product
     mutable bool C2_ready = false;   // C2 holds the split of the current C
+    mutable float4 *WH2 = nullptr;   // double-float U^H rows (cols x nC row-major) for the mixed inner operator
+    mutable float4 *Vr2 = nullptr;   // double-float rows of V Sigma diag(coef) (nB x cols row-major)
+    mutable bool A2_off = false;     // no memory for them, or an entry beyond GS_DF_LIMIT: FP64 products
+    mutable bool A2_ready = false;   // WH2 and Vr2 hold the split of the current factorisation
     cplx *beta = nullptr;        // n, last solution
     int sweeps = 0;              // FP64 Jacobi sweeps of the grating factorisation
     int sweeps32 = 0;            // FP32-guided sweeps before them
@@ -135,6 +139,8 @@ struct gs_ctx {
     float2 *b32 = nullptr;                               // n, complex64 copy of the source coefficients
     float4 *img32 = nullptr;                             // 3M, (hi, lo) float image coordinates
     float4 *xdf = nullptr;                               // n, double-float split of the operator input
+    float4 *adf = nullptr;                               // adf_n, double-float split of A^+'s vectors
+    long adf_n = 0;
     int *iflag = nullptr;                                // one int, device-side flag
     cplx *htab = nullptr;                                // pair table of translation coefficients (optional)
     gs_tab32 tab32;                                      // its complex64 copy (on first complex64 use)

@@ -127,7 +127,9 @@ __global__ void k_split_df(const cplx *__restrict__ a, long n, float4 *__restric
 constexpr int GEMV_DF_THREADS = 128;
 __global__ void __launch_bounds__(GEMV_DF_THREADS) k_gemv_rows_df(const float4 *__restrict__ C2, int nrows, long ncols,
                                                                  const float4 *__restrict__ x2,
-                                                                 cplx *__restrict__ y) {
+                                                                 cplx *__restrict__ y,
+                                                                 const double *__restrict__ scale = nullptr,
+                                                                 float2 *__restrict__ y32 = nullptr) {
     const int r = blockIdx.x;
     if (r >= nrows) return;
     const float4 *a = C2 + (size_t)r * ncols;
@@ -141,8 +143,31 @@ __global__ void __launch_bounds__(GEMV_DF_THREADS) k_gemv_rows_df(const float4 *
     if (threadIdx.x == 0) {
         dfc t = part[0];
         for (int k = 1; k < GEMV_DF_THREADS / 32; ++k) dfc_add(t, part[k]);
-        y[r] = C((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
+        cplx v = C((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
+        if (scale) v = cscale(v, scale[r]);   // scale, y32: optional row scale and complex64 copy
+        y[r] = v;
+        if (y32) y32[r] = make_float2((float)v.x, (float)v.y);
     }
+}
+
+// WH2[j][i] = split(conj(W[i][j])) for i < nr, j < ncols (W column-major with leading dimension m):
+// the rows of U^H restricted to C's rows, for k_gemv_rows_df
+__global__ void k_split_df_conjT(const cplx *__restrict__ W, int m, int nr, int ncols, float4 *__restrict__ WH2) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)nr * ncols) return;
+    const int j = (int)(e / nr), i = (int)(e % nr);
+    const cplx v = W[(size_t)j * m + i];
+    WH2[e] = df_split(v.x, -v.y);
+}
+
+// Vr2[r][j] = split(Vr[r][j] coef[j]) (row-major nrows x ncols); flag set beyond lim
+__global__ void k_split_df_colscale(const cplx *__restrict__ Vr, int nrows, int ncols, const double *__restrict__ coef,
+                                    float4 *__restrict__ Vr2, double lim, int *__restrict__ flag) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)nrows * ncols) return;
+    const cplx v = cscale(Vr[e], coef[e % ncols]);
+    Vr2[e] = df_split(v.x, v.y);
+    if (!(fabs(v.x) <= lim && fabs(v.y) <= lim)) *flag = 1;
 }
 
 // y[r] = x[r] - s[r] t[r] + s[r] (B v)[r] with B and v complex64 (FP32 products), warp per row.  v
@@ -442,6 +467,46 @@ int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
             a.C2_off = true;
         }
     }
+    // double-float copies of U^H (C's rows) and of V Sigma diag(coef) for A^+, once per factorisation;
+    // their vectors go through the context's scratch adf, which geometry changes free
+    const long need = std::max((long)nC, (long)ly.cols);
+    if (!a.A2_off && c->adf_n < need) {
+        if (c->adf) cudaFree(c->adf);
+        c->adf = nullptr;
+        c->adf_n = 0;
+        if (cudaMalloc((void **)&c->adf, sizeof(float4) * need) != cudaSuccess) {
+            cudaGetLastError();   // no room: the FP64 products stay
+            c->adf = nullptr;
+            a.A2_off = true;
+        } else {
+            c->adf_n = need;
+        }
+    }
+    if (!a.A2_ready && !a.A2_off) {
+        const long nw = (long)ly.cols * nC, nv = (long)nB * ly.cols;
+        if (!a.WH2 && (cudaMalloc((void **)&a.WH2, sizeof(float4) * nw) != cudaSuccess ||
+                       cudaMalloc((void **)&a.Vr2, sizeof(float4) * nv) != cudaSuccess)) {
+            cudaGetLastError();   // no room: the FP64 products stay
+            if (a.WH2) cudaFree(a.WH2);
+            a.WH2 = nullptr;
+            a.Vr2 = nullptr;
+            a.A2_off = true;
+        }
+        if (a.WH2 && !a.A2_off) {
+            GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
+            GS_COUNT_LAUNCH(c);
+            k_split_df_conjT<<<(int)((nw + 255) / 256), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, a.WH2);
+            GS_COUNT_LAUNCH(c);
+            k_split_df_colscale<<<(int)((nv + 255) / 256), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, a.coef, a.Vr2,
+                                                                                GS_DF_LIMIT, c->iflag);
+            GS_CHECK_LAUNCH(c);
+            int big = 0;
+            GS_CUDA(c, cudaMemcpyAsync(&big, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            GS_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (big) a.A2_off = true;
+            else a.A2_ready = true;
+        }
+    }
     if (a.C2 && !a.C2_ready) {
         const long nc2 = (long)nC * n;
         GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
@@ -463,8 +528,8 @@ int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
     return GS_OK;
 }
 
-// y = x - s .* t + s .* (B_phys A^+ C x) for the mixed inner operator, t = T x given: C x in
-// double-float arithmetic (or FP64 when the copy is off), A^+ in FP64, B_phys in complex64.  Only
+// y = x - s .* t + s .* (B_phys A^+ C x) for the mixed inner operator, t = T x given: C x and A^+
+// in double-float arithmetic (each in FP64 when its copies are off), B_phys in complex64.  Only
 // launches kernels (after gs_prepare_c64).
 int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, cplx *y) {
     const Layout &ly = c->lay;
@@ -478,10 +543,23 @@ int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, 
     } else {
         k_gemv_rows_blk<<<nC, GEMV_BLK_THREADS, 0, c->stream>>>(a.Cm, nC, n, x, c->g);
     }
-    GS_COUNT_LAUNCH(c);
-    k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
-    GS_COUNT_LAUNCH(c);
-    k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x, c->x32);
+    if (a.A2_ready && a.WH2 && a.Vr2 && c->adf && c->adf_n >= std::max((long)nC, (long)ly.cols)) {
+        // A^+ g in double-float: U^H g, then (V Sigma diag(coef)) (U^H g), scaled by D
+        GS_COUNT_LAUNCH(c);
+        k_split_df<<<(nC + 255) / 256, 256, 0, c->stream>>>(c->g, nC, c->adf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows_df<<<ly.cols, GEMV_DF_THREADS, 0, c->stream>>>(a.WH2, ly.cols, nC, c->adf, c->w);
+        GS_COUNT_LAUNCH(c);
+        k_split_df<<<(ly.cols + 255) / 256, 256, 0, c->stream>>>(c->w, ly.cols, c->adf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows_df<<<nB, GEMV_DF_THREADS, 0, c->stream>>>(a.Vr2, nB, ly.cols, c->adf, c->x, a.dscale, c->x32);
+    } else {
+        GS_COUNT_LAUNCH(c);
+        k_gemv_colsH<<<warps_blocks(ly.cols), 256, 0, c->stream>>>(a.W, ly.rows, nC, ly.cols, c->g, a.coef, c->w);
+        GS_COUNT_LAUNCH(c);
+        k_gemv_rows<<<warps_blocks(nB), 256, 0, c->stream>>>(a.Vr, nB, ly.cols, ly.cols, c->w, a.dscale, c->x,
+                                                             c->x32);
+    }
     GS_COUNT_LAUNCH(c);
     if (c->Sblk) {   // general shapes: y = x + S (B v - t), in two steps through the scratch c->v6
         k_B_minus_t<float2><<<warps_blocks(n), 256, 0, c->stream>>>(a.B32, n, nB, c->x, t, c->v6);

@@ -1036,6 +1036,8 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     const Layout &ly = c->lay;
     const int m = ly.rows, n = ly.cols;
     cudaStream_t st = c->stream;
+    a.A2_ready = false;   // W, Vr and coef are rewritten: their double-float copies are stale
+    a.A2_off = false;
     cplx *Aqr = c->Vtmp;                       // m x n: scaled A, then R and the reflectors
     cplx *X = c->Xtmp;                         // n x n: R^*, rotated into W_x
     cplx *Vx = c->Vxtmp;                       // n x n: accumulated rotations

@@ -241,8 +241,8 @@ def test_translate_c64_matches_oracle(small):
 
 def test_operator_c64_matches_oracle(small):
     """complex64 inner operator: complex64 translation and a complex64 copy of B_phys with FP32
-    products, C x in double-float arithmetic, U^* and V Sigma in FP64: single-precision accuracy,
-    1e-5 relative in norm."""
+    products, C x, U^* and V Sigma in double-float arithmetic: single-precision accuracy, 1e-5
+    relative in norm."""
     from paper_1412_7466_gb300 import GS_C64
     cfg, prob, gs = small
     rng = np.random.default_rng(6)
@@ -300,6 +300,28 @@ def test_new_geometry_keeps_grating_factorisation():
     b = gs2.bragg()
     gs2.close()
     np.testing.assert_allclose(np.r_[a["c"], a["d"]], np.r_[b["c"], b["d"]], rtol=0, atol=1e-12)
+
+
+def test_new_geometry_after_mixed_solve():
+    """A mixed solve, then gs_set_inclusions with another geometry and a second mixed solve on the
+    same context (the geometry's scratch, which the double-float low-rank products use, is rebuilt
+    in between): the second solve matches the same geometry's mixed solve on a fresh context."""
+    from paper_1412_7466_gb300 import GS_C64
+    cfg = W.config("small")
+    g, th = cfg["grating"], cfg["theta"]
+    d2 = W.disks(7, 0.04, 0.02, 2.0, g["k"][0], seed=77, p=10)
+    gs = _setup_gpu(g, th, cfg["disks"])
+    gs.solve(tol=1e-12, maxit=500, precision=GS_C64)
+    gs.set_inclusions(d2)
+    gs.factor()
+    gs.solve(tol=1e-12, maxit=500, precision=GS_C64)
+    a = gs.bragg()
+    gs.close()
+    gs2 = _setup_gpu(g, th, d2)
+    gs2.solve(tol=1e-12, maxit=500, precision=GS_C64)
+    b = gs2.bragg()
+    gs2.close()
+    np.testing.assert_allclose(np.r_[a["c"], a["d"]], np.r_[b["c"], b["d"]], rtol=0, atol=1e-11)
 
 
 @pytest.mark.parametrize("budget", [0.0, -1.0])
