@@ -355,6 +355,32 @@ __global__ void __launch_bounds__(BATCH_DF_THREADS)
     }
 }
 
+// y[g][r] = scale[r] (A2 x2_g)[r] for every active geometry g, in double-float arithmetic (A2 rows x
+// ncols row-major, x2_g = x2 + g ldx, both (hi, lo) complex64 pairs); the A^+ products of the mixed
+// inner operator, whose matrices (the angle's U^H and V Sigma diag(coef)) all geometries share.  One
+// block per (row, geometry), the geometry fastest so that neighbouring blocks read the same row.
+__global__ void __launch_bounds__(BATCH_DF_THREADS)
+    k_batch_gemv_df(const float4 *__restrict__ A2, int nrows, int ncols, const float4 *__restrict__ x2, int ldx, int G,
+                    const int *__restrict__ active, cplx *__restrict__ y, int ldy, const double *__restrict__ scale,
+                    float2 *__restrict__ y32) {
+    const int r = blockIdx.x / G, g = blockIdx.x % G;
+    if (r >= nrows || (active && !active[g])) return;
+    dfc s = {0.f, 0.f, 0.f, 0.f};
+    dfc_row_dot<BATCH_DF_THREADS>(s, A2 + (size_t)r * ncols, x2 + (size_t)g * ldx, ncols, threadIdx.x);
+    dfc_warp_sum(s);
+    __shared__ dfc part[BATCH_DF_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dfc t = part[0];
+        for (int k = 1; k < BATCH_DF_THREADS / 32; ++k) dfc_add(t, part[k]);
+        cplx v = C((double)t.rh + (double)t.rl, (double)t.ih + (double)t.il);
+        if (scale) v = cscale(v, scale[r]);
+        y[(size_t)g * ldy + r] = v;
+        if (y32) y32[(size_t)g * ldy + r] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
 // Bragg: gfull = f - C_g beta_g on the C rows, f elsewhere (one geometry)
 __global__ void k_b_f_minus_Cx(const cplx *__restrict__ Cg, int nC, int n, const cplx *__restrict__ x,
                                const cplx *__restrict__ f, int rows, cplx *__restrict__ gout) {
@@ -419,6 +445,7 @@ struct gs_batch {
     float2 *b32 = nullptr;
     float4 *img32 = nullptr;       // (hi, lo) float image coordinates, 3 M_g per geometry at 3 moff_g
     float4 *xdf = nullptr;         // Ntot: double-float split of the operator input
+    float4 *adf = nullptr;         // G max(nC, cols): double-float split of A^+'s vectors
     int *dflag = nullptr;          // range flag of the double-float split of C
     cplx *gC = nullptr, *w = nullptr, *xv = nullptr;   // G nC, G cols, G cols
     float2 *xv32 = nullptr;        // G cols: complex64 copy of xv (the B_phys input of the mixed operator)
@@ -482,6 +509,7 @@ void batch_free(gs_batch *b) {
     dfree_b(b->b32);
     dfree_b(b->img32);
     dfree_b(b->xdf);
+    dfree_b(b->adf);
     dfree_b(b->dflag);
     dfree_b(b->gC);
     dfree_b(b->w);
@@ -609,11 +637,26 @@ int batch_apply(gs_ctx *c, gs_batch *b, int angle, const cplx *x, cplx *y, int p
         k_batch_C<<<wblk((long)b->G * nC), 256, 0, st>>>(b->Cm[angle], b->coff, b->geo, b->G, nC, b->nc, active, x,
                                                          b->gC);
     }
-    GS_COUNT_LAUNCH(c);
-    k_batch_UH<<<wblk((long)b->G * cols), 256, 0, st>>>(a.W, ly.rows, nC, cols, b->gC, nC, a.coef, b->G, active, b->w);
-    GS_COUNT_LAUNCH(c);
-    k_batch_V<<<wblk((long)b->G * nB), 256, 0, st>>>(a.Vr, nB, cols, b->w, a.dscale, b->G, active, b->xv,
-                                                       precision == GS_C64 ? b->xv32 : nullptr);
+    if (precision == GS_C64 && a.A2_ready && a.WH2 && a.Vr2 && b->adf) {
+        // A^+ in double-float: U^H gC_g, then (V Sigma diag(coef)) w_g, scaled by D
+        GS_COUNT_LAUNCH(c);
+        k_b_split_df<<<nblk((long)b->G * nC), 256, 0, st>>>(b->gC, (long)b->G * nC, b->adf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_batch_gemv_df<<<b->G * cols, BATCH_DF_THREADS, 0, st>>>(a.WH2, cols, nC, b->adf, nC, b->G, active, b->w, cols,
+                                                                    nullptr, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_b_split_df<<<nblk((long)b->G * cols), 256, 0, st>>>(b->w, (long)b->G * cols, b->adf, 0.0, nullptr);
+        GS_COUNT_LAUNCH(c);
+        k_batch_gemv_df<<<b->G * nB, BATCH_DF_THREADS, 0, st>>>(a.Vr2, nB, cols, b->adf, cols, b->G, active, b->xv, nB,
+                                                                  a.dscale, b->xv32);
+    } else {
+        GS_COUNT_LAUNCH(c);
+        k_batch_UH<<<wblk((long)b->G * cols), 256, 0, st>>>(a.W, ly.rows, nC, cols, b->gC, nC, a.coef, b->G, active,
+                                                            b->w);
+        GS_COUNT_LAUNCH(c);
+        k_batch_V<<<wblk((long)b->G * nB), 256, 0, st>>>(a.Vr, nB, cols, b->w, a.dscale, b->G, active, b->xv,
+                                                           precision == GS_C64 ? b->xv32 : nullptr);
+    }
     GS_COUNT_LAUNCH(c);
     if (precision == GS_C64) {
         k_batch_Bcombine32<<<wblk(b->Ntot), 256, 0, st>>>(b->B32[angle], b->Ntot, nB, b->gid, b->nc, active, b->xv32,
@@ -1010,6 +1053,7 @@ int gs_factor_batch(gs_ctx *c) {
             GS_CUDA(c, cudaStreamSynchronize(c->stream));
             if (big) dfree_b(b->C2[q]);
         }
+        GS_TRY(gs_prepare_apinv_df(c, c->ang[q]));   // the angle's A^+ in double-float, shared by all geometries
     }
     // workspace
     b->kdim = 0;
@@ -1024,6 +1068,7 @@ int gs_factor_batch(gs_ctx *c) {
     GS_TRY(dalloc_b(c, &b->b32, N));
     GS_TRY(dalloc_b(c, &b->img32, 3 * (size_t)b->Mtot));
     GS_TRY(dalloc_b(c, &b->xdf, N));
+    GS_TRY(dalloc_b(c, &b->adf, (size_t)G * std::max(ly.nC(), ly.cols)));
     for (int g = 0; g < G; ++g)
         GS_TRY(gs_build_images_c64(c, b->xy + 2 * (size_t)b->moff[g], b->M[g], b->img32 + 3 * (size_t)b->moff[g],
                                    c->stream));

@@ -279,6 +279,7 @@ int gs_apply_impl(gs_ctx *c, const AngleData &a, const cplx *x, cplx *y, int pre
 // per geometry and angle (allocates), then y = x - s t + s B_phys A^+ C x for a given t = T x
 // (launches only; uses the context's scratch vectors g, w, x, xdf)
 int gs_prepare_c64(gs_ctx *c, const AngleData &a);
+int gs_prepare_apinv_df(gs_ctx *c, const AngleData &a);
 int gs_lowrank_c64(gs_ctx *c, const AngleData &a, const cplx *x, const cplx *t, cplx *y);
 int gs_rhs_impl(gs_ctx *c, const AngleData &a, cplx *b);
 // w = B_phys A^+ f: incoming coefficients of the empty grating's field about every centre

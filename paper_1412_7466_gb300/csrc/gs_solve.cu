@@ -448,27 +448,12 @@ int gs_pinv_impl(gs_ctx *c, const AngleData &a, const cplx *g, cplx *x) {
     return GS_OK;
 }
 
-// complex64 copy of B_phys and double-float copy of C for the mixed inner operator, once per
-// geometry and angle (allocates: not inside a stream capture)
-int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
+// double-float copies of U^H (C's rows) and of V Sigma diag(coef) for the mixed inner operator's A^+,
+// once per factorisation (allocates: not inside a stream capture); a.A2_ready tells whether they hold
+int gs_prepare_apinv_df(gs_ctx *c, const AngleData &a) {
     const Layout &ly = c->lay;
-    const int n = c->n(), nB = ly.nB(), nC = ly.nC();
-    if (!a.B32) {
-        const long nb = (long)n * nB;
-        GS_CUDA(c, cudaMalloc((void **)&a.B32, sizeof(float2) * nb));
-        GS_COUNT_LAUNCH(c);
-        k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
-    }
-    if (!a.C2 && !a.C2_off) {
-        const long nc2 = (long)nC * n;
-        if (cudaMalloc((void **)&a.C2, sizeof(float4) * nc2) != cudaSuccess) {
-            cudaGetLastError();   // no room for the copy: the FP64 product stays
-            a.C2 = nullptr;
-            a.C2_off = true;
-        }
-    }
-    // double-float copies of U^H (C's rows) and of V Sigma diag(coef) for A^+, once per factorisation;
-    // their vectors go through the context's scratch adf, which geometry changes free
+    const int nB = ly.nB(), nC = ly.nC();
+    // the vectors go through the context's scratch adf, which geometry changes free
     const long need = std::max((long)nC, (long)ly.cols);
     if (!a.A2_off && c->adf_n < need) {
         if (c->adf) cudaFree(c->adf);
@@ -481,6 +466,11 @@ int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
         } else {
             c->adf_n = need;
         }
+    }
+    if (!a.A2_off && !c->iflag && cudaMalloc((void **)&c->iflag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->iflag = nullptr;
+        a.A2_off = true;
     }
     if (!a.A2_ready && !a.A2_off) {
         const long nw = (long)ly.cols * nC, nv = (long)nB * ly.cols;
@@ -507,6 +497,29 @@ int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
             else a.A2_ready = true;
         }
     }
+    return GS_OK;
+}
+
+// complex64 copy of B_phys and double-float copy of C for the mixed inner operator, once per
+// geometry and angle (allocates: not inside a stream capture)
+int gs_prepare_c64(gs_ctx *c, const AngleData &a) {
+    const Layout &ly = c->lay;
+    const int n = c->n(), nB = ly.nB(), nC = ly.nC();
+    if (!a.B32) {
+        const long nb = (long)n * nB;
+        GS_CUDA(c, cudaMalloc((void **)&a.B32, sizeof(float2) * nb));
+        GS_COUNT_LAUNCH(c);
+        k_to_c64_vec<<<(int)((nb + 255) / 256), 256, 0, c->stream>>>(a.B, nb, a.B32);
+    }
+    if (!a.C2 && !a.C2_off) {
+        const long nc2 = (long)nC * n;
+        if (cudaMalloc((void **)&a.C2, sizeof(float4) * nc2) != cudaSuccess) {
+            cudaGetLastError();   // no room for the copy: the FP64 product stays
+            a.C2 = nullptr;
+            a.C2_off = true;
+        }
+    }
+    GS_TRY(gs_prepare_apinv_df(c, a));
     if (a.C2 && !a.C2_ready) {
         const long nc2 = (long)nC * n;
         GS_CUDA(c, cudaMemsetAsync(c->iflag, 0, sizeof(int), c->stream));
