@@ -605,19 +605,22 @@ __global__ void __launch_bounds__(256) k_offdiag_max(const cplx *G, int n, unsig
 __global__ void __launch_bounds__(256) k_zgemm_hn(const cplx *__restrict__ A, const cplx *__restrict__ B,
                                                   cplx *__restrict__ Cm, int n);
 
-// C = A B, complex128, all n x n column-major (64 x 64 tile per block, 4 x 4 per thread)
+// C = A B, complex128, all n x n column-major (64 x 64 tile per block, 4 x 4 per thread); with
+// LOWER_A, A is lower triangular (R^*) and a row tile stops at its last non-zero column
 constexpr int ZG = 64, ZK = 8;
+template <bool LOWER_A = false>
 __global__ void __launch_bounds__(256) k_zgemm_nn(const cplx *__restrict__ A, const cplx *__restrict__ B,
                                                   cplx *__restrict__ Cm, int n) {
     __shared__ cplx As[ZK][ZG + 1], Bs[ZK][ZG + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.x * ZG, j0 = blockIdx.y * ZG;
+    const int kend = LOWER_A ? min(n, i0 + ZG) : n;
     cplx acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = C(0.0, 0.0);
-    for (int k0 = 0; k0 < n; k0 += ZK) {
+    for (int k0 = 0; k0 < kend; k0 += ZK) {
         __syncthreads();
         for (int e = threadIdx.x; e < ZG * ZK; e += 256) {
             const int i = e % ZG, k = e / ZG;
@@ -1266,7 +1269,7 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
         }
     }
     GS_COUNT_LAUNCH(c);
-    k_zgemm_nn<<<zg, 256, 0, st>>>(X, Vx, T, n);
+    k_zgemm_nn<true><<<zg, 256, 0, st>>>(X, Vx, T, n);
     GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaMemcpyAsync(X, T, sizeof(cplx) * nn, cudaMemcpyDeviceToDevice, st));
     GS_CUDA(c, cudaEventRecord(ev.e[4], st));
