@@ -31,13 +31,24 @@ namespace {
 
 constexpr int JTPB = 256;
 
+// FP64 accumulations written as FMA chains: the FP64 pipe is the bound of the kernels below, and
+// a*b + c*d + acc as written costs a multiply, an FMA and an add where two FMAs do
+__device__ __forceinline__ double abs2_acc(cplx a, double s) { return fma(a.x, a.x, fma(a.y, a.y, s)); }
+__device__ __forceinline__ void cdot_acc(double &re, double &im, cplx a, cplx b) {   // += conj(a) b
+    re = fma(a.x, b.x, fma(a.y, b.y, re));
+    im = fma(a.x, b.y, fma(-a.y, b.x, im));
+}
+__device__ __forceinline__ cplx csub_mul(cplx y, cplx f, cplx v) {   // y - f v
+    return C(fma(-f.x, v.x, fma(f.y, v.y, y.x)), fma(-f.x, v.y, fma(-f.y, v.x, y.y)));
+}
+
 __global__ void k_colnorm_scale(cplx *A, int lda, int rows, int c0, int c1, double *dscale) {
     int col = c0 + blockIdx.x;
     if (col >= c1) return;
     __shared__ double sh[32];
     cplx *a = A + (size_t)col * lda;
     double s = 0.0;
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) s += cabs2(a[i]);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) s = abs2_acc(a[i], s);
     s = block_sum(s, sh);
     double sc = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
     if (threadIdx.x == 0) dscale[col] = sc;
@@ -65,10 +76,9 @@ __device__ void jacobi_pair(cplx *W, int m, cplx *V, int n, int pc, int qc, doub
     double al = 0, be = 0, gr = 0, gi = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         cplx x = wp[i], y = wq[i];
-        al += cabs2(x);
-        be += cabs2(y);
-        gr += x.x * y.x + x.y * y.y;   // conj(x) y
-        gi += x.x * y.y - x.y * y.x;
+        al = abs2_acc(x, al);
+        be = abs2_acc(y, be);
+        cdot_acc(gr, gi, x, y);   // conj(x) y
     }
     // the four sums in one block reduction
     al = warp_sum(al);
@@ -779,7 +789,7 @@ __global__ void k_sigma(const cplx *W, int m, int n, double eps, double *sigma, 
     __shared__ double sh[32];
     const cplx *a = W + (size_t)col * m;
     double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s += cabs2(a[i]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s = abs2_acc(a[i], s);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
         double sg = sqrt(s);
@@ -874,7 +884,7 @@ __global__ void __launch_bounds__(1024) k_qr_pivot_house(cplx *A, int m, int n, 
     __syncthreads();
     cplx *a = A + (size_t)j * m;
     double s2 = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) s2 += cabs2(a[i]);
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) s2 = abs2_acc(a[i], s2);
     s2 = block_sum(s2, shs);
     if (threadIdx.x == 0) {
         cplx x0 = a[j];
@@ -906,8 +916,7 @@ __global__ void k_qr_apply(cplx *A, int m, int n, int j, const cplx *tau, double
     for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
         cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
         cplx ai = a[i];
-        wr += vi.x * ai.x + vi.y * ai.y;
-        wi += vi.x * ai.y - vi.y * ai.x;
+        cdot_acc(wr, wi, vi, ai);
     }
     wr = block_sum(wr, sh);
     wi = block_sum(wi, sh);
@@ -915,9 +924,9 @@ __global__ void k_qr_apply(cplx *A, int m, int n, int j, const cplx *tau, double
     double s2 = 0.0;
     for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
         cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
-        cplx ai = csub(a[i], cmul(f, vi));
+        cplx ai = csub_mul(a[i], f, vi);
         a[i] = ai;
-        if (i > j) s2 += cabs2(ai);
+        if (i > j) s2 = abs2_acc(ai, s2);
     }
     s2 = block_sum(s2, sh);
     if (threadIdx.x == 0) nrm2[k] = s2;
@@ -928,7 +937,7 @@ __global__ void k_colnorm2(const cplx *A, int m, int n, double *nrm2) {
     if (col >= n) return;
     __shared__ double sh[32];
     double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s += cabs2(A[(size_t)col * m + i]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s = abs2_acc(A[(size_t)col * m + i], s);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) nrm2[col] = s;
 }
@@ -965,15 +974,14 @@ __global__ void k_apply_reflector(const cplx *Aqr, int m, int j, const cplx *tau
     for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
         cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
         cplx yi = y[i];
-        wr += vi.x * yi.x + vi.y * yi.y;
-        wi += vi.x * yi.y - vi.y * yi.x;
+        cdot_acc(wr, wi, vi, yi);
     }
     wr = block_sum(wr, sh);
     wi = block_sum(wi, sh);
     cplx f = cmul(tau[j], C(wr, wi));
     for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
         cplx vi = (i == j) ? C(1.0, 0.0) : v[i];
-        y[i] = csub(y[i], cmul(f, vi));
+        y[i] = csub_mul(y[i], f, vi);
     }
 }
 
@@ -997,15 +1005,14 @@ __global__ void __launch_bounds__(256) k_apply_reflectors_all(const cplx *__rest
         for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
             const cplx vi = (i == j) ? C(1.0, 0.0) : __ldg(&v[i]);
             const cplx yi = ys[i];
-            wr += vi.x * yi.x + vi.y * yi.y;
-            wi += vi.x * yi.y - vi.y * yi.x;
+            cdot_acc(wr, wi, vi, yi);
         }
         wr = block_sum(wr, sh);
         wi = block_sum(wi, sh);
         const cplx f = cmul(tau[j], C(wr, wi));
         for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
             const cplx vi = (i == j) ? C(1.0, 0.0) : __ldg(&v[i]);
-            ys[i] = csub(ys[i], cmul(f, vi));
+            ys[i] = csub_mul(ys[i], f, vi);
         }
         __syncthreads();   // the next reflector's inner product reads entries other threads updated
     }
