@@ -169,6 +169,38 @@ __global__ void __launch_bounds__(JTPB) k_jacobi_pairs(cplx *W, int m, cplx *V, 
     jacobi_pair(W, m, V, n, pq.x, pq.y, tol, nrot);
 }
 
+// The pairs (i, c) with c one of the nt columns cols[] (inT[] flags them) that lie further than tol
+// from orthogonal, by the criterion of jacobi_pair, from the columns themselves (a warp per (c, i));
+// appended to pairs[] as (min, max), a pair of two listed columns once
+__global__ void k_cols_violators(const cplx *__restrict__ W, int m, int n, const int *__restrict__ cols, int nt,
+                                 const int *__restrict__ inT, double tol, int2 *__restrict__ pairs,
+                                 unsigned long long *count) {
+    const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (long)nt * n) return;
+    const int k = (int)(gw / n), i = (int)(gw % n), cc = cols[k];
+    if (i == cc || (inT[i] && i < cc)) return;
+    const cplx *wi = W + (size_t)i * m, *wc = W + (size_t)cc * m;
+    double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+    for (int e = lane; e < m; e += 32) {
+        const cplx x = wi[e], y = wc[e];
+        al = abs2_acc(x, al);
+        be = abs2_acc(y, be);
+        cdot_acc(gr, gi, x, y);
+    }
+    al = warp_sum(al);
+    be = warp_sum(be);
+    gr = warp_sum(gr);
+    gi = warp_sum(gi);
+    if (lane == 0) {
+        const double g = hypot(gr, gi);
+        if (g != 0.0 && g > tol * sqrt(al * be)) {
+            const unsigned long long q = atomicAdd(count, 1ull);
+            pairs[q] = make_int2(min(i, cc), max(i, cc));
+        }
+    }
+}
+
 // The pairs (r, c), r < c, whose Gram entry G[r][c] = <w_r, w_c> (G column-major n x n) lies further
 // than tol from orthogonal, by the criterion of jacobi_pair; appended to pairs[] through *count
 __global__ void k_gram_violators(const cplx *G, int n, double tol, int2 *pairs, unsigned long long *count) {
@@ -1287,14 +1319,33 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
     // finds them, and only they are rotated, in rounds of disjoint pairs.  A sweep ends the phase
     // when the Gram matrix shows no pair further than tol from orthogonal or when none of the
     // listed pairs, re-tested from its columns, needs a rotation.
+    // After a listed pass that touched few columns, only the pairs involving those columns can have
+    // moved since the last check (every other pair was below tol then and is unchanged), so the next
+    // check computes just their inner products from the columns instead of the whole Gram matrix.
+    constexpr int TMAX = 128;
+    int *dcols = (int *)(vsched + npairs), *dinT = dcols + TMAX;   // after both pair lists in a.W
+    std::vector<int> tcols, tflag;
+    bool partial = false;
+    const bool room_t = (size_t)m * n * sizeof(cplx) >= sizeof(int2) * 2 * (size_t)npairs + sizeof(int) * (TMAX + n);
     for (int sweep = 0; sweep < 30; ++sweep) {
         GS_CUDA(c, cudaMemsetAsync(c->dcount, 0, 2 * sizeof(unsigned long long), st));
         bool circle = true;
         if (sweep >= 2 && npairs > 0) {
-            GS_COUNT_LAUNCH(c);
-            k_zgemm_hn<<<zg, 256, 0, st>>>(X, X, G, n);
-            GS_COUNT_LAUNCH(c);
-            k_gram_violators<<<eb, 256, 0, st>>>(G, n, tol, vlist, c->dcount + 1);
+            if (partial) {
+                tflag.assign(n, 0);
+                for (int q : tcols) tflag[q] = 1;
+                GS_CUDA(c, cudaMemcpyAsync(dcols, tcols.data(), sizeof(int) * tcols.size(), cudaMemcpyHostToDevice, st));
+                GS_CUDA(c, cudaMemcpyAsync(dinT, tflag.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+                const long warps = (long)tcols.size() * n;
+                GS_COUNT_LAUNCH(c);
+                k_cols_violators<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(X, n, n, dcols, (int)tcols.size(),
+                                                                                 dinT, tol, vlist, c->dcount + 1);
+            } else {
+                GS_COUNT_LAUNCH(c);
+                k_zgemm_hn<<<zg, 256, 0, st>>>(X, X, G, n);
+                GS_COUNT_LAUNCH(c);
+                k_gram_violators<<<eb, 256, 0, st>>>(G, n, tol, vlist, c->dcount + 1);
+            }
             GS_CHECK_LAUNCH(c);
             unsigned long long nv = 0;
             GS_CUDA(c, cudaMemcpyAsync(&nv, c->dcount + 1, sizeof(nv), cudaMemcpyDeviceToHost, st));
@@ -1314,8 +1365,20 @@ int gs_factor_angle(gs_ctx *c, AngleData &a) {
                                                                             c->dcount);
                 }
                 GS_CHECK_LAUNCH(c);
+                // the columns this pass touched (hpairs holds its listed pairs)
+                tcols.clear();
+                tflag.assign(n, 0);
+                for (const int2 &pq : hpairs) {
+                    for (int q : {pq.x, pq.y})
+                        if (!tflag[q]) {
+                            tflag[q] = 1;
+                            tcols.push_back(q);
+                        }
+                    if ((int)tcols.size() > TMAX) break;
+                }
             }
         }
+        partial = !circle && (int)tcols.size() <= TMAX && room_t;
         if (circle) {
             for (int r = 0; r < npad - 1; ++r) {
                 GS_COUNT_LAUNCH(c);
